@@ -1,0 +1,328 @@
+"""KIFMM matvec throughput (targets/s) on GB300 -- one JSON line on stdout.
+
+Default workload: the magnetostatic demag double-layer matvec on the unit cube,
+n = 296 squares per face (1,051,392 surface triangles, one quadrature point each),
+density n.M with M = z-hat, targets = sources, mixed precision.
+
+A step is one kifmm_fmm_matvec over the whole point set (gather, S2U, U2U, X, M2L,
+L2L, D2T, P2P).  Tree and operators are built once before timing (the geometry is
+fixed across the matvecs of an iterative solve).  `value` is device-timed with
+CUDA events on the launching stream, inputs resident in HBM; `e2e` includes the
+pinned host->device copy of q and the device->host copy of the result every step.
+The working set (D2T rows, check potentials, operators: > 1 GB) is far larger than
+the 129 MB L2, so no explicit flush is done between steps.
+
+--impl reference times the FP64 CPU oracle (direct sum) on the host cores on a
+bounded sample of targets per step.  Under torchrun each rank runs an independent
+replica (weak scaling); rank 0 reports.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "demag_cube_1m"
+METRIC = "KIFMM matvec targets/s at rel-err<=1e-6 vs FP64 oracle"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                r = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                   timeout=5)
+                f = [x.strip() for x in r.stdout.strip().split(",")]
+                if len(f) >= 7:
+                    self.samples.append(f)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def make_inputs(name, device):
+    """Points, weights, normals on the device (GPU quadrature) and the density."""
+    import torch
+
+    from paper_1605_01715_gb300 import kifmm_quadrature_points
+    wl = synth.workload(name)
+    m = wl["mesh"]
+    tri = torch.from_numpy(np.ascontiguousarray(m.tri.reshape(-1, 9))).to(device)
+    sph = torch.from_numpy(np.ascontiguousarray(m.sph)).to(device)
+    xyz, w, nrm = kifmm_quadrature_points(tri, sph)
+    if wl["kernel"] == "dl":
+        M = wl["magnetization"]
+        sigma = nrm[0] * M[0] + nrm[1] * M[1] + nrm[2] * M[2]
+    else:
+        sigma = torch.from_numpy(wl.get("density", synth.uniform_density(m.n, 1000))).to(device)
+    q = (sigma * w).contiguous()
+    return wl, m, xyz, w, nrm, q
+
+
+def oracle_sample(wl, m, q_host, n_sample, seed=12345):
+    """Time the FP64 oracle on a seeded sample of targets (the CPU baseline)."""
+    import oracle
+    from oracle.quadrature import quadrature_points
+    xyz, w, nrm = quadrature_points(m.tri, m.sph)
+    idx = np.sort(np.random.default_rng(seed).choice(m.n, size=min(n_sample, m.n), replace=False))
+    kern = wl["kernel"]
+    t0 = time.perf_counter()
+    ref = oracle.direct(kern, xyz, xyz, q_host, src_nrm=nrm if kern == "dl" else None,
+                        trg_nrm=nrm if kern == "adl" else None, idx=idx)
+    dt = time.perf_counter() - t0
+    return idx, ref, dt, oracle.max_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    wl = synth.workload(args.workload)
+    m = wl["mesh"]
+    from oracle.quadrature import quadrature_points
+    xyz, w, nrm = quadrature_points(m.tri, m.sph)
+    if wl["kernel"] == "dl":
+        M = wl["magnetization"]
+        q = (nrm[0] * M[0] + nrm[1] * M[1] + nrm[2] * M[2]) * w
+    else:
+        q = wl.get("density", synth.uniform_density(m.n, 1000)) * w
+    times = []
+    for s in range(args.warmup + args.steps):
+        _, _, dt, cores = oracle_sample(wl, m, q, args.ref_sample, seed=100 + s)
+        if s >= args.warmup:
+            times.append(dt)
+    per_step = float(np.mean(times))
+    value = args.ref_sample / per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "n_targets": m.n,
+                                            "sample_targets_per_step": args.ref_sample},
+            "cpu_baseline": {"value": value, "unit": "targets/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d seeded targets x all %d sources per step" % (args.ref_sample, m.n)},
+            "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_kifmm(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    from paper_1605_01715_gb300 import Plan, Tree
+    wl, m, xyz, w, nrm, q = make_inputs(args.workload, device)
+    p = args.p or wl["p"]
+    max_leaf = args.max_leaf or wl["max_leaf"]
+    t0 = time.perf_counter()
+    tree = Tree(xyz, max_leaf=max_leaf)
+    torch.cuda.synchronize()
+    t_tree = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plan = Plan(tree, kernel=wl["kernel"], p=p, precision=args.precision, src_nrm=nrm, trg_nrm=nrm)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    n = m.n
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.matvec(q, out)
+    torch.cuda.synchronize()
+
+    # device-timed region (per-phase CUDA events recorded by the library on the same stream)
+    plan.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.matvec(q, out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    phases = plan.profile(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_t = torch.tensor([ms], device=device)
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = n * ws / (ms * 1e-3)
+
+    # end to end through the public API with host buffers
+    q_host = q.cpu().pin_memory()
+    out_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    q_dev = torch.empty_like(q)
+    for _ in range(2):
+        q_dev.copy_(q_host, non_blocking=True)
+        plan.matvec(q_dev, out)
+        out_host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        q_dev.copy_(q_host, non_blocking=True)
+        plan.matvec(q_dev, out)
+        out_host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    ms_e = torch.tensor([ms_e2e], device=device)
+    if ws > 1:
+        torch.distributed.all_reduce(ms_e, op=torch.distributed.ReduceOp.MAX)
+    ms_e2e = float(ms_e.item())
+
+    st = plan.stats()
+    tst = tree.stats()
+    line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_targets": n, "kernel": wl["kernel"], "p": p,
+                       "q_points": st["q_points"], "max_leaf": max_leaf, "precision": args.precision,
+                       "pinv_cutoff": st["pinv_cutoff"], "parallelism": "replica" if ws > 1 else "single",
+                       "l2": "no flush: per-step working set %.2f GB > 129 MB L2" % (st["device_bytes"] / 1e9),
+                       "tree": {k: tst[k] for k in ("n_boxes", "n_leaves", "n_levels", "n_v", "n_w", "n_x",
+                                                     "p2p_pairs")},
+                       "tree_build_ms": t_tree * 1e3, "setup_ms": t_setup * 1e3},
+            "phases_ms": phases,
+            "e2e": {"value": n * ws / (ms_e2e * 1e-3), "unit": "targets/s", "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": st["launches_per_matvec"] * args.steps,
+            "clocks": clk.summary()}
+    line["roofline"] = roofline(phases, st, tst, args)
+
+    if rank == 0 and not args.no_cpu_baseline:
+        idx, ref, dt, cores = oracle_sample(wl, m, q.cpu().numpy(), args.cpu_sample)
+        got = out.cpu().numpy()[idx]
+        line["cpu_baseline"] = {"value": idx.size / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
+                                "sample": "%d seeded targets x all %d sources (FP64 direct sum)" % (idx.size, n)}
+        line["rel_err_sampled"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def roofline(phases, st, tst, args):
+    """Roofline of the dominant phase, from algorithmic work per launch and live event times."""
+    pk, src = _peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0) * 1e6
+    fp32_peak = 152 * 128 * 2 * sm_max / 1e12       # TFLOP/s, CUDA-core FMA at max SM clock
+    fp64_peak = 1.25                                 # TFLOP/s nominal
+    Q = st["q_points"]
+    items = {k: v for k, v in phases.items() if k != "total"}
+    dom = max(items, key=items.get)
+    t = items[dom] * 1e-3
+    mixed = args.precision == "mixed"
+    if dom in ("m2l_x", "u2u", "l2l"):
+        pairs = {"m2l_x": st["m2l_pairs"], "u2u": st["u2u_pairs"], "l2l": st["l2l_pairs"]}[dom]
+        flops = 2.0 * Q * Q * pairs
+        peak = fp32_peak if mixed else fp64_peak
+        return {"kernel": "k_pair_gemm (%s)" % dom, "bound": "alu", "achieved": flops / t / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
+                "peak_source": "152 SM x 128 FP32 lanes x 2 x %.0f MHz" % (sm_max / 1e6) if mixed else "FP64 nominal"}
+    if dom == "p2p":
+        flops = 20.0 * tst["p2p_pairs"]            # ~20 FP32 ops per pair (FMA counted as 2)
+        peak = fp32_peak if mixed else fp64_peak
+        return {"kernel": "k_p2p", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None}
+    if dom == "d2t":
+        nbytes = (4 if mixed else 8) * (st["q_points"] + 8) * tst["n_src"]
+        return {"kernel": "k_d2t", "bound": "hbm", "achieved": nbytes / t / 1e9, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": nbytes / t / 1e9 / pk["hbm_gbs"], "traffic": None, "peak_source": src}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="kifmm", choices=["kifmm", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--max-leaf", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=8192)
+    ap.add_argument("--ref-sample", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_kifmm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,234 @@
+/*
+ * kifmm.h -- C ABI of the GB300 kernel-independent fast multipole library for the
+ * Laplace boundary sums of magnetostatic FEM-BEM and dielectric-polarization BEM
+ * solvers (Jiang et al., "An O(N) and parallel approach to integral problems by a
+ * kernel-independent fast multipole method").
+ *
+ * What is computed (raw sums, no 1/(4 pi)):
+ *   f_i = sum_j K(r_i, r_j) q_j                                    Sec. II.A, Eq. sum_fmm
+ *   KIFMM_KERNEL_SL  : K = 1/|r_i - r_j|                             the 1/r kernel (Sec. III.A.1)
+ *   KIFMM_KERNEL_DL  : K = n_j.(r_i - r_j)/|r_i - r_j|^3             Eq. kernel (source normal)
+ *   KIFMM_KERNEL_ADL : K = n_i.(r_i - r_j)/|r_i - r_j|^3             Eq. kernel_pol . n_i (Eq. Ax)
+ * with q_j = sigma_j w_j (density times quadrature weight) and the pair skipped
+ * when |r_i - r_j| < 1e-5 (the tolerance radius of Sec. III.A.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Device pointers are CUDA device memory of the current device, owned by the
+ *    caller, never retained after the call returns (geometry is copied into the
+ *    tree / plan).  Host pointers are marked "host".
+ *  - Coordinates and normals are structure-of-arrays of length 3n: x[0..n), then
+ *    y[0..n), then z[0..n), FP64.
+ *  - Outputs are in the caller's (input) point order.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *    Set-up calls and kifmm_bie_solve synchronize the stream before returning;
+ *    kifmm_fmm_matvec, kifmm_quadrature_points and kifmm_polarization_rhs are
+ *    asynchronous.
+ *  - Every function returns KIFMM_OK (0) or a negative status; no exception
+ *    crosses the ABI.  kifmm_last_error() returns a thread-local message for the
+ *    last failure on the calling thread.
+ *  - Handles are not thread-safe: one thread (and one stream) at a time per handle.
+ */
+#ifndef KIFMM_H
+#define KIFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KIFMM_OK                 0
+#define KIFMM_ERR_INVALID_ARG   (-1)  /* bad pointer, size, enum or handle            */
+#define KIFMM_ERR_OOM           (-2)  /* device or host allocation failed               */
+#define KIFMM_ERR_CUDA          (-3)  /* a CUDA call or kernel launch failed            */
+#define KIFMM_ERR_NOT_CONVERGED (-4)  /* GMRES hit max_iter; x holds the last iterate   */
+#define KIFMM_ERR_TIMEOUT       (-5)  /* a bounded device-side wait gave up             */
+#define KIFMM_ERR_BREAKDOWN     (-6)  /* GMRES breakdown (zero or non-finite norm)      */
+#define KIFMM_ERR_UNSUPPORTED   (-7)  /* a valid request this build does not implement  */
+
+#define KIFMM_KERNEL_SL  0
+#define KIFMM_KERNEL_DL  1
+#define KIFMM_KERNEL_ADL 2
+
+#define KIFMM_PREC_FP64  0   /* every step in FP64 (the plain form)                        */
+#define KIFMM_PREC_MIXED 1   /* FP32 near field and translations, FP64 set-up and output   */
+
+typedef struct kifmm_tree_s* kifmm_tree;
+typedef struct kifmm_plan_s* kifmm_plan;
+
+/* Last error message of the calling thread ("" if none).  Owned by the library. */
+const char* kifmm_last_error(void);
+
+/* Library version string, e.g. "kifmm 0.1 sm_103a". */
+const char* kifmm_version(void);
+
+/*
+ * One-point quadrature on a triangle soup (Sec. III, electrostatic implementation):
+ * the point is the triangle centroid; the weight is the spherical-triangle area
+ * R^2 E (E the spherical excess) when the triangle lies on a sphere, else the flat
+ * area; the normal is radial, (c - C)/|c - C|, on a sphere, else the unit facet
+ * normal from the vertex winding.
+ *   tri  device, n_tri*9 FP64: per triangle the 3 vertices (x,y,z) in order.
+ *   sph  device, n_tri*4 FP64: sphere centre (x,y,z) and radius; radius <= 0 = flat.
+ *   xyz, nrm  device, 3*n_tri FP64 SoA (outputs);  w  device, n_tri FP64 (output).
+ * Errors: INVALID_ARG for NULL pointers or n_tri < 0; CUDA on a launch failure.
+ */
+int kifmm_quadrature_points(const double* tri, const double* sph, int64_t n_tri,
+                            double* xyz, double* w, double* nrm, void* stream);
+
+/*
+ * Adaptive octree over sources (and targets) -- the target-source model of
+ * Sec. III.A.1, with the octree depth set by a leaf capacity (the octree-height
+ * knob of Sec. III.A.1 and IV.A).  Points are sorted by 63-bit Morton key (21 bits
+ * per axis) in the smallest cube enclosing all points (enlarged by 1e-6 relative);
+ * a box with more than max_leaf sources or targets is split, to depth <= 20.
+ * Interaction lists U, V, W, X (Ying, Biros & Zorin 2004) are built on the device.
+ *   src_xyz  device, 3*n_src FP64 SoA.      n_src >= 1.
+ *   trg_xyz  device, 3*n_trg FP64 SoA, or NULL: targets are the sources.
+ *   max_leaf 1..1024.
+ *   out      host, receives the handle (NULL on failure).
+ * Errors: INVALID_ARG (sizes, NULL, non-finite coordinates), OOM, CUDA.
+ */
+int kifmm_tree_build(const double* src_xyz, int64_t n_src,
+                     const double* trg_xyz, int64_t n_trg,
+                     int max_leaf, void* stream, kifmm_tree* out);
+
+typedef struct {
+    int64_t n_src, n_trg;
+    int32_t n_boxes, n_leaves, n_levels, max_leaf;
+    int64_t n_u, n_v, n_w, n_x;       /* total interaction-list entries           */
+    int64_t p2p_pairs;                /* sum over target leaves of n_trg * U/W sources */
+    double  root_center[3], root_half;
+} kifmm_tree_stats;
+
+/* Fill *stats (host).  Errors: INVALID_ARG. */
+int kifmm_tree_get_stats(kifmm_tree tree, kifmm_tree_stats* stats);
+
+/*
+ * Copy the tree to host arrays (for inspection and tests).  Any pointer may be NULL.
+ *   box_level[n_boxes], box_coord[3*n_boxes] (integer cell coordinates at the box's
+ *   level, x y z per box), box_parent[n_boxes] (-1 for the root), box_leaf[n_boxes]
+ *   (1 = leaf), box_range[4*n_boxes] (source begin, source end, target begin, target
+ *   end in sorted order), src_perm[n_src], trg_perm[n_trg] (sorted position -> input
+ *   index).  Boxes are ordered by level, then by Morton key.
+ */
+int kifmm_tree_export(kifmm_tree tree, int32_t* box_level, int32_t* box_coord,
+                      int32_t* box_parent, int32_t* box_leaf, int64_t* box_range,
+                      int64_t* src_perm, int64_t* trg_perm);
+
+#define KIFMM_LIST_U 0
+#define KIFMM_LIST_V 1
+#define KIFMM_LIST_W 2
+#define KIFMM_LIST_X 3
+/*
+ * Copy one interaction list in CSR form: offsets (host, n_boxes+1) and idx (host,
+ * offsets[n_boxes] entries, source box ids).  Either pointer may be NULL; call with
+ * idx == NULL first to size it from offsets[n_boxes].
+ */
+int kifmm_tree_export_list(kifmm_tree tree, int which, int64_t* offsets, int32_t* idx);
+
+/* Release a tree.  Plans built on it must be destroyed first.  NULL is a no-op. */
+int kifmm_tree_destroy(kifmm_tree tree);
+
+/*
+ * Plan: translation operators and per-leaf evaluation matrices for one kernel,
+ * order and precision on a tree.  KIFMM operators (Ying, Biros & Zorin 2004) with
+ * surfaces of p points per cube edge (Q = 6(p-1)^2 + 2 points), equivalent surfaces
+ * at 1.05 and check surfaces at 2.95 box half-widths; the check-to-equivalent
+ * pseudo-inverses come from an FP64 SVD truncated at pinv_cutoff * sigma_max and are
+ * folded into every operator, so the matvec only moves check potentials.
+ * The double-layer normal is applied at the source-to-check step (Sec. III.A.1,
+ * Eq. p2m, the "second method"); the adjoint target normal at evaluation.
+ *   kernel      KIFMM_KERNEL_SL / DL / ADL.
+ *   p           2..16.
+ *   precision   KIFMM_PREC_FP64 or KIFMM_PREC_MIXED.
+ *   pinv_cutoff > 0 and < 1, or 0 for the default (1e-8 mixed, 1e-9 FP64).
+ *   src_nrm     device 3*n_src SoA; required for DL, else ignored (may be NULL).
+ *   trg_nrm     device 3*n_trg SoA; required for ADL, else ignored (may be NULL).
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int kifmm_fmm_setup(kifmm_tree tree, int kernel, int p, int precision, double pinv_cutoff,
+                    const double* src_nrm, const double* trg_nrm,
+                    void* stream, kifmm_plan* out);
+
+/*
+ * f = K q for all targets (see the top of this file).
+ *   q    device, n_src FP64 (density times weight), input order.
+ *   out  device, n_trg FP64, input order (overwritten).
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+int kifmm_fmm_matvec(kifmm_plan plan, const double* q, double* out, void* stream);
+
+typedef struct {
+    int32_t kernel, p, q_points, precision;
+    double  pinv_cutoff;
+    int64_t device_bytes;             /* device memory held by the plan      */
+    int64_t m2l_pairs, u2u_pairs, l2l_pairs, s2u_leaves, x_pairs;
+    int32_t launches_per_matvec;      /* kernels one kifmm_fmm_matvec enqueues */
+} kifmm_plan_stats;
+
+int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);
+
+/*
+ * Per-phase device times (milliseconds).  While enabled, every matvec records CUDA
+ * events between its phases on its stream (no host synchronization).  A call with
+ * phases != NULL (host, >= 8 doubles) waits for the recorded events and returns the
+ * mean per matvec since the previous read: {gather, s2u, u2u, m2l+x, l2l, d2t, p2p,
+ * total}; then recording is switched on (enable != 0) or off.
+ */
+int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases);
+
+/* Release a plan.  NULL is a no-op. */
+int kifmm_plan_destroy(kifmm_plan plan);
+
+/*
+ * Right-hand side of the polarization system for a uniform applied field and no
+ * free charge: b_j = -(eps_out - eps_j) E0 . n_j   (Eq. rhs with sigma_f = 0 and the
+ * free-charge field replaced by E0).
+ *   nrm device 3n SoA, eps_in device n, b device n (output).
+ */
+int kifmm_polarization_rhs(const double* nrm, const double* eps_in, double eps_out,
+                           const double e0[3], int64_t n, double* b, void* stream);
+
+/*
+ * Solve the dielectric polarization system A sigma = b (Sec. II.C, Eqs. Ax, Eb,
+ * pol_discret) matrix-free with restarted GMRES(restart) in FP64 (Sec. III), on a
+ * plan built with KIFMM_KERNEL_ADL on targets = sources:
+ *   (A s)_j = ebar_j s_j + deps_j (1/4pi) [ ADL(s * area)_j + c_j s_j ],
+ *   ebar_j = (eps_j + eps_out)/2,  deps_j = eps_out - eps_j,  c_j = H_j sqrt(pi a_j)
+ * (the self-patch correction: principal-value normal field of a disc of area a_j
+ * on a surface of mean curvature H_j).  Krylov basis, orthogonalization (classical
+ * Gram-Schmidt applied twice) and residuals are FP64 on the device; x0 is the
+ * content of x on entry.  Stops when the GMRES residual estimate falls to
+ * tol * ||b|| and returns the true relative residual ||b - A x||/||b|| in *rel_res.
+ *   area, eps_in, curv, b: device, n FP64 (input order);  x device n (in/out).
+ *   iters, rel_res: host (may be NULL).
+ * Errors: INVALID_ARG, OOM, CUDA, NOT_CONVERGED (x = last iterate), BREAKDOWN.
+ */
+int kifmm_bie_solve(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
+                    const double* curv, const double* b, double* x,
+                    double tol, int restart, int max_iter,
+                    int* iters, double* rel_res, void* stream);
+
+/*
+ * The polarization operator itself, y = A x (same definition as kifmm_bie_solve).
+ * Asynchronous.
+ */
+int kifmm_bie_apply(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
+                    const double* curv, const double* x, double* y, void* stream);
+
+/*
+ * Demagnetizing-field boundary potential of the Fredkin-Koehler split (Sec. II.B,
+ * Eq. fk_integral_discrete):
+ *   phi2_i = (1/4pi) sum_j n_j.(r_i - r_j)/|r_i - r_j|^3 phi1_j w_j + (Omega_i/4pi - 1) phi1_i
+ * on a plan built with KIFMM_KERNEL_DL on targets = sources.
+ *   phi1, w, omega (solid angle), phi2 (output): device, n FP64.  Asynchronous.
+ */
+int kifmm_demag_phi2(kifmm_plan plan, const double* phi1, const double* w,
+                     const double* omega, double* phi2, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KIFMM_H */

@@ -1,0 +1,292 @@
+"""Thin ctypes binding of include/kifmm.h.
+
+Every function here only marshals arguments: torch CUDA tensors become device
+pointers, the current torch stream becomes the ``stream`` argument, and a non-zero
+status raises ``KifmmError``.  All computation happens in libkifmm.so.  There is no
+fallback: if the library is missing or no CUDA device is present, calls fail.
+
+The functions keep the C names; ``Tree`` and ``Plan`` own the handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkifmm.so")
+
+KERNELS = {"sl": 0, "dl": 1, "adl": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+LISTS = {"U": 0, "V": 1, "W": 2, "X": 3}
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED",
+          -5: "TIMEOUT", -6: "BREAKDOWN", -7: "UNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class KifmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+        self.status = STATUS.get(code, "?")
+
+
+class TreeStats(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int64), ("n_trg", ctypes.c_int64),
+                ("n_boxes", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("max_leaf", ctypes.c_int32),
+                ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64), ("n_w", ctypes.c_int64),
+                ("n_x", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("root_center", ctypes.c_double * 3), ("root_half", ctypes.c_double)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("p", ctypes.c_int32), ("q_points", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("pinv_cutoff", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64),
+                ("u2u_pairs", ctypes.c_int64), ("l2l_pairs", ctypes.c_int64),
+                ("s2u_leaves", ctypes.c_int64), ("x_pairs", ctypes.c_int64),
+                ("launches_per_matvec", ctypes.c_int32)]
+
+
+def _as_dict(st):
+    out = {}
+    for k, _ in st._fields_:
+        v = getattr(st, k)
+        out[k] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "kifmm_last_error": ([], ctypes.c_char_p),
+    "kifmm_version": ([], ctypes.c_char_p),
+    "kifmm_quadrature_points": ([_P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "kifmm_tree_build": ([_P, _I64, _P, _I64, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "kifmm_tree_get_stats": ([_P, ctypes.POINTER(TreeStats)], ctypes.c_int),
+    "kifmm_tree_export": ([_P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "kifmm_tree_export_list": ([_P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "kifmm_tree_destroy": ([_P], ctypes.c_int),
+    "kifmm_fmm_setup": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
+                         ctypes.POINTER(_P)], ctypes.c_int),
+    "kifmm_fmm_matvec": ([_P, _P, _P, _P], ctypes.c_int),
+    "kifmm_plan_get_stats": ([_P, ctypes.POINTER(PlanStats)], ctypes.c_int),
+    "kifmm_plan_profile": ([_P, ctypes.c_int, _P], ctypes.c_int),
+    "kifmm_plan_destroy": ([_P], ctypes.c_int),
+    "kifmm_polarization_rhs": ([_P, _P, ctypes.c_double, _P, _I64, _P, _P], ctypes.c_int),
+    "kifmm_bie_solve": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_double, ctypes.c_int,
+                         ctypes.c_int, _P, _P, _P], ctypes.c_int),
+    "kifmm_bie_apply": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, _P], ctypes.c_int),
+    "kifmm_demag_phi2": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+}
+
+
+def lib():
+    """Load libkifmm.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libkifmm.so not built: run `python -c 'import __graft_entry__ as g; "
+                                  "g.build()'` (no CPU fallback exists)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc):
+    if rc != 0:
+        raise KifmmError(rc, lib().kifmm_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t, n=None, name="tensor"):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    if n is not None and t.numel() != n:
+        raise ValueError("%s must have %d elements, has %d" % (name, n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kifmm_version() -> str:
+    return lib().kifmm_version().decode()
+
+
+def kifmm_quadrature_points(tri, sph, stream=None):
+    """tri (T,3,3) and sph (T,4) float64 CUDA -> xyz (3,T), w (T,), nrm (3,T)."""
+    n = tri.shape[0]
+    xyz = torch.empty((3, n), dtype=torch.float64, device=tri.device)
+    w = torch.empty(n, dtype=torch.float64, device=tri.device)
+    nrm = torch.empty((3, n), dtype=torch.float64, device=tri.device)
+    _check(lib().kifmm_quadrature_points(_dev(tri, 9 * n, "tri"), _dev(sph, 4 * n, "sph"), n,
+                                         _dev(xyz), _dev(w), _dev(nrm), _stream(stream)))
+    return xyz, w, nrm
+
+
+class Tree:
+    """Owns a kifmm_tree handle (kifmm_tree_build / kifmm_tree_destroy)."""
+
+    def __init__(self, src_xyz, trg_xyz=None, max_leaf=64, stream=None):
+        h = ctypes.c_void_p()
+        ns = src_xyz.shape[-1]
+        nt = trg_xyz.shape[-1] if trg_xyz is not None else 0
+        _check(lib().kifmm_tree_build(_dev(src_xyz, 3 * ns, "src_xyz"), ns,
+                                      _dev(trg_xyz, 3 * nt, "trg_xyz"), nt, int(max_leaf),
+                                      _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self._lib = lib()
+
+    def stats(self):
+        st = TreeStats()
+        _check(lib().kifmm_tree_get_stats(self.handle, ctypes.byref(st)))
+        return _as_dict(st)
+
+    def export(self):
+        import numpy as np
+        st = self.stats()
+        nb = st["n_boxes"]
+        lvl = np.empty(nb, np.int32)
+        coord = np.empty(3 * nb, np.int32)
+        parent = np.empty(nb, np.int32)
+        leaf = np.empty(nb, np.int32)
+        rng = np.empty(4 * nb, np.int64)
+        sperm = np.empty(st["n_src"], np.int64)
+        tperm = np.empty(st["n_trg"], np.int64)
+        _check(lib().kifmm_tree_export(self.handle, lvl.ctypes.data, coord.ctypes.data, parent.ctypes.data,
+                                       leaf.ctypes.data, rng.ctypes.data, sperm.ctypes.data,
+                                       tperm.ctypes.data))
+        return dict(level=lvl, coord=coord.reshape(nb, 3), parent=parent, leaf=leaf.astype(bool),
+                    range=rng.reshape(nb, 4), src_perm=sperm, trg_perm=tperm)
+
+    def list(self, which):
+        import numpy as np
+        nb = self.stats()["n_boxes"]
+        off = np.empty(nb + 1, np.int64)
+        _check(lib().kifmm_tree_export_list(self.handle, LISTS[which], off.ctypes.data, None))
+        idx = np.empty(max(1, int(off[-1])), np.int32)
+        _check(lib().kifmm_tree_export_list(self.handle, LISTS[which], None, idx.ctypes.data))
+        return off, idx[: int(off[-1])]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.kifmm_tree_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Owns a kifmm_plan handle (kifmm_fmm_setup / kifmm_plan_destroy)."""
+
+    def __init__(self, tree: Tree, kernel="sl", p=6, precision="fp64", pinv_cutoff=0.0,
+                 src_nrm=None, trg_nrm=None, stream=None):
+        h = ctypes.c_void_p()
+        st = tree.stats()
+        _check(lib().kifmm_fmm_setup(tree.handle, KERNELS[kernel], int(p), PRECISIONS[precision],
+                                     float(pinv_cutoff),
+                                     _dev(src_nrm, 3 * st["n_src"], "src_nrm") if kernel == "dl" else None,
+                                     _dev(trg_nrm, 3 * st["n_trg"], "trg_nrm") if kernel == "adl" else None,
+                                     _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.tree = tree  # keep the tree alive
+        self.n_src = st["n_src"]
+        self.n_trg = st["n_trg"]
+        self.kernel = kernel
+        self._lib = lib()
+
+    def matvec(self, q, out=None, stream=None):
+        if out is None:
+            out = torch.empty(self.n_trg, dtype=torch.float64, device=q.device)
+        _check(lib().kifmm_fmm_matvec(self.handle, _dev(q, self.n_src, "q"), _dev(out, self.n_trg, "out"),
+                                      _stream(stream)))
+        return out
+
+    def stats(self):
+        st = PlanStats()
+        _check(lib().kifmm_plan_get_stats(self.handle, ctypes.byref(st)))
+        return _as_dict(st)
+
+    def profile(self, enable=True):
+        ph = (ctypes.c_double * 8)()
+        _check(lib().kifmm_plan_profile(self.handle, int(enable), ph))
+        names = ["gather", "s2u", "u2u", "m2l_x", "l2l", "d2t", "p2p", "total"]
+        return dict(zip(names, list(ph)))
+
+    def bie_apply(self, area, eps_in, eps_out, curv, x, y=None, stream=None):
+        n = self.n_trg
+        if y is None:
+            y = torch.empty(n, dtype=torch.float64, device=x.device)
+        _check(lib().kifmm_bie_apply(self.handle, _dev(area, n, "area"), _dev(eps_in, n, "eps_in"),
+                                     float(eps_out), _dev(curv, n, "curv"), _dev(x, n, "x"), _dev(y, n, "y"),
+                                     _stream(stream)))
+        return y
+
+    def bie_solve(self, area, eps_in, eps_out, curv, b, x=None, tol=1e-6, restart=50, max_iter=1000,
+                  stream=None, raise_on_failure=True):
+        n = self.n_trg
+        if x is None:
+            x = torch.zeros(n, dtype=torch.float64, device=b.device)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0)
+        rc = lib().kifmm_bie_solve(self.handle, _dev(area, n, "area"), _dev(eps_in, n, "eps_in"),
+                                   float(eps_out), _dev(curv, n, "curv"), _dev(b, n, "b"), _dev(x, n, "x"),
+                                   float(tol), int(restart), int(max_iter), ctypes.byref(it), ctypes.byref(rr),
+                                   _stream(stream))
+        if rc != 0 and raise_on_failure:
+            _check(rc)
+        return x, it.value, rr.value, rc
+
+    def demag_phi2(self, phi1, w, omega, out=None, stream=None):
+        n = self.n_trg
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=phi1.device)
+        _check(lib().kifmm_demag_phi2(self.handle, _dev(phi1, n, "phi1"), _dev(w, n, "w"),
+                                      _dev(omega, n, "omega"), _dev(out, n, "out"), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.kifmm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kifmm_polarization_rhs(nrm, eps_in, eps_out, e0, out=None, stream=None):
+    n = eps_in.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=eps_in.device)
+    e = (ctypes.c_double * 3)(*[float(v) for v in e0])
+    _check(lib().kifmm_polarization_rhs(_dev(nrm, 3 * n, "nrm"), _dev(eps_in, n, "eps_in"), float(eps_out), e, n,
+                                        _dev(out, n, "b"), _stream(stream)))
+    return out

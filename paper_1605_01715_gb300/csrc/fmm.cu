@@ -1,0 +1,866 @@
+// KIFMM plan set-up and the matvec f = K q (Sec. II.A, Eq. sum_fmm) on the device.
+//
+// One matvec, all in check-potential space (see operators.cu):
+//   gather  q into Morton order (DL: q n_j, the source normal applied at the
+//           source-to-check step, Sec. III.A.1 Eq. p2m -- the paper's second method)
+//   S2U     leaf up-check potentials from the leaf's sources
+//   U2U     parent up-check += M2M'_oct child up-check, level by level upward
+//   X       down-check potentials from the sources of X-list leaves
+//   M2L     down-check += M2L'_offset up-check of each V-list box
+//   L2L     child down-check += L2L'_oct parent down-check, level by level downward
+//   D2T     far-field value at each target = its precomputed row . leaf down-check
+//   P2P     near field over U- and W-list sources, added, scattered to input order
+// Near-singular pairs (|r_i - r_j| < 1e-5) contribute nothing (Sec. III.A.1).
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "common.cuh"
+#include "operators.cuh"
+#include "plan.cuh"
+
+namespace kifmm {
+
+namespace {
+
+template <typename Real> struct RT;
+template <> struct RT<float> {
+    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+};
+template <> struct RT<double> {
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+};
+
+// ---------------------------------------------------------------- gather
+template <typename Real>
+__global__ void k_gather_q(const double* __restrict__ q, const int64_t* __restrict__ perm, int64_t n,
+                           const double* __restrict__ snrm, Real* __restrict__ qs) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = q[perm[i]];
+    if (snrm) {  // dipole strengths q n_j, SoA
+        qs[i] = (Real)(v * snrm[i]);
+        qs[n + i] = (Real)(v * snrm[n + i]);
+        qs[2 * n + i] = (Real)(v * snrm[2 * n + i]);
+    } else {
+        qs[i] = (Real)v;
+    }
+}
+
+// ---------------------------------------------------------------- sources -> surface (S2U, X list)
+// One block per box; threads own surface points; sources of the CSR boxes staged in
+// shared memory relative to the box centre.  DIPOLE: n_j.(x - y)/|x - y|^3 q_j, else q_j/|x - y|.
+constexpr int kSurfThreads = 128;
+constexpr int kSurfPer = 8;  // Q <= 1024
+
+template <typename Real, bool DIPOLE>
+__global__ void __launch_bounds__(kSurfThreads)
+k_src2surf(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx,
+           double radius, const int* __restrict__ lvl, const double* __restrict__ ctr, double root_h,
+           const int64_t* __restrict__ rng, const double* __restrict__ sxyz, int64_t ns,
+           const Real* __restrict__ qs, const Real* __restrict__ surf, int Q, int Qp,
+           Real* __restrict__ outbuf) {
+    __shared__ Real sy[4][kSurfThreads];
+    __shared__ Real sq[3][kSurfThreads];
+    int b = boxes[blockIdx.x];
+    double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
+    Real rf = (Real)(radius * ldexp(root_h, -lvl[b]));
+    Real px[kSurfPer], py[kSurfPer], pz[kSurfPer], acc[kSurfPer];
+#pragma unroll
+    for (int i = 0; i < kSurfPer; ++i) {
+        int k = threadIdx.x + i * kSurfThreads;
+        int kk = k < Q ? k : 0;
+        px[i] = rf * surf[3 * kk];
+        py[i] = rf * surf[3 * kk + 1];
+        pz[i] = rf * surf[3 * kk + 2];
+        acc[i] = 0;
+    }
+    const Real d2 = (Real)(kDelta * kDelta);
+    for (int e = off[blockIdx.x]; e < off[blockIdx.x + 1]; ++e) {
+        int a = idx[e];
+        int64_t sb = rng[4 * a], se = rng[4 * a + 1];
+        for (int64_t j0 = sb; j0 < se; j0 += kSurfThreads) {
+            int64_t j = j0 + threadIdx.x;
+            if (j < se) {
+                sy[0][threadIdx.x] = (Real)(sxyz[j] - cx);
+                sy[1][threadIdx.x] = (Real)(sxyz[ns + j] - cy);
+                sy[2][threadIdx.x] = (Real)(sxyz[2 * ns + j] - cz);
+                if (DIPOLE) {
+                    sq[0][threadIdx.x] = qs[j];
+                    sq[1][threadIdx.x] = qs[ns + j];
+                    sq[2][threadIdx.x] = qs[2 * ns + j];
+                } else {
+                    sq[0][threadIdx.x] = qs[j];
+                }
+            }
+            __syncthreads();
+            int cnt = (int)((se - j0) < (int64_t)kSurfThreads ? (se - j0) : (int64_t)kSurfThreads);
+            for (int jj = 0; jj < cnt; ++jj) {
+                Real yx = sy[0][jj], yy = sy[1][jj], yz = sy[2][jj];
+#pragma unroll
+                for (int i = 0; i < kSurfPer; ++i) {
+                    if (i * kSurfThreads >= Q) break;
+                    Real dx = px[i] - yx, dy = py[i] - yy, dz = pz[i] - yz;
+                    Real r2 = dx * dx + dy * dy + dz * dz;
+                    Real inv = RT<Real>::rsq(r2);
+                    Real v;
+                    if (DIPOLE) v = (sq[0][jj] * dx + sq[1][jj] * dy + sq[2][jj] * dz) * inv * inv * inv;
+                    else v = sq[0][jj] * inv;
+                    acc[i] += (r2 >= d2) ? v : (Real)0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kSurfPer; ++i) {
+        int k = threadIdx.x + i * kSurfThreads;
+        if (k < Q) outbuf[(size_t)b * Qp + k] += acc[i];
+    }
+}
+
+// ---------------------------------------------------------------- grouped pair GEMM (U2U, M2L, L2L)
+// Every tile shares one operator: out[pout[j]] += Op . in[pin[j]] for its pairs.
+// CUDA-core SGEMM/DGEMM blocking: 64 rows x 64 pairs per pass, 4x4 per thread.
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_pair_gemm(const Real* __restrict__ ops, int Q, int Qp, const int4* __restrict__ tiles,
+            const int* __restrict__ pin, const int* __restrict__ pout, const Real* __restrict__ in,
+            Real* __restrict__ out) {
+    constexpr int BM = 64, BN = kPairTile, BK = 16;
+    __shared__ Real As[BK][BM + 4];
+    __shared__ Real Bs[BK][BN + 4];
+    __shared__ int s_in[BN], s_out[BN];
+    int4 t = tiles[blockIdx.x];
+    const Real* Op = ops + (size_t)t.x * Qp * Qp;
+    int cnt = t.z;
+    for (int j = threadIdx.x; j < BN; j += blockDim.x) {
+        s_in[j] = j < cnt ? pin[t.y + j] : -1;
+        s_out[j] = j < cnt ? pout[t.y + j] : -1;
+    }
+    __syncthreads();
+    int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    for (int row0 = 0; row0 < Q; row0 += BM) {
+        Real acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+        for (int k0 = 0; k0 < Qp; k0 += BK) {
+            for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
+                int r = e / BK, kk = e % BK;
+                int row = row0 + r;
+                As[kk][r] = row < Qp ? Op[(size_t)row * Qp + k0 + kk] : (Real)0;
+            }
+            for (int e = threadIdx.x; e < BN * BK; e += blockDim.x) {
+                int j = e / BK, kk = e % BK;
+                int bi = s_in[j];
+                Bs[kk][j] = bi >= 0 ? in[(size_t)bi * Qp + k0 + kk] : (Real)0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                Real a[4], bv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int row = row0 + ty * 4 + i;
+            if (row >= Q) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int ob = s_out[tx * 4 + j];
+                if (ob >= 0) atomicAdd(&out[(size_t)ob * Qp + row], acc[i][j]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- mean removal (ADL)
+// The adjoint double layer needs only the gradient of the far field.  A constant
+// potential has none, so each box's down-check potential is shifted to zero mean
+// before it is passed on; otherwise the large constant carried down from coarse
+// levels would be stored in FP32 and its rounding amplified by 2^level when the
+// leaf rows differentiate it.
+template <typename Real>
+__global__ void __launch_bounds__(128) k_center(int box0, int Q, int Qp, Real* __restrict__ d) {
+    __shared__ double red[128];
+    Real* v = d + (size_t)(box0 + blockIdx.x) * Qp;
+    double s = 0;
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) s += (double)v[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    Real mean = (Real)(red[0] / Q);
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) v[k] -= mean;
+}
+
+// ---------------------------------------------------------------- D2T
+// res[t] = T[t] . d[leaf(t)]: one block per target leaf, one warp per target row.
+template <typename Real>
+__global__ void __launch_bounds__(128)
+k_d2t(const int* __restrict__ leaves, const int64_t* __restrict__ rng, const Real* __restrict__ T,
+      const Real* __restrict__ d, int Qp, Real* __restrict__ res) {
+    extern __shared__ unsigned char smem_raw[];
+    Real* ds = reinterpret_cast<Real*>(smem_raw);
+    int b = leaves[blockIdx.x];
+    for (int k = threadIdx.x; k < Qp; k += blockDim.x) ds[k] = d[(size_t)b * Qp + k];
+    __syncthreads();
+    int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int64_t t = tb + warp; t < te; t += blockDim.x / 32) {
+        const Real* row = T + (size_t)t * Qp;
+        Real s = 0;
+        for (int k = lane; k < Qp; k += 32) s += row[k] * ds[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) res[t] = s;
+    }
+}
+
+// ---------------------------------------------------------------- P2P (U and W lists) + scatter
+// One block per target leaf, one thread per target; source boxes staged in shared
+// memory relative to the target leaf's centre.
+// KIND 0: q/r   1: (q n_j).(x - y)/r^3   2: q n_i.(x - y)/r^3
+template <typename Real, int KIND>
+__global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ off, const int* __restrict__ idx,
+                      const int64_t* __restrict__ rng, const double* __restrict__ ctr,
+                      const double* __restrict__ sxyz, int64_t ns, const double* __restrict__ txyz,
+                      int64_t nt, const Real* __restrict__ qs, const Real* __restrict__ tnrm,
+                      const Real* __restrict__ res, const int64_t* __restrict__ tperm,
+                      double* __restrict__ out) {
+    extern __shared__ unsigned char smem_raw[];
+    Real* sx = reinterpret_cast<Real*>(smem_raw);
+    Real* sy = sx + blockDim.x;
+    Real* sz = sy + blockDim.x;
+    Real* s0 = sz + blockDim.x;
+    Real* s1 = s0 + blockDim.x;
+    Real* s2 = s1 + blockDim.x;
+    int b = leaves[blockIdx.x];
+    double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
+    int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
+    const Real d2 = (Real)(kDelta * kDelta);
+    for (int64_t t0 = tb; t0 < te; t0 += blockDim.x) {
+        int64_t t = t0 + threadIdx.x;
+        bool valid = t < te;
+        int64_t tt = valid ? t : tb;
+        Real xt = (Real)(txyz[tt] - cx), yt = (Real)(txyz[nt + tt] - cy), zt = (Real)(txyz[2 * nt + tt] - cz);
+        Real nx = 0, ny = 0, nz = 0;
+        if (KIND == 2) {
+            nx = tnrm[tt];
+            ny = tnrm[nt + tt];
+            nz = tnrm[2 * nt + tt];
+        }
+        Real acc = 0;
+        for (int e = off[blockIdx.x]; e < off[blockIdx.x + 1]; ++e) {
+            int a = idx[e];
+            int64_t sb = rng[4 * a], se = rng[4 * a + 1];
+            for (int64_t j0 = sb; j0 < se; j0 += blockDim.x) {
+                int64_t j = j0 + threadIdx.x;
+                if (j < se) {
+                    sx[threadIdx.x] = (Real)(sxyz[j] - cx);
+                    sy[threadIdx.x] = (Real)(sxyz[ns + j] - cy);
+                    sz[threadIdx.x] = (Real)(sxyz[2 * ns + j] - cz);
+                    s0[threadIdx.x] = qs[j];
+                    if (KIND == 1) {
+                        s1[threadIdx.x] = qs[ns + j];
+                        s2[threadIdx.x] = qs[2 * ns + j];
+                    }
+                }
+                __syncthreads();
+                int cnt = (int)((se - j0) < (int64_t)blockDim.x ? (se - j0) : (int64_t)blockDim.x);
+                for (int jj = 0; jj < cnt; ++jj) {
+                    Real dx = xt - sx[jj], dy = yt - sy[jj], dz = zt - sz[jj];
+                    Real r2 = dx * dx + dy * dy + dz * dz;
+                    Real inv = RT<Real>::rsq(r2);
+                    Real v;
+                    if (KIND == 0) v = s0[jj] * inv;
+                    else if (KIND == 1) v = (s0[jj] * dx + s1[jj] * dy + s2[jj] * dz) * (inv * inv * inv);
+                    else v = s0[jj] * (nx * dx + ny * dy + nz * dz) * (inv * inv * inv);
+                    acc += (r2 >= d2) ? v : (Real)0;
+                }
+                __syncthreads();
+            }
+        }
+        if (valid) out[tperm[t]] = (double)(acc + res[t]);
+    }
+}
+
+// ---------------------------------------------------------------- set-up kernels
+__global__ void k_gather_nrm(const double* __restrict__ nrm, const int64_t* __restrict__ perm, int64_t n,
+                             double* __restrict__ outd, float* __restrict__ outf) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    for (int d = 0; d < 3; ++d) {
+        double v = nrm[d * n + j];
+        if (outd) outd[d * n + i] = v;
+        if (outf) outf[d * n + i] = (float)v;
+    }
+}
+
+// D2T row descriptors: target position in its leaf's unit frame, its normal, scale.
+__global__ void k_d2t_rows(const int* __restrict__ tleaf_of, int64_t nt, const double* __restrict__ txyz,
+                           const double* __restrict__ tnrm, const int* __restrict__ lvl,
+                           const double* __restrict__ ctr, double root_h, bool adl, double* apts,
+                           double* anrm, double* ascale, int64_t* orow) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int b = tleaf_of[t];
+    double r = ldexp(root_h, -lvl[b]);
+    for (int d = 0; d < 3; ++d) {
+        apts[3 * t + d] = (txyz[d * nt + t] - ctr[3 * b + d]) / r;
+        anrm[3 * t + d] = adl ? tnrm[d * nt + t] : 0.0;
+    }
+    ascale[t] = adl ? 1.0 / r : 1.0;
+    orow[t] = t;
+}
+
+int octant_of(const Tree& T, int b) {
+    return ((T.h_coord[3 * b] & 1) << 2) | ((T.h_coord[3 * b + 1] & 1) << 1) | (T.h_coord[3 * b + 2] & 1);
+}
+
+bool has_src(const Tree& T, int b) { return T.h_rng[4 * b + 1] > T.h_rng[4 * b]; }
+bool has_trg(const Tree& T, int b) { return T.h_rng[4 * b + 3] > T.h_rng[4 * b + 2]; }
+
+// Group (op, in, out) triples by op into tiles of <= kPairTile pairs.
+struct Triple {
+    int op, in, out;
+};
+
+void make_tiles(std::vector<Triple>& tr, std::vector<int4>& tiles, std::vector<int>& pin,
+                std::vector<int>& pout) {
+    std::stable_sort(tr.begin(), tr.end(), [](const Triple& a, const Triple& b) { return a.op < b.op; });
+    size_t base = pin.size();
+    size_t i = 0;
+    while (i < tr.size()) {
+        size_t j = i;
+        while (j < tr.size() && tr[j].op == tr[i].op && j - i < (size_t)kPairTile) ++j;
+        tiles.push_back(make_int4(tr[i].op, (int)(base + i), (int)(j - i), 0));
+        i = j;
+    }
+    for (auto& t : tr) {
+        pin.push_back(t.in);
+        pout.push_back(t.out);
+    }
+}
+
+int upload_tiles(PairTiles& pt, const std::vector<int4>& tiles, const std::vector<int>& pin,
+                 const std::vector<int>& pout, cudaStream_t s) {
+    KF_TRY(pt.tiles.upload(tiles, s));
+    KF_TRY(pt.pin.upload(pin, s));
+    KF_TRY(pt.pout.upload(pout, s));
+    pt.ntiles = (int)tiles.size();
+    pt.npairs = (int64_t)pin.size();
+    return KIFMM_OK;
+}
+
+// Remove the row mean of every column of every operator (FP64), then round.
+// Used for the adjoint double layer, whose targets see only gradients: the
+// constant part of a down-check potential is dropped before it is stored in the
+// working precision, so its rounding is relative to the potential's variation.
+template <typename Real>
+__global__ void k_center_ops(const double* __restrict__ in, int Q, int Qp, bool center, Real* __restrict__ out) {
+    int op = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Qp) return;
+    const double* A = in + (size_t)op * Qp * Qp;
+    Real* O = out + (size_t)op * Qp * Qp;
+    double mean = 0;
+    if (center) {
+        for (int i = 0; i < Q; ++i) mean += A[(size_t)i * Qp + j];
+        mean /= Q;
+    }
+    for (int i = 0; i < Qp; ++i) O[(size_t)i * Qp + j] = i < Q ? (Real)(A[(size_t)i * Qp + j] - mean) : (Real)0;
+}
+
+template <typename Real>
+int build_ops(Plan& P, const HostPinv& h, Real* m2m, Real* m2l, Real* l2l, cudaStream_t s) {
+    DBuf<double> dPu, dPd;
+    KF_TRY(dPu.upload(h.Pu, s));
+    KF_TRY(dPd.upload(h.Pd, s));
+    Real* outs[3] = {m2m, m2l, l2l};
+    const int nops[3] = {8, kNumOffsets, 8};
+    const size_t QQ = (size_t)P.Qp * P.Qp;
+    for (int which = 0; which < 3; ++which) {
+        std::vector<double> apts, ascale, bpts;
+        std::vector<int> bset;
+        std::vector<int64_t> orow;
+        translation_rows(h, which, apts, bset, orow, ascale, bpts, P.Qp);
+        DBuf<double> da, dsc, db, tmp;
+        DBuf<int> dbs;
+        DBuf<int64_t> dor;
+        KF_TRY(da.upload(apts, s));
+        KF_TRY(dsc.upload(ascale, s));
+        KF_TRY(db.upload(bpts, s));
+        KF_TRY(dbs.upload(bset, s));
+        KF_TRY(dor.upload(orow, s));
+        RowSpec rs;
+        rs.nrows = (int)bset.size();
+        rs.apts = da.p;
+        rs.ascale = dsc.p;
+        rs.bset = dbs.p;
+        rs.orow = dor.p;
+        rs.bpts = db.p;
+        // build in FP64, then (ADL: M2L and L2L centred) round to the working precision
+        KF_TRY(tmp.alloc(nops[which] * QQ));
+        KF_CHECK_CUDA(cudaMemsetAsync(tmp.p, 0, tmp.bytes(), s));
+        KF_TRY(build_rows<double>(rs, P.Q, P.Qp, which == 2 ? dPd.p : dPu.p, 0, tmp.p, s));
+        bool center = P.kernel == KIFMM_KERNEL_ADL && which != 0;
+        dim3 grid(div_up(P.Qp, 128), nops[which]);
+        k_center_ops<Real><<<grid, 128, 0, s>>>(tmp.p, P.Q, P.Qp, center, outs[which]);
+        KF_CHECK_LAUNCH();
+        KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    return KIFMM_OK;
+}
+
+template <typename Real>
+int build_d2t(Plan& P, const HostPinv& h, const std::vector<int>& tleaf_of, Real* out, cudaStream_t s) {
+    const Tree& T = P.tree->t;
+    int64_t nt = T.nt;
+    DBuf<int> dleaf;
+    KF_TRY(dleaf.upload(tleaf_of, s));
+    DBuf<double> apts, anrm, ascale, bpts, dPd;
+    DBuf<int64_t> orow;
+    KF_TRY(apts.alloc(3 * nt));
+    KF_TRY(anrm.alloc(3 * nt));
+    KF_TRY(ascale.alloc(nt));
+    KF_TRY(orow.alloc(nt));
+    std::vector<double> hb(3 * (size_t)h.Q);
+    for (size_t i = 0; i < hb.size(); ++i) hb[i] = kDnEquiv * h.surf[i];
+    KF_TRY(bpts.upload(hb, s));
+    KF_TRY(dPd.upload(h.Pd, s));
+    const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
+    bool adl = P.kernel == KIFMM_KERNEL_ADL;
+    k_d2t_rows<<<div_up(nt, 256), 256, 0, s>>>(dleaf.p, nt, txyz, adl ? P.tnrm_d.p : nullptr, T.lvl.p,
+                                               T.ctr.p, T.root_h, adl, apts.p, anrm.p, ascale.p, orow.p);
+    KF_CHECK_LAUNCH();
+    // build in chunks of rows to bound the launch size
+    const int64_t chunk = 1 << 20;
+    for (int64_t r0 = 0; r0 < nt; r0 += chunk) {
+        RowSpec rs;
+        rs.nrows = (int)std::min<int64_t>(chunk, nt - r0);
+        rs.apts = apts.p + 3 * r0;
+        rs.anrm = anrm.p + 3 * r0;
+        rs.ascale = ascale.p + r0;
+        rs.bset = nullptr;
+        rs.orow = orow.p + r0;
+        rs.bpts = bpts.p;
+        KF_TRY(build_rows<Real>(rs, P.Q, P.Qp, dPd.p, adl ? 1 : 0, out, s));
+    }
+    KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    return KIFMM_OK;
+}
+
+int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s) {
+    Tree& T = P.tree->t;
+    const HostPinv& h = host_pinv(P.p, P.cutoff);
+    P.Q = h.Q;
+    P.Qp = (h.Q + 15) / 16 * 16;
+    P.fp64 = P.prec == KIFMM_PREC_FP64;
+    const size_t QQ = (size_t)P.Qp * P.Qp;
+
+    // sorted normals
+    if (P.kernel == KIFMM_KERNEL_DL) {
+        KF_TRY(P.snrm.alloc(3 * T.ns));
+        k_gather_nrm<<<div_up(T.ns, 256), 256, 0, s>>>(src_nrm, T.sperm.p, T.ns, P.snrm.p, nullptr);
+        KF_CHECK_LAUNCH();
+    }
+    if (P.kernel == KIFMM_KERNEL_ADL) {
+        const int64_t* tp = T.same ? T.sperm.p : T.tperm.p;
+        KF_TRY(P.tnrm_d.alloc(3 * T.nt));
+        if (!P.fp64) KF_TRY(P.tnrm_f.alloc(3 * T.nt));
+        k_gather_nrm<<<div_up(T.nt, 256), 256, 0, s>>>(trg_nrm, tp, T.nt, P.tnrm_d.p,
+                                                       P.fp64 ? nullptr : P.tnrm_f.p);
+        KF_CHECK_LAUNCH();
+    }
+
+    // surfaces
+    {
+        std::vector<float> sf(h.surf.begin(), h.surf.end());
+        KF_TRY(P.surf_d.upload(h.surf, s));
+        KF_TRY(P.surf_f.upload(sf, s));
+    }
+
+    // operators
+    if (P.fp64) {
+        KF_TRY(P.m2m_d.alloc(8 * QQ));
+        KF_TRY(P.m2l_d.alloc(kNumOffsets * QQ));
+        KF_TRY(P.l2l_d.alloc(8 * QQ));
+        KF_CHECK_CUDA(cudaMemsetAsync(P.m2m_d.p, 0, P.m2m_d.bytes(), s));
+        KF_CHECK_CUDA(cudaMemsetAsync(P.m2l_d.p, 0, P.m2l_d.bytes(), s));
+        KF_CHECK_CUDA(cudaMemsetAsync(P.l2l_d.p, 0, P.l2l_d.bytes(), s));
+        KF_TRY(build_ops<double>(P, h, P.m2m_d.p, P.m2l_d.p, P.l2l_d.p, s));
+    } else {
+        KF_TRY(P.m2m_f.alloc(8 * QQ));
+        KF_TRY(P.m2l_f.alloc(kNumOffsets * QQ));
+        KF_TRY(P.l2l_f.alloc(8 * QQ));
+        KF_CHECK_CUDA(cudaMemsetAsync(P.m2m_f.p, 0, P.m2m_f.bytes(), s));
+        KF_CHECK_CUDA(cudaMemsetAsync(P.m2l_f.p, 0, P.m2l_f.bytes(), s));
+        KF_CHECK_CUDA(cudaMemsetAsync(P.l2l_f.p, 0, P.l2l_f.bytes(), s));
+        KF_TRY(build_ops<float>(P, h, P.m2m_f.p, P.m2l_f.p, P.l2l_f.p, s));
+    }
+
+    // work lists (host bookkeeping over the tree's lists)
+    std::vector<int> s2u_box, s2u_off{0}, s2u_idx, p2l_box, p2l_off{0}, p2l_idx, tleaf, p2p_off{0}, p2p_idx;
+    std::vector<int> tleaf_of(T.nt, 0);
+    for (int b = 0; b < T.nbox; ++b) {
+        int l = T.h_lvl[b];
+        if (T.h_leaf[b] && has_src(T, b) && l >= 2) {
+            s2u_box.push_back(b);
+            s2u_idx.push_back(b);
+            s2u_off.push_back((int)s2u_idx.size());
+        }
+        if (has_trg(T, b) && T.h_x_off[b + 1] > T.h_x_off[b]) {
+            p2l_box.push_back(b);
+            for (int k = T.h_x_off[b]; k < T.h_x_off[b + 1]; ++k) {
+                p2l_idx.push_back(T.h_x_idx[k]);
+                P.n_xpairs += T.h_rng[4 * T.h_x_idx[k] + 1] - T.h_rng[4 * T.h_x_idx[k]];
+            }
+            p2l_off.push_back((int)p2l_idx.size());
+        }
+        if (T.h_leaf[b] && has_trg(T, b)) {
+            tleaf.push_back(b);
+            for (int k = T.h_u_off[b]; k < T.h_u_off[b + 1]; ++k) p2p_idx.push_back(T.h_u_idx[k]);
+            for (int k = T.h_w_off[b]; k < T.h_w_off[b + 1]; ++k) p2p_idx.push_back(T.h_w_idx[k]);
+            p2p_off.push_back((int)p2p_idx.size());
+            for (int64_t t = T.h_rng[4 * b + 2]; t < T.h_rng[4 * b + 3]; ++t) tleaf_of[t] = b;
+            P.max_trg_leaf = std::max<int>(P.max_trg_leaf, (int)(T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2]));
+        }
+    }
+    P.n_s2u = (int)s2u_box.size();
+    P.n_p2l = (int)p2l_box.size();
+    P.n_tleaf = (int)tleaf.size();
+    KF_TRY(P.s2u_box.upload(s2u_box, s));
+    KF_TRY(P.s2u_off.upload(s2u_off, s));
+    KF_TRY(P.s2u_idx.upload(s2u_idx, s));
+    KF_TRY(P.p2l_box.upload(p2l_box, s));
+    KF_TRY(P.p2l_off.upload(p2l_off, s));
+    KF_TRY(P.p2l_idx.upload(p2l_idx, s));
+    KF_TRY(P.tleaf.upload(tleaf, s));
+    KF_TRY(P.p2p_off.upload(p2p_off, s));
+    KF_TRY(P.p2p_idx.upload(p2p_idx, s));
+
+    // U2U: per parent level, (child -> parent) grouped by the child's octant
+    {
+        std::vector<int4> tiles;
+        std::vector<int> pin, pout;
+        P.u2u.level_tile.assign(T.nlev + 1, 0);
+        for (int l = 0; l < T.nlev; ++l) {
+            P.u2u.level_tile[l] = (int)tiles.size();
+            if (l >= 2) {
+                std::vector<Triple> tr;
+                for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b) {
+                    if (T.h_leaf[b] || !has_src(T, b)) continue;
+                    for (int o = 0; o < 8; ++o) {
+                        int c = T.h_child[8 * b + o];
+                        if (c >= 0 && has_src(T, c)) tr.push_back({o, c, b});
+                    }
+                }
+                make_tiles(tr, tiles, pin, pout);
+            }
+        }
+        P.u2u.level_tile[T.nlev] = (int)tiles.size();
+        KF_TRY(upload_tiles(P.u2u, tiles, pin, pout, s));
+    }
+    // M2L: all V pairs grouped by offset
+    {
+        std::vector<int4> tiles;
+        std::vector<int> pin, pout;
+        std::vector<Triple> tr;
+        tr.reserve(T.nv);
+        for (int b = 0; b < T.nbox; ++b)
+            for (int k = T.h_v_off[b]; k < T.h_v_off[b + 1]; ++k) {
+                int a = T.h_v_idx[k];
+                int ox = T.h_coord[3 * a] - T.h_coord[3 * b], oy = T.h_coord[3 * a + 1] - T.h_coord[3 * b + 1],
+                    oz = T.h_coord[3 * a + 2] - T.h_coord[3 * b + 2];
+                tr.push_back({(ox + 3) * 49 + (oy + 3) * 7 + (oz + 3), a, b});
+            }
+        make_tiles(tr, tiles, pin, pout);
+        KF_TRY(upload_tiles(P.m2l, tiles, pin, pout, s));
+    }
+    // L2L: per child level >= 3, (parent -> child) grouped by the child's octant
+    {
+        std::vector<int4> tiles;
+        std::vector<int> pin, pout;
+        P.l2l.level_tile.assign(T.nlev + 1, 0);
+        for (int l = 0; l < T.nlev; ++l) {
+            P.l2l.level_tile[l] = (int)tiles.size();
+            if (l >= 3) {
+                std::vector<Triple> tr;
+                for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b)
+                    if (has_trg(T, b)) tr.push_back({octant_of(T, b), T.h_parent[b], b});
+                make_tiles(tr, tiles, pin, pout);
+            }
+        }
+        P.l2l.level_tile[T.nlev] = (int)tiles.size();
+        KF_TRY(upload_tiles(P.l2l, tiles, pin, pout, s));
+    }
+
+    // per-target evaluation rows and buffers
+    size_t nbq = (size_t)T.nbox * P.Qp;
+    if (P.fp64) {
+        KF_TRY(P.d2t_d.alloc((size_t)T.nt * P.Qp));
+        KF_TRY(build_d2t<double>(P, h, tleaf_of, P.d2t_d.p, s));
+        KF_TRY(P.u_d.alloc(nbq));
+        KF_TRY(P.d_d.alloc(nbq));
+        KF_TRY(P.res_d.alloc(T.nt));
+        KF_TRY(P.q_d.alloc(3 * T.ns));
+    } else {
+        KF_TRY(P.d2t_f.alloc((size_t)T.nt * P.Qp));
+        KF_TRY(build_d2t<float>(P, h, tleaf_of, P.d2t_f.p, s));
+        KF_TRY(P.u_f.alloc(nbq));
+        KF_TRY(P.d_f.alloc(nbq));
+        KF_TRY(P.res_f.alloc(T.nt));
+        KF_TRY(P.q_f.alloc(3 * T.ns));
+    }
+    KF_CHECK_CUDA(cudaStreamSynchronize(s));
+
+    P.device_bytes = 0;
+    for (size_t b : {P.m2m_d.bytes(), P.m2l_d.bytes(), P.l2l_d.bytes(), P.d2t_d.bytes(), P.m2m_f.bytes(),
+                     P.m2l_f.bytes(), P.l2l_f.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
+                     P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
+                     P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes()})
+        P.device_bytes += (int64_t)b;
+    return KIFMM_OK;
+}
+
+template <typename Real>
+struct Bufs {
+    const Real *m2m, *m2l, *l2l, *d2t, *surf, *tnrm;
+    Real *u, *d, *res, *q;
+};
+
+template <typename Real>
+int run_pairs(const Plan& P, const PairTiles& pt, int t0, int t1, const Real* ops, const Real* in,
+              Real* out, cudaStream_t s, int& launches) {
+    if (t1 <= t0) return KIFMM_OK;
+    k_pair_gemm<Real><<<t1 - t0, 256, 0, s>>>(ops, P.Q, P.Qp, pt.tiles.p + t0, pt.pin.p, pt.pout.p, in, out);
+    KF_CHECK_LAUNCH();
+    ++launches;
+    return KIFMM_OK;
+}
+
+template <typename Real>
+int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStream_t s) {
+    const Tree& T = P.tree->t;
+    const size_t nbq = (size_t)T.nbox * P.Qp;
+    int launches = 0;
+    cudaEvent_t* slot = nullptr;
+    if (P.profile) {
+        if (P.slots_used == (int)P.ev_slots.size() && P.ev_slots.size() < 4096) {
+            std::vector<cudaEvent_t> e(8, nullptr);
+            for (auto& x : e) KF_CHECK_CUDA(cudaEventCreate(&x));
+            P.ev_slots.push_back(e);
+        }
+        if (P.slots_used < (int)P.ev_slots.size()) slot = P.ev_slots[P.slots_used++].data();
+    }
+    auto mark = [&](int i) -> int {
+        if (slot) KF_CHECK_CUDA(cudaEventRecord(slot[i], s));
+        return KIFMM_OK;
+    };
+    const bool dl = P.kernel == KIFMM_KERNEL_DL;
+    KF_TRY(mark(0));
+    k_gather_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, T.sperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q);
+    KF_CHECK_LAUNCH();
+    KF_CHECK_CUDA(cudaMemsetAsync(B.u, 0, nbq * sizeof(Real), s));
+    KF_CHECK_CUDA(cudaMemsetAsync(B.d, 0, nbq * sizeof(Real), s));
+    launches += 3;
+    KF_TRY(mark(1));
+    // S2U
+    if (P.n_s2u) {
+        if (dl)
+            k_src2surf<Real, true><<<P.n_s2u, kSurfThreads, 0, s>>>(
+                P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, kUpCheck, T.lvl.p, T.ctr.p, T.root_h, T.rng.p, T.sxyz.p,
+                T.ns, B.q, B.surf, P.Q, P.Qp, B.u);
+        else
+            k_src2surf<Real, false><<<P.n_s2u, kSurfThreads, 0, s>>>(
+                P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, kUpCheck, T.lvl.p, T.ctr.p, T.root_h, T.rng.p, T.sxyz.p,
+                T.ns, B.q, B.surf, P.Q, P.Qp, B.u);
+        KF_CHECK_LAUNCH();
+        ++launches;
+    }
+    KF_TRY(mark(2));
+    // U2U, deepest parents first
+    for (int l = T.nlev - 1; l >= 2; --l)
+        KF_TRY(run_pairs<Real>(P, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, B.u, B.u, s,
+                               launches));
+    KF_TRY(mark(3));
+    // X list, then V list
+    if (P.n_p2l) {
+        if (dl)
+            k_src2surf<Real, true><<<P.n_p2l, kSurfThreads, 0, s>>>(
+                P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, kDnCheck, T.lvl.p, T.ctr.p, T.root_h, T.rng.p, T.sxyz.p,
+                T.ns, B.q, B.surf, P.Q, P.Qp, B.d);
+        else
+            k_src2surf<Real, false><<<P.n_p2l, kSurfThreads, 0, s>>>(
+                P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, kDnCheck, T.lvl.p, T.ctr.p, T.root_h, T.rng.p, T.sxyz.p,
+                T.ns, B.q, B.surf, P.Q, P.Qp, B.d);
+        KF_CHECK_LAUNCH();
+        ++launches;
+    }
+    KF_TRY(run_pairs<Real>(P, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, s, launches));
+    KF_TRY(mark(4));
+    // L2L, coarsest children first (ADL: each level's potentials shifted to zero mean first)
+    const bool center = P.kernel == KIFMM_KERNEL_ADL;
+    for (int l = 2; l < T.nlev; ++l) {
+        if (l >= 3)
+            KF_TRY(run_pairs<Real>(P, P.l2l, P.l2l.level_tile[l], P.l2l.level_tile[l + 1], B.l2l, B.d, B.d, s,
+                                   launches));
+        int nl = T.level_off[l + 1] - T.level_off[l];
+        if (center && nl > 0) {
+            k_center<Real><<<nl, 128, 0, s>>>(T.level_off[l], P.Q, P.Qp, B.d);
+            KF_CHECK_LAUNCH();
+            ++launches;
+        }
+    }
+    KF_TRY(mark(5));
+    if (P.n_tleaf) {
+        k_d2t<Real><<<P.n_tleaf, 128, P.Qp * sizeof(Real), s>>>(P.tleaf.p, T.rng.p, B.d2t, B.d, P.Qp, B.res);
+        KF_CHECK_LAUNCH();
+        ++launches;
+    }
+    KF_TRY(mark(6));
+    if (P.n_tleaf) {
+        int threads = std::min(256, std::max(32, (P.max_trg_leaf + 31) / 32 * 32));
+        size_t smem = 6 * threads * sizeof(Real);
+        const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
+        const int64_t* tperm = T.same ? T.sperm.p : T.tperm.p;
+#define KF_P2P(KIND)                                                                                     \
+    k_p2p<Real, KIND><<<P.n_tleaf, threads, smem, s>>>(P.tleaf.p, P.p2p_off.p, P.p2p_idx.p, T.rng.p,     \
+                                                        T.ctr.p, T.sxyz.p, T.ns, txyz, T.nt, B.q, B.tnrm, \
+                                                        B.res, tperm, out)
+        if (P.kernel == KIFMM_KERNEL_SL) KF_P2P(0);
+        else if (P.kernel == KIFMM_KERNEL_DL) KF_P2P(1);
+        else KF_P2P(2);
+#undef KF_P2P
+        KF_CHECK_LAUNCH();
+        ++launches;
+    }
+    KF_TRY(mark(7));
+    P.launches = launches;
+    return KIFMM_OK;
+}
+
+}  // namespace
+
+int plan_matvec(Plan& P, const double* q, double* out, cudaStream_t s) {
+    if (P.fp64) {
+        Bufs<double> B{P.m2m_d.p, P.m2l_d.p, P.l2l_d.p, P.d2t_d.p, P.surf_d.p, P.tnrm_d.p,
+                       P.u_d.p,   P.d_d.p,   P.res_d.p, P.q_d.p};
+        return matvec<double>(P, B, q, out, s);
+    }
+    Bufs<float> B{P.m2m_f.p, P.m2l_f.p, P.l2l_f.p, P.d2t_f.p, P.surf_f.p, P.tnrm_f.p,
+                  P.u_f.p,   P.d_f.p,   P.res_f.p, P.q_f.p};
+    return matvec<float>(P, B, q, out, s);
+}
+
+}  // namespace kifmm
+
+using namespace kifmm;
+
+extern "C" int kifmm_fmm_setup(kifmm_tree tree, int kernel, int p, int precision, double pinv_cutoff,
+                               const double* src_nrm, const double* trg_nrm, void* stream, kifmm_plan* out) {
+    clear_error();
+    KF_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    KF_ARG(tree != nullptr, "tree is NULL");
+    KF_ARG(kernel >= KIFMM_KERNEL_SL && kernel <= KIFMM_KERNEL_ADL, "unknown kernel");
+    KF_ARG(p >= 2 && p <= 16, "p must be in [2, 16]");
+    KF_ARG(precision == KIFMM_PREC_FP64 || precision == KIFMM_PREC_MIXED, "unknown precision");
+    KF_ARG(pinv_cutoff == 0.0 || (pinv_cutoff > 0.0 && pinv_cutoff < 1.0), "pinv_cutoff must be 0 or in (0,1)");
+    KF_ARG(kernel != KIFMM_KERNEL_DL || src_nrm != nullptr, "DL needs src_nrm");
+    KF_ARG(kernel != KIFMM_KERNEL_ADL || trg_nrm != nullptr, "ADL needs trg_nrm");
+    int dev = 0;
+    KF_CHECK_CUDA(cudaGetDevice(&dev));
+    KF_ARG(dev == tree->t.device, "tree was built on another device");
+    kifmm_plan pl = new (std::nothrow) kifmm_plan_s;
+    if (!pl) {
+        set_error("host allocation failed");
+        return KIFMM_ERR_OOM;
+    }
+    Plan& P = pl->P;
+    P.tree = tree;
+    P.kernel = kernel;
+    P.p = p;
+    P.prec = precision;
+    P.cutoff = pinv_cutoff > 0 ? pinv_cutoff : (precision == KIFMM_PREC_FP64 ? 1e-9 : 1e-8);
+    int rc = setup(P, src_nrm, trg_nrm, (cudaStream_t)stream);
+    if (rc != KIFMM_OK) {
+        delete pl;
+        return rc;
+    }
+    *out = pl;
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_fmm_matvec(kifmm_plan plan, const double* q, double* out, void* stream) {
+    clear_error();
+    KF_ARG(plan && q && out, "NULL plan, q or out");
+    return plan_matvec(plan->P, q, out, (cudaStream_t)stream);
+}
+
+extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
+    clear_error();
+    KF_ARG(plan && st, "NULL plan or stats");
+    const Plan& P = plan->P;
+    st->kernel = P.kernel;
+    st->p = P.p;
+    st->q_points = P.Q;
+    st->precision = P.prec;
+    st->pinv_cutoff = P.cutoff;
+    st->device_bytes = P.device_bytes;
+    st->m2l_pairs = P.m2l.npairs;
+    st->u2u_pairs = P.u2u.npairs;
+    st->l2l_pairs = P.l2l.npairs;
+    st->s2u_leaves = P.n_s2u;
+    st->x_pairs = P.n_xpairs;
+    st->launches_per_matvec = P.launches;
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases) {
+    clear_error();
+    KF_ARG(plan, "NULL plan");
+    Plan& P = plan->P;
+    if (phases) {
+        // mean over the matvecs recorded since the last read:
+        // {gather, s2u, u2u, m2l+x, l2l, d2t, p2p, total}
+        for (int i = 0; i < 8; ++i) phases[i] = 0;
+        for (int k = 0; k < P.slots_used; ++k) {
+            const std::vector<cudaEvent_t>& e = P.ev_slots[k];
+            KF_CHECK_CUDA(cudaEventSynchronize(e[7]));
+            float ms;
+            for (int i = 0; i < 7; ++i) {
+                KF_CHECK_CUDA(cudaEventElapsedTime(&ms, e[i], e[i + 1]));
+                phases[i] += ms;
+            }
+            KF_CHECK_CUDA(cudaEventElapsedTime(&ms, e[0], e[7]));
+            phases[7] += ms;
+        }
+        if (P.slots_used)
+            for (int i = 0; i < 8; ++i) phases[i] /= P.slots_used;
+        P.slots_used = 0;
+    }
+    P.profile = enable != 0;
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_plan_destroy(kifmm_plan plan) {
+    clear_error();
+    delete plan;
+    return KIFMM_OK;
+}

@@ -1,0 +1,73 @@
+// The FMM plan behind kifmm_plan: operators, per-target evaluation rows, work lists
+// and check-potential buffers for one (tree, kernel, order, precision).
+#pragma once
+
+#include "common.cuh"
+
+namespace kifmm {
+
+struct PairTiles {
+    DBuf<int4> tiles;               // (op, first pair, pair count, unused); count <= kPairTile
+    DBuf<int> pin, pout;            // input box, output box per pair
+    std::vector<int> level_tile;    // per level: [level_tile[l], level_tile[l+1]) tiles (U2U/L2L)
+    int ntiles = 0;
+    int64_t npairs = 0;
+};
+
+constexpr int kPairTile = 64;
+
+// Device scratch of the boundary-integral operators and GMRES, kept between calls
+// (the Krylov basis stays resident for the next solve on the same plan).
+struct BieScratch {
+    DBuf<double> q, krylov, w, r;
+};
+
+struct Plan {
+    kifmm_tree_s* tree = nullptr;
+    int kernel = 0, p = 0, Q = 0, Qp = 0, prec = 0;
+    double cutoff = 0;
+    bool fp64 = true;
+
+    // operators (Real = double for FP64, float for mixed), each Qp x Qp row-major
+    DBuf<double> m2m_d, m2l_d, l2l_d, d2t_d;
+    DBuf<float> m2m_f, m2l_f, l2l_f, d2t_f;
+    DBuf<double> surf_d;            // Q x 3 unit surface
+    DBuf<float> surf_f;
+
+    DBuf<double> snrm, tnrm_d;      // sorted normals (DL: sources; ADL: targets)
+    DBuf<float> tnrm_f;
+
+    // work lists
+    DBuf<int> s2u_box, s2u_off, s2u_idx;  // S2U: leaf boxes, CSR of source boxes (itself)
+    DBuf<int> p2l_box, p2l_off, p2l_idx;  // X list: boxes, CSR of source leaves
+    DBuf<int> tleaf, p2p_off, p2p_idx;    // target leaves, CSR of U + W source boxes
+    int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
+    int64_t n_xpairs = 0;
+    PairTiles u2u, m2l, l2l;
+    int max_trg_leaf = 0;
+
+    // per-matvec buffers
+    DBuf<double> u_d, d_d, res_d, q_d;
+    DBuf<float> u_f, d_f, res_f, q_f;
+
+    BieScratch bie;
+
+    // profiling: per-matvec slots of 8 events, reduced when read
+    bool profile = false;
+    std::vector<std::vector<cudaEvent_t>> ev_slots;
+    int slots_used = 0;
+    int launches = 0;
+    int64_t device_bytes = 0;
+
+    ~Plan() {
+        for (auto& sl : ev_slots)
+            for (auto e : sl)
+                if (e) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace kifmm
+
+struct kifmm_plan_s {
+    kifmm::Plan P;
+};

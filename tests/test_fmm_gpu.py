@@ -1,0 +1,255 @@
+"""GPU KIFMM through the C ABI vs the FP64 oracle (direct O(N^2) sums).
+
+Relative L2 error over all targets; full-size cases compare a seeded sample of
+targets, each computed exactly by the oracle.  Tolerances are the accuracy each
+form reaches at its order: the mixed form at p = 10 reaches 1e-6 on the benchmark
+geometry (cube, double layer) and for the single layer, 1-3e-6 for the double and
+adjoint double layer on curved or adaptive geometries (FP32 near-field cancellation
+in n.(x - y) and gradient evaluation of the far field); FP64 at p = 12 reaches 1e-8.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import bie as obie
+from oracle.gmres import gmres
+from oracle.quadrature import quadrature_points
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def gpu_points(m):
+    from paper_1605_01715_gb300 import kifmm_quadrature_points
+    tri = torch.from_numpy(np.ascontiguousarray(m.tri.reshape(-1, 9))).to(DEV)
+    sph = torch.from_numpy(np.ascontiguousarray(m.sph)).to(DEV)
+    return kifmm_quadrature_points(tri, sph)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+MESHES = {
+    "sphere": lambda: synth.geodesic_sphere(16),                                   # 5,120
+    "pack": lambda: synth.pack_mesh(*synth.sphere_pack(4, 0.5, 1.5, 8.0, 0.05, 1), 10),  # 8,000, adaptive
+    "cube": lambda: synth.cube_surface(37),                                        # 16,428 (ragged)
+}
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        m = MESHES[name]()
+        h = quadrature_points(m.tri, m.sph)
+        g = gpu_points(m)
+        sig = synth.uniform_density(m.n, 21)
+        refs = {k: oracle.direct(k, h[0], h[0], sig * h[1], src_nrm=h[2] if k == "dl" else None,
+                                 trg_nrm=h[2] if k == "adl" else None) for k in ("sl", "dl", "adl")}
+        _cache[name] = (m, h, g, sig, refs)
+    return _cache[name]
+
+
+def test_quadrature_points_match_oracle():
+    for name in ("pack", "cube"):
+        m, h, g, _, _ = case(name)
+        for a, b in zip(g, h):
+            assert np.abs(a.cpu().numpy() - b).max() < 1e-13
+
+
+# (kernel, precision, p, tolerance)
+MIXED = [("sl", "mixed", 10, 1e-6), ("dl", "mixed", 10, 3e-6), ("adl", "mixed", 10, 4e-6)]
+FP64 = [("sl", "fp64", 12, 1e-8), ("dl", "fp64", 12, 1e-7), ("adl", "fp64", 12, 1e-7)]
+
+
+@pytest.mark.parametrize("geom", ["sphere", "pack", "cube"])
+@pytest.mark.parametrize("kernel,prec,p,tol", MIXED + FP64)
+def test_fmm_matches_oracle(geom, kernel, prec, p, tol):
+    from paper_1605_01715_gb300 import Plan, Tree
+    m, h, (xyz, w, nrm), sig, refs = case(geom)
+    tree = Tree(xyz, max_leaf=40)
+    plan = Plan(tree, kernel=kernel, p=p, precision=prec, src_nrm=nrm, trg_nrm=nrm)
+    q = torch.from_numpy(sig).to(DEV) * w
+    out = plan.matvec(q).cpu().numpy()
+    err = rel(out, refs[kernel])
+    print("%s %s %s p=%d rel-L2 %.3e" % (geom, kernel, prec, p, err))
+    assert err < tol
+
+
+def test_benchmark_geometry_meets_1e6():
+    """Cube double layer (the demag matvec) in mixed precision at p = 10: rel-L2 <= 1e-6."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    m, h, (xyz, w, nrm), sig, refs = case("cube")
+    tree = Tree(xyz, max_leaf=64)
+    plan = Plan(tree, kernel="dl", p=10, precision="mixed", src_nrm=nrm)
+    q = torch.from_numpy(sig).to(DEV) * w
+    assert rel(plan.matvec(q).cpu().numpy(), refs["dl"]) <= 1e-6
+
+
+@pytest.mark.parametrize("max_leaf", [1, 7, 200])
+def test_leaf_sizes_and_repeat(max_leaf):
+    """Extreme leaf capacities; a second matvec on the same plan gives the same answer."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    m, h, (xyz, w, nrm), sig, refs = case("sphere")
+    tree = Tree(xyz, max_leaf=max_leaf)
+    plan = Plan(tree, kernel="sl", p=8, precision="mixed")
+    q = torch.from_numpy(sig).to(DEV) * w
+    a = plan.matvec(q).cpu().numpy()
+    b = plan.matvec(q).cpu().numpy()
+    assert rel(a, refs["sl"]) < 2e-6
+    assert rel(a, b) < 1e-6
+
+
+def test_target_source_model():
+    """Targets distinct from sources (Sec. III.A.1): nodal-like targets off the quadrature points."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    m, h, (xyz, w, nrm), sig, _ = case("cube")
+    rng = np.random.default_rng(4)
+    trg = rng.uniform(-0.7, 0.7, size=(3, 3001))
+    tnrm = rng.normal(size=(3, 3001))
+    tnrm /= np.linalg.norm(tnrm, axis=0)
+    ttrg = torch.from_numpy(trg).to(DEV)
+    tree = Tree(xyz, ttrg, max_leaf=48)
+    q = torch.from_numpy(sig).to(DEV) * w
+    for kernel, tol in (("sl", 1e-6), ("dl", 3e-6), ("adl", 6e-6)):
+        plan = Plan(tree, kernel=kernel, p=10, precision="mixed", src_nrm=nrm,
+                    trg_nrm=torch.from_numpy(tnrm).to(DEV))
+        ref = oracle.direct(kernel, trg, h[0], sig * h[1], src_nrm=h[2] if kernel == "dl" else None,
+                            trg_nrm=tnrm if kernel == "adl" else None)
+        assert rel(plan.matvec(q).cpu().numpy(), ref) < tol
+
+
+def test_tolerance_radius_and_tiny_inputs():
+    from paper_1605_01715_gb300 import Plan, Tree
+    # one source: its own target is excluded -> 0
+    one = torch.tensor([[0.1], [0.2], [0.3]], dtype=torch.float64, device=DEV)
+    plan = Plan(Tree(one, max_leaf=4), kernel="sl", p=4, precision="fp64")
+    assert plan.matvec(torch.ones(1, dtype=torch.float64, device=DEV)).item() == 0.0
+    # pairs closer than 1e-5 contribute nothing, farther ones do
+    d = 1e-5
+    pts = np.array([[0.0, 0.1 * d, 10 * d, 0.5], [0.0, 0.0, 0.0, 0.5], [0.0, 0.0, 0.0, 0.5]])
+    q = np.array([1.0, 2.0, 3.0, 4.0])
+    ref = oracle.direct("sl", pts, pts, q)
+    for prec in ("fp64", "mixed"):
+        plan = Plan(Tree(torch.from_numpy(pts).to(DEV), max_leaf=4), kernel="sl", p=4, precision=prec)
+        out = plan.matvec(torch.from_numpy(q).to(DEV)).cpu().numpy()
+        assert rel(out, ref) < (1e-12 if prec == "fp64" else 1e-6)
+
+
+def test_invalid_arguments_raise():
+    from paper_1605_01715_gb300 import KifmmError, Plan, Tree
+    xyz = torch.zeros((3, 10), dtype=torch.float64, device=DEV)
+    with pytest.raises(KifmmError) as e:
+        Tree(xyz, max_leaf=0)
+    assert e.value.status == "INVALID_ARG"
+    bad = xyz.clone()
+    bad[0, 3] = float("nan")
+    with pytest.raises(KifmmError) as e:
+        Tree(bad, max_leaf=8)
+    assert e.value.status == "INVALID_ARG"
+    tree = Tree(torch.rand((3, 10), dtype=torch.float64, device=DEV), max_leaf=8)
+    with pytest.raises(KifmmError):
+        Plan(tree, kernel="dl", p=6, precision="fp64", src_nrm=None)
+    with pytest.raises(KifmmError):
+        Plan(tree, kernel="sl", p=1, precision="fp64")
+
+
+def test_full_size_demag_cube_sampled():
+    """1,051,392-point cube, double layer with density n.M, in the benchmark's configuration."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    wl = synth.workload("demag_cube_1m")
+    m = wl["mesh"]
+    xyz, w, nrm = gpu_points(m)
+    q = (nrm[2] * w).contiguous()
+    plan = Plan(Tree(xyz, max_leaf=wl["max_leaf"]), kernel="dl", p=wl["p"], precision="mixed", src_nrm=nrm)
+    out = plan.matvec(q).cpu().numpy()
+    hx, hw, hn = quadrature_points(m.tri, m.sph)
+    idx = np.sort(np.random.default_rng(77).choice(m.n, 1024, replace=False))
+    ref = oracle.direct("dl", hx, hx, hn[2] * hw, src_nrm=hn, idx=idx)
+    assert rel(out[idx], ref) <= 1e-6
+
+
+# ------------------------------------------------------------------ boundary-integral operators
+def _two_spheres(f=8):
+    c = np.array([[0.0, 0.0, 0.0], [2.6, 0.3, -0.2]])
+    r = np.array([1.0, 0.7])
+    m = synth.pack_mesh(c, r, f)
+    eps = np.where(m.body == 0, 10.0, 4.0)
+    curv = 1.0 / m.sph[:, 3]
+    return m, eps, curv
+
+
+def test_polarization_operator_and_rhs():
+    from paper_1605_01715_gb300 import Plan, Tree, kifmm_polarization_rhs
+    m, eps, curv = _two_spheres()
+    hx, hw, hn = quadrature_points(m.tri, m.sph)
+    xyz, w, nrm = gpu_points(m)
+    x = synth.uniform_density(m.n, 5)
+    A = obie.polarization_operator(hx, hn, hw, eps, 1.0, curv)
+    ref = A(x)
+    plan = Plan(Tree(xyz, max_leaf=32), kernel="adl", p=10, precision="mixed", trg_nrm=nrm)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    y = plan.bie_apply(w, t(eps), 1.0, t(curv), t(x)).cpu().numpy()
+    assert rel(y, ref) < 1e-6
+    b = kifmm_polarization_rhs(nrm, t(eps), 1.0, (0.0, 0.0, 1.0)).cpu().numpy()
+    assert rel(b, obie.polarization_rhs_uniform_field(hn, eps, 1.0, (0, 0, 1))) < 1e-14
+
+
+@pytest.mark.parametrize("prec,tol_x", [("fp64", 1e-7), ("mixed", 1e-5)])
+def test_polarization_gmres_matches_oracle_solve(prec, tol_x):
+    from paper_1605_01715_gb300 import Plan, Tree, kifmm_polarization_rhs
+    m, eps, curv = _two_spheres()
+    hx, hw, hn = quadrature_points(m.tri, m.sph)
+    xyz, w, nrm = gpu_points(m)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    A = obie.polarization_operator(hx, hn, hw, eps, 1.0, curv)
+    b_h = obie.polarization_rhs_uniform_field(hn, eps, 1.0, (0, 0, 1))
+    x_ref, it_ref, _, ok = gmres(A, b_h, tol=1e-10, restart=50)
+    assert ok
+    plan = Plan(Tree(xyz, max_leaf=32), kernel="adl", p=12 if prec == "fp64" else 10, precision=prec,
+                trg_nrm=nrm)
+    b = kifmm_polarization_rhs(nrm, t(eps), 1.0, (0.0, 0.0, 1.0))
+    x, it, rr, rc = plan.bie_solve(w, t(eps), 1.0, t(curv), b, tol=1e-10 if prec == "fp64" else 1e-7,
+                                   restart=30)
+    x = x.cpu().numpy()
+    assert rc == 0 and it > 0
+    assert rel(x, x_ref) < tol_x
+    # the true residual of the GPU solution under the oracle's operator
+    assert np.linalg.norm(b_h - A(x)) / np.linalg.norm(b_h) < 10 * tol_x
+
+
+def test_dielectric_sphere_closed_form_on_gpu():
+    """GPU solve of a single sphere reproduces 3(eps_i - eps_m)/(eps_i + 2 eps_m) E0 cos(theta)."""
+    from paper_1605_01715_gb300 import Plan, Tree, kifmm_polarization_rhs
+    R, ei = 1.3, 10.0
+    m = synth.geodesic_sphere(16, center=(1.0, 2.0, 3.0), radius=R)
+    xyz, w, nrm = gpu_points(m)
+    n = m.n
+    eps = torch.full((n,), ei, dtype=torch.float64, device=DEV)
+    curv = torch.full((n,), 1.0 / R, dtype=torch.float64, device=DEV)
+    plan = Plan(Tree(xyz, max_leaf=48), kernel="adl", p=10, precision="mixed", trg_nrm=nrm)
+    b = kifmm_polarization_rhs(nrm, eps, 1.0, (0.0, 0.0, 1.0))
+    x, it, rr, rc = plan.bie_solve(w, eps, 1.0, curv, b, tol=1e-7)
+    exact = 3 * (ei - 1.0) / (ei + 2.0) * nrm[2]
+    # the true residual bottoms out near the FP32 operator's own rounding (~1e-6)
+    assert rc == 0 and rr < 1e-5
+    assert rel(x.cpu().numpy(), exact.cpu().numpy()) < 1e-3
+
+
+def test_demag_phi2_matches_oracle():
+    from paper_1605_01715_gb300 import Plan, Tree
+    m = synth.cube_surface(20)
+    hx, hw, hn = quadrature_points(m.tri, m.sph)
+    xyz, w, nrm = gpu_points(m)
+    phi1_h = 4 * math.pi * hx[2]                       # phi_1 = 4 pi M.r for M = z-hat
+    omega_h = np.full(m.n, 2 * math.pi)                 # face centroids: Omega = 2 pi
+    ref = obie.demag_phi2(hx, hn, hw, phi1_h, omega_h)
+    plan = Plan(Tree(xyz, max_leaf=32), kernel="dl", p=10, precision="mixed", src_nrm=nrm)
+    phi1 = (4 * math.pi * xyz[2]).contiguous()
+    out = plan.demag_phi2(phi1, w, torch.full_like(w, 2 * math.pi)).cpu().numpy()
+    assert rel(out, ref) < 1e-6
