@@ -123,10 +123,10 @@ k_src2surf(const int* __restrict__ boxes, const int* __restrict__ off, const int
 // Every tile shares one operator: out[pout[j]] += Op . in[pin[j]] for its pairs.
 // CUDA-core SGEMM/DGEMM blocking: 64 rows x 64 pairs per pass, 4x4 per thread.
 template <typename Real>
-__global__ void __launch_bounds__(256)
-k_pair_gemm(const Real* __restrict__ ops, int Q, int Qp, const int4* __restrict__ tiles,
-            const int* __restrict__ pin, const int* __restrict__ pout, const Real* __restrict__ in,
-            Real* __restrict__ out) {
+__device__ __forceinline__ void pair_gemm_body(const Real* __restrict__ ops, int Q, int Qp,
+                                               const int4* __restrict__ tiles, const int* __restrict__ pin,
+                                               const int* __restrict__ pout, const Real* __restrict__ in,
+                                               Real* __restrict__ out) {
     constexpr int BM = 64, BN = kPairTile, BK = 16;
     __shared__ Real As[BK][BM + 4];
     __shared__ Real Bs[BK][BN + 4];
@@ -184,6 +184,20 @@ k_pair_gemm(const Real* __restrict__ ops, int Q, int Qp, const int4* __restrict_
         }
     }
 }
+
+// One kernel name per translation so profiles tell them apart.
+#define KF_PAIR_KERNEL(NAME)                                                                              \
+    template <typename Real>                                                                              \
+    __global__ void __launch_bounds__(256)                                                               \
+        NAME(const Real* __restrict__ ops, int Q, int Qp, const int4* __restrict__ tiles,                \
+             const int* __restrict__ pin, const int* __restrict__ pout, const Real* __restrict__ in,     \
+             Real* __restrict__ out) {                                                                    \
+        pair_gemm_body<Real>(ops, Q, Qp, tiles, pin, pout, in, out);                                      \
+    }
+KF_PAIR_KERNEL(k_u2u_gemm)
+KF_PAIR_KERNEL(k_m2l_gemm)
+KF_PAIR_KERNEL(k_l2l_gemm)
+#undef KF_PAIR_KERNEL
 
 // ---------------------------------------------------------------- mean removal (ADL)
 // The adjoint double layer needs only the gradient of the far field.  A constant
@@ -644,11 +658,14 @@ struct Bufs {
     Real *u, *d, *res, *q;
 };
 
+enum { kU2U = 0, kM2L = 1, kL2L = 2 };
+
 template <typename Real>
-int run_pairs(const Plan& P, const PairTiles& pt, int t0, int t1, const Real* ops, const Real* in,
+int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const Real* ops, const Real* in,
               Real* out, cudaStream_t s, int& launches) {
     if (t1 <= t0) return KIFMM_OK;
-    k_pair_gemm<Real><<<t1 - t0, 256, 0, s>>>(ops, P.Q, P.Qp, pt.tiles.p + t0, pt.pin.p, pt.pout.p, in, out);
+    auto kern = which == kU2U ? k_u2u_gemm<Real> : which == kM2L ? k_m2l_gemm<Real> : k_l2l_gemm<Real>;
+    kern<<<t1 - t0, 256, 0, s>>>(ops, P.Q, P.Qp, pt.tiles.p + t0, pt.pin.p, pt.pout.p, in, out);
     KF_CHECK_LAUNCH();
     ++launches;
     return KIFMM_OK;
@@ -696,7 +713,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_TRY(mark(2));
     // U2U, deepest parents first
     for (int l = T.nlev - 1; l >= 2; --l)
-        KF_TRY(run_pairs<Real>(P, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, B.u, B.u, s,
+        KF_TRY(run_pairs<Real>(P, kU2U, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, B.u, B.u, s,
                                launches));
     KF_TRY(mark(3));
     // X list, then V list
@@ -712,13 +729,13 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         KF_CHECK_LAUNCH();
         ++launches;
     }
-    KF_TRY(run_pairs<Real>(P, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, s, launches));
+    KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, s, launches));
     KF_TRY(mark(4));
     // L2L, coarsest children first (ADL: each level's potentials shifted to zero mean first)
     const bool center = P.kernel == KIFMM_KERNEL_ADL;
     for (int l = 2; l < T.nlev; ++l) {
         if (l >= 3)
-            KF_TRY(run_pairs<Real>(P, P.l2l, P.l2l.level_tile[l], P.l2l.level_tile[l + 1], B.l2l, B.d, B.d, s,
+            KF_TRY(run_pairs<Real>(P, kL2L, P.l2l, P.l2l.level_tile[l], P.l2l.level_tile[l + 1], B.l2l, B.d, B.d, s,
                                    launches));
         int nl = T.level_off[l + 1] - T.level_off[l];
         if (center && nl > 0) {

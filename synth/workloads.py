@@ -34,6 +34,11 @@ def _demag_cube_1m():
     return dict(mesh=m, kernel="dl", p=10, max_leaf=64, magnetization=(0.0, 0.0, 1.0))
 
 
+def _demag_cube_270k():
+    m = cube_surface(150)
+    return dict(mesh=m, kernel="dl", p=10, max_leaf=64, magnetization=(0.0, 0.0, 1.0))
+
+
 def _demag_sphere_1m():
     m = geodesic_sphere(229)
     return dict(mesh=m, kernel="dl", p=10, max_leaf=64, magnetization=(0.0, 0.0, 1.0))
@@ -50,6 +55,7 @@ def _polar_64():
 WORKLOADS = {
     "sl_sphere_20k": _sl_sphere_20k,
     "demag_cube_1m": _demag_cube_1m,
+    "demag_cube_270k": _demag_cube_270k,
     "demag_sphere_1m": _demag_sphere_1m,
     "polar_64": _polar_64,
 }
