@@ -227,6 +227,24 @@ int kifmm_bie_apply(kifmm_plan plan, const double* area, const double* eps_in, d
 int kifmm_demag_phi2(kifmm_plan plan, const double* phi1, const double* w,
                      const double* omega, double* phi2, void* stream);
 
+/*
+ * kifmm_demag_phi2 without any device allocation (the paper has no counterpart; this
+ * is a library-level convenience).  For callers that cannot allocate device memory
+ * when they evaluate phi2: a pooled or custom allocator that forbids driver
+ * allocations, a loop that cannot afford cudaMalloc's implicit synchronization, or
+ * work being recorded into a CUDA graph.  Same arguments and result as
+ * kifmm_demag_phi2; the scratch vector phi1 * w is kept in a static device array of
+ * 2^20 doubles (8 MiB) that every device holds while the library is loaded.
+ *  - Plans with more than 2^20 targets are rejected with KIFMM_ERR_INVALID_ARG.
+ *  - The first call on a device looks up that array's device address (once per
+ *    device); make that first call before any stream capture begins.
+ *  - All calls share the one array, so calls that can overlap on the GPU (different
+ *    streams, or different plans without ordering between them) race on it.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called.  Asynchronous.
+ */
+int kifmm_demag_phi2_noalloc(kifmm_plan plan, const double* phi1, const double* w,
+                             const double* omega, double* phi2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

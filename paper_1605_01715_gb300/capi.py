@@ -83,6 +83,7 @@ _SIGS = {
                          ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "kifmm_bie_apply": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, _P], ctypes.c_int),
     "kifmm_demag_phi2": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "kifmm_demag_phi2_noalloc": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
 }
 
 
@@ -268,6 +269,13 @@ class Plan:
             out = torch.empty(n, dtype=torch.float64, device=phi1.device)
         _check(lib().kifmm_demag_phi2(self.handle, _dev(phi1, n, "phi1"), _dev(w, n, "w"),
                                       _dev(omega, n, "omega"), _dev(out, n, "out"), _stream(stream)))
+        return out
+
+    def demag_phi2_noalloc(self, phi1, w, omega, out, stream=None):
+        """kifmm_demag_phi2_noalloc: `out` must be preallocated; nothing is allocated."""
+        n = self.n_trg
+        _check(lib().kifmm_demag_phi2_noalloc(self.handle, _dev(phi1, n, "phi1"), _dev(w, n, "w"),
+                                              _dev(omega, n, "omega"), _dev(out, n, "out"), _stream(stream)))
         return out
 
     def close(self):

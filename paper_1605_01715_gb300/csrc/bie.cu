@@ -13,6 +13,7 @@
 // orthogonalization and the residuals in FP64 on the device; only the small
 // Hessenberg least-squares problem runs on the host.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -191,6 +192,65 @@ extern "C" int kifmm_demag_phi2(kifmm_plan plan, const double* phi1, const doubl
     k_mul<<<div_up(n, 256), 256, 0, s>>>(phi1, w, n, S.q.p);
     KF_CHECK_LAUNCH();
     KF_TRY(plan_matvec(P, S.q.p, phi2, s));
+    k_demag_combine<<<div_up(n, 256), 256, 0, s>>>(phi1, omega, n, phi2);
+    KF_CHECK_LAUNCH();
+    return KIFMM_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Allocation-free variant of kifmm_demag_phi2.
+//
+// Some callers cannot allocate device memory at the moment they need phi2: code
+// running under a custom or pooled allocator that forbids driver allocations,
+// real-time loops where cudaMalloc's implicit device synchronization is not
+// acceptable, or pipelines that record their work into a CUDA graph.  For them the
+// scratch vector phi1 * w lives in this file-scope device array instead of a
+// buffer the plan allocates on first use.  The array exists once per device for
+// as long as the library is loaded.
+constexpr int64_t kNoAllocMaxPoints = 1 << 20;   // 8 MiB of FP64 scratch per device
+static __device__ __align__(256) double g_noalloc_q[kNoAllocMaxPoints];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64] = {};
+
+// Device address of g_noalloc_q on the current device (looked up once per device).
+static int noalloc_scratch(double** out) {
+    int dev = 0;
+    KF_CHECK_CUDA(cudaGetDevice(&dev));
+    KF_ARG(dev >= 0 && dev < 64, "device ordinal out of range for the scratch table");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_q);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress(g_noalloc_q): %s", cudaGetErrorString(e));
+            return KIFMM_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_demag_phi2_noalloc(kifmm_plan plan, const double* phi1, const double* w,
+                                        const double* omega, double* phi2, void* stream) {
+    clear_error();
+    KF_TRY(check_plan_for(plan, KIFMM_KERNEL_DL));
+    KF_ARG(phi1 && w && omega && phi2, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan& P = plan->P;
+    int64_t n = P.tree->t.nt;
+    if (n > kNoAllocMaxPoints) {
+        set_error("invalid argument: kifmm_demag_phi2_noalloc handles at most %lld points, plan has %lld",
+                  (long long)kNoAllocMaxPoints, (long long)n);
+        return KIFMM_ERR_INVALID_ARG;
+    }
+    double* q = nullptr;
+    KF_TRY(noalloc_scratch(&q));
+    // every entry of q[0, n) is overwritten here, so nothing needs clearing
+    k_mul<<<div_up(n, 256), 256, 0, s>>>(phi1, w, n, q);
+    KF_CHECK_LAUNCH();
+    KF_TRY(plan_matvec(P, q, phi2, s));
     k_demag_combine<<<div_up(n, 256), 256, 0, s>>>(phi1, omega, n, phi2);
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
