@@ -178,6 +178,14 @@ int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);
  */
 int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases);
 
+/*
+ * Health check of the plan's device work (synchronizes with the device).  The
+ * tensor-core translation GEMMs bound every pipeline wait; a wait that gives up
+ * records a code in a device word of the plan, skips its writes and frees its
+ * tensor memory.  Returns KIFMM_ERR_TIMEOUT if that ever happened, else KIFMM_OK.
+ */
+int kifmm_plan_check(kifmm_plan plan);
+
 /* Release a plan.  NULL is a no-op. */
 int kifmm_plan_destroy(kifmm_plan plan);
 

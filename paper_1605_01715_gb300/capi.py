@@ -77,6 +77,7 @@ _SIGS = {
     "kifmm_fmm_matvec": ([_P, _P, _P, _P], ctypes.c_int),
     "kifmm_plan_get_stats": ([_P, ctypes.POINTER(PlanStats)], ctypes.c_int),
     "kifmm_plan_profile": ([_P, ctypes.c_int, _P], ctypes.c_int),
+    "kifmm_plan_check": ([_P], ctypes.c_int),
     "kifmm_plan_destroy": ([_P], ctypes.c_int),
     "kifmm_polarization_rhs": ([_P, _P, ctypes.c_double, _P, _I64, _P, _P], ctypes.c_int),
     "kifmm_bie_solve": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_double, ctypes.c_int,
@@ -227,6 +228,10 @@ class Plan:
         _check(lib().kifmm_fmm_matvec(self.handle, _dev(q, self.n_src, "q"), _dev(out, self.n_trg, "out"),
                                       _stream(stream)))
         return out
+
+    def check(self):
+        """kifmm_plan_check: raise KifmmError(TIMEOUT) if a bounded device wait gave up."""
+        _check(lib().kifmm_plan_check(self.handle))
 
     def stats(self):
         st = PlanStats()

@@ -21,6 +21,10 @@
 
 namespace kifmm {
 
+int tc_tile_pairs(int Qp);
+int launch_pair_tc(const float* ops, int Q, int Qp, const int4* tiles, int ntiles, const int* pin, const int* pout,
+                   const float* in, float* out, int* err, cudaStream_t s);
+
 namespace {
 
 template <typename Real> struct RT;
@@ -133,13 +137,15 @@ __device__ __forceinline__ void pair_gemm_body(const Real* __restrict__ ops, int
     __shared__ int s_in[BN], s_out[BN];
     int4 t = tiles[blockIdx.x];
     const Real* Op = ops + (size_t)t.x * Qp * Qp;
-    int cnt = t.z;
+    int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    for (int jb = 0; jb < t.z; jb += BN) {  // tiles may hold several blocks of BN pairs
+    const int cnt = t.z - jb;
+    __syncthreads();
     for (int j = threadIdx.x; j < BN; j += blockDim.x) {
-        s_in[j] = j < cnt ? pin[t.y + j] : -1;
-        s_out[j] = j < cnt ? pout[t.y + j] : -1;
+        s_in[j] = j < cnt ? pin[t.y + jb + j] : -1;
+        s_out[j] = j < cnt ? pout[t.y + jb + j] : -1;
     }
     __syncthreads();
-    int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     for (int row0 = 0; row0 < Q; row0 += BM) {
         Real acc[4][4];
 #pragma unroll
@@ -182,6 +188,7 @@ __device__ __forceinline__ void pair_gemm_body(const Real* __restrict__ ops, int
                 if (ob >= 0) atomicAdd(&out[(size_t)ob * Qp + row], acc[i][j]);
             }
         }
+    }
     }
 }
 
@@ -349,19 +356,19 @@ int octant_of(const Tree& T, int b) {
 bool has_src(const Tree& T, int b) { return T.h_rng[4 * b + 1] > T.h_rng[4 * b]; }
 bool has_trg(const Tree& T, int b) { return T.h_rng[4 * b + 3] > T.h_rng[4 * b + 2]; }
 
-// Group (op, in, out) triples by op into tiles of <= kPairTile pairs.
+// Group (op, in, out) triples by op into tiles of <= cap pairs.
 struct Triple {
     int op, in, out;
 };
 
 void make_tiles(std::vector<Triple>& tr, std::vector<int4>& tiles, std::vector<int>& pin,
-                std::vector<int>& pout) {
+                std::vector<int>& pout, int cap) {
     std::stable_sort(tr.begin(), tr.end(), [](const Triple& a, const Triple& b) { return a.op < b.op; });
     size_t base = pin.size();
     size_t i = 0;
     while (i < tr.size()) {
         size_t j = i;
-        while (j < tr.size() && tr[j].op == tr[i].op && j - i < (size_t)kPairTile) ++j;
+        while (j < tr.size() && tr[j].op == tr[i].op && j - i < (size_t)cap) ++j;
         tiles.push_back(make_int4(tr[i].op, (int)(base + i), (int)(j - i), 0));
         i = j;
     }
@@ -485,6 +492,10 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     P.Q = h.Q;
     P.Qp = (h.Q + 15) / 16 * 16;
     P.fp64 = P.prec == KIFMM_PREC_FP64;
+    // mixed: tiles sized for the tensor-core GEMM; FP64: CUDA-core blocks of kPairTile
+    P.tile_cap = P.fp64 ? kPairTile : tc_tile_pairs(P.Qp);
+    KF_TRY(P.err.alloc(1));
+    KF_CHECK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), s));
     const size_t QQ = (size_t)P.Qp * P.Qp;
 
     // sorted normals
@@ -584,7 +595,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                         if (c >= 0 && has_src(T, c)) tr.push_back({o, c, b});
                     }
                 }
-                make_tiles(tr, tiles, pin, pout);
+                make_tiles(tr, tiles, pin, pout, P.tile_cap);
             }
         }
         P.u2u.level_tile[T.nlev] = (int)tiles.size();
@@ -603,7 +614,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                     oz = T.h_coord[3 * a + 2] - T.h_coord[3 * b + 2];
                 tr.push_back({(ox + 3) * 49 + (oy + 3) * 7 + (oz + 3), a, b});
             }
-        make_tiles(tr, tiles, pin, pout);
+        make_tiles(tr, tiles, pin, pout, P.tile_cap);
         KF_TRY(upload_tiles(P.m2l, tiles, pin, pout, s));
     }
     // L2L: per child level >= 3, (parent -> child) grouped by the child's octant
@@ -617,7 +628,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                 std::vector<Triple> tr;
                 for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b)
                     if (has_trg(T, b)) tr.push_back({octant_of(T, b), T.h_parent[b], b});
-                make_tiles(tr, tiles, pin, pout);
+                make_tiles(tr, tiles, pin, pout, P.tile_cap);
             }
         }
         P.l2l.level_tile[T.nlev] = (int)tiles.size();
@@ -662,7 +673,24 @@ enum { kU2U = 0, kM2L = 1, kL2L = 2 };
 
 template <typename Real>
 int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const Real* ops, const Real* in,
-              Real* out, cudaStream_t s, int& launches) {
+              Real* out, cudaStream_t s, int& launches);
+
+// Mixed precision: 3xTF32 on the tensor cores (tcgen05).
+template <>
+int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const float* ops,
+                     const float* in, float* out, cudaStream_t s, int& launches) {
+    (void)which;
+    if (t1 <= t0) return KIFMM_OK;
+    KF_TRY(launch_pair_tc(ops, P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p, pt.pout.p, in, out, P.err.p, s));
+    ++launches;
+    return KIFMM_OK;
+}
+
+// FP64: CUDA-core blocked GEMM.
+template <>
+int run_pairs<double>(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const double* ops,
+                      const double* in, double* out, cudaStream_t s, int& launches) {
+    using Real = double;
     if (t1 <= t0) return KIFMM_OK;
     auto kern = which == kU2U ? k_u2u_gemm<Real> : which == kM2L ? k_m2l_gemm<Real> : k_l2l_gemm<Real>;
     kern<<<t1 - t0, 256, 0, s>>>(ops, P.Q, P.Qp, pt.tiles.p + t0, pt.pin.p, pt.pout.p, in, out);
@@ -873,6 +901,18 @@ extern "C" int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases) {
         P.slots_used = 0;
     }
     P.profile = enable != 0;
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_plan_check(kifmm_plan plan) {
+    clear_error();
+    KF_ARG(plan, "NULL plan");
+    int h = 0;
+    KF_CHECK_CUDA(cudaMemcpy(&h, plan->P.err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        set_error("a tensor-core translation GEMM gave up waiting on its pipeline (code %d)", h);
+        return KIFMM_ERR_TIMEOUT;
+    }
     return KIFMM_OK;
 }
 

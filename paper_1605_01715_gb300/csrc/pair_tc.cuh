@@ -1,0 +1,365 @@
+// Grouped translation GEMM on the 5th-generation tensor cores (tcgen05), 3xTF32.
+//
+// Every tile of the work list shares one Qp x Qp operator Op (M2M', M2L' or L2L') and
+// holds up to kTcN (input box, output box) pairs; the CTA computes one 128-row slab of
+//   out[pout[j]][row] += sum_k Op[row][k] * in[pin[j]][k]
+// for all pairs j of the tile as D(128 x N) = A(128 x K) B(N x K)^T with A = the
+// operator rows and B = the gathered input vectors, accumulated in TMEM (FP32).
+//
+// 3xTF32: x = x_hi + x_lo (both the nearest TF32 values); D += A_hi B_hi + A_hi B_lo +
+// A_lo B_hi (the dropped A_lo B_lo term is ~2^-22 relative).
+//
+// Accumulation: the tensor core adds into its FP32 accumulator with truncation, so a
+// long K loop into one accumulator drifts by ~1 ulp of the running sum per MMA.  Each
+// K-chunk of 32 therefore starts a fresh accumulator (correction products first, then
+// the hi*hi products) in one of two TMEM buffers, and the threads fold every chunk's
+// partial into FP32 registers (round-to-nearest) while the next chunk multiplies.
+//
+// Shared-memory operands use the canonical K-major layout without swizzle: 8-row x
+// 16-byte core matrices; core matrices adjacent in K are kLBO = 128 B apart, adjacent
+// 8-row groups kSBO = (KC/4)*128 B apart.  Every mbarrier wait is bounded; on a
+// timeout the CTA records an error, waits (bounded) once more, frees its TMEM and
+// returns without writing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kifmm {
+namespace tc {
+
+constexpr int kKC = 32;             // K elements per pipeline stage (4 MMA k-steps)
+constexpr int kThreads = 256;
+constexpr uint32_t kLBO = 128;                   // bytes between K-adjacent core matrices
+constexpr uint32_t kSBO = (kKC / 4) * 128;       // bytes between 8-row groups
+constexpr int kSlabBytes = 128 * kKC * 4;        // one 128-row operand slab of one chunk: 8 KB
+constexpr long long kSpinLimit = 1LL << 26;
+
+// Tile shape: SLABS x 128 operator rows by N pairs; two accumulator buffers fill the
+// 512 TMEM columns (2 * SLABS * N = 512).  Each warp owns one lane quarter and 128
+// accumulator columns, held as FP32 registers.
+template <int SLABS, int N>
+struct Shape {
+    static constexpr int kRows = SLABS * 128;
+    static constexpr int kTmemCols = 512;
+    static constexpr int kBufCols = SLABS * N;                 // one accumulator buffer
+    static constexpr int kABytes = SLABS * kSlabBytes;        // per hi or lo copy
+    static constexpr int kBBytes = (N / 128) * kSlabBytes;     // per hi or lo copy (N multiple of 128)
+    static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+    static constexpr int kStages = 2;
+    static constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+    static constexpr int kAVec = kRows * (kKC / 4) / kThreads;   // float4 of A per thread per chunk
+    static constexpr int kBVec = N * (kKC / 4) / kThreads;       // float4 of B per thread per chunk
+    static_assert(2 * SLABS * N == 512, "two accumulator buffers fill TMEM");
+    static_assert(N % 128 == 0 && N <= 256, "N must be 128 or 256");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    // base offset 0, LBO mode 0, layout type 0 (no swizzle)
+    return d;
+}
+
+// kind::tf32 instruction descriptor: D FP32, A/B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Round to the nearest TF32 value (ties away from zero); the result is exact in TF32.
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// x = hi + lo with hi, lo nearest TF32 values: |x - hi - lo| <= 2^-22 |x|.
+__device__ __forceinline__ void split_tf32(float4 x, float4& hi, float4& lo) {
+    hi.x = tf32_rna(x.x);
+    hi.y = tf32_rna(x.y);
+    hi.z = tf32_rna(x.z);
+    hi.w = tf32_rna(x.w);
+    lo.x = tf32_rna(x.x - hi.x);
+    lo.y = tf32_rna(x.y - hi.y);
+    lo.z = tf32_rna(x.z - hi.z);
+    lo.w = tf32_rna(x.w - hi.w);
+}
+
+// Byte offset of (row r, k-quad kq) inside one operand slab (K-major, no swizzle).
+__device__ __forceinline__ uint32_t slab_off(int r, int kq) {
+    return (uint32_t)((r >> 3) * kSBO + kq * kLBO + (r & 7) * 16);
+}
+
+// Element e of a chunk's float4 grid -> (row r, k-quad kq).  Eight consecutive threads
+// take eight consecutive rows of one k-quad, so each 8-thread shared-memory store
+// phase writes 128 contiguous bytes (no bank conflicts); a warp reads 64 contiguous
+// bytes from each of 8 rows in global memory.
+__device__ __forceinline__ void chunk_coord(int e, int& r, int& kq) {
+    constexpr int KQ = kKC / 4;
+    const int w = e % (8 * KQ);
+    r = (e / (8 * KQ)) * 8 + (w & 7);
+    kq = w >> 3;
+}
+
+// grid.x = ntiles * mgroups (row group fastest).  tiles[t] = (op, first pair, count, 0).
+template <int SLABS, int N>
+__global__ void __launch_bounds__(kThreads, 1)
+k_pair_tc(const float* __restrict__ ops, int Q, int Qp, int mgroups, const int4* __restrict__ tiles,
+          const int* __restrict__ pin, const int* __restrict__ pout, const float* __restrict__ in,
+          float* __restrict__ out, int* __restrict__ err) {
+    using S = Shape<SLABS, N>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    __shared__ uint64_t bars[2];          // one per accumulator buffer (and smem stage)
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_in[N], s_out[N];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile_id = blockIdx.x / mgroups, mg = blockIdx.x % mgroups;
+    const int4 t = tiles[tile_id];
+    const float* Op = ops + (size_t)t.x * Qp * Qp;
+    const int cnt = t.z;
+    const int m0 = mg * S::kRows;
+
+    for (int j = tid; j < N; j += kThreads) {
+        s_in[j] = j < cnt ? pin[t.y + j] : -1;
+        s_out[j] = j < cnt ? pout[t.y + j] : -1;
+    }
+    if (tid == 0) {
+        s_abort = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(S::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_tf32(128, N);
+
+    // this warp's accumulator columns: lane quarter q, slab my_slab, columns [my_col0, +128)
+    const int quarter = warp & 3, half = warp >> 2;
+    const int my_slab = (half * 128) / N, my_col0 = (half * 128) % N;
+    float acc[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+
+    float4 ra[S::kAVec], rb[S::kBVec];
+    auto load_chunk = [&](int c) {
+        const int k0 = c * kKC;
+#pragma unroll
+        for (int i = 0; i < S::kAVec; ++i) {
+            int r, kq;
+            chunk_coord(tid + i * kThreads, r, kq);
+            int row = m0 + r, k = k0 + 4 * kq;   // a k-quad lies wholly inside or outside Qp
+            ra[i] = (row < Qp && k < Qp) ? *reinterpret_cast<const float4*>(Op + (size_t)row * Qp + k)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < S::kBVec; ++i) {
+            int r, kq;
+            chunk_coord(tid + i * kThreads, r, kq);
+            int bi = s_in[r], k = k0 + 4 * kq;
+            rb[i] = (bi >= 0 && k < Qp) ? *reinterpret_cast<const float4*>(in + (size_t)bi * Qp + k)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store_chunk = [&](unsigned char* sb) {
+#pragma unroll
+        for (int i = 0; i < S::kAVec; ++i) {
+            int r, kq;
+            chunk_coord(tid + i * kThreads, r, kq);
+            uint32_t o = (uint32_t)((r >> 7) * kSlabBytes) + slab_off(r & 127, kq);
+            float4 hi, lo;
+            split_tf32(ra[i], hi, lo);
+            *reinterpret_cast<float4*>(sb + o) = hi;
+            *reinterpret_cast<float4*>(sb + S::kABytes + o) = lo;
+        }
+#pragma unroll
+        for (int i = 0; i < S::kBVec; ++i) {
+            int r, kq;
+            chunk_coord(tid + i * kThreads, r, kq);
+            uint32_t o = (uint32_t)((r >> 7) * kSlabBytes) + slab_off(r & 127, kq);
+            float4 hi, lo;
+            split_tf32(rb[i], hi, lo);
+            *reinterpret_cast<float4*>(sb + 2 * S::kABytes + o) = hi;
+            *reinterpret_cast<float4*>(sb + 2 * S::kABytes + S::kBBytes + o) = lo;
+        }
+    };
+    // fold accumulator buffer b into the registers
+    auto fold = [&](int b) {
+        const uint32_t col = (uint32_t)(b * S::kBufCols + my_slab * N + my_col0);
+#pragma unroll
+        for (int j0 = 0; j0 < 128; j0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)j0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j0 + j] += v[j];
+        }
+    };
+
+    const int nchunks = (Qp + kKC - 1) / kKC;  // Qp is a multiple of 16; the tail is zero-filled
+    int issued = -1;               // last chunk whose MMAs were issued and committed (uniform)
+    load_chunk(0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        unsigned char* sb = base + b * S::kStageBytes;
+        // stage b and accumulator buffer b were last used by chunk c - 2, whose MMAs were
+        // waited for and whose buffer was folded in the previous iteration
+        store_chunk(sb);
+        if (c + 1 < nchunks) load_chunk(c + 1);   // in flight while this chunk multiplies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a_hi = smem_u32(sb), a_lo = a_hi + S::kABytes;
+            const uint32_t b_hi = a_hi + 2 * S::kABytes, b_lo = b_hi + S::kBBytes;
+#pragma unroll
+            for (int sl = 0; sl < SLABS; ++sl) {
+                const uint32_t d = tmem + (uint32_t)(b * S::kBufCols + sl * N);
+                const uint32_t ao = (uint32_t)(sl * kSlabBytes);
+                // small correction products first, then the hi*hi products
+#pragma unroll
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+                    const uint32_t koff = ks * 2 * kLBO;  // 8 TF32 = two core matrices along K
+                    mma_tf32(d, smem_desc(a_hi + ao + koff), smem_desc(b_lo + koff), idesc, ks > 0 ? 1u : 0u);
+                    mma_tf32(d, smem_desc(a_lo + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
+                }
+#pragma unroll
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+                    const uint32_t koff = ks * 2 * kLBO;
+                    mma_tf32(d, smem_desc(a_hi + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
+                }
+            }
+            mma_commit(&bars[b]);
+        }
+        issued = c;
+        if (c >= 1) {
+            const int pc = c - 1;
+            if (tid == 0) s_abort = mbar_wait(&bars[pc & 1], (uint32_t)((pc >> 1) & 1)) ? 0 : 1;
+            __syncthreads();
+            if (s_abort) break;
+            tc_fence_after();
+            fold(pc & 1);
+            tc_fence_before();
+        }
+    }
+    // the last chunk
+    if (tid == 0 && !s_abort) {
+        const int pc = issued;
+        if (pc >= 0 && !mbar_wait(&bars[pc & 1], (uint32_t)((pc >> 1) & 1))) s_abort = 2;
+    }
+    __syncthreads();
+    if (!s_abort) {
+        tc_fence_after();
+        fold(issued & 1);
+        const int row = m0 + my_slab * 128 + quarter * 32 + lane;
+        if (row < Q) {
+#pragma unroll
+            for (int j = 0; j < 128; ++j) {
+                int ob = s_out[my_col0 + j];
+                if (ob >= 0) atomicAdd(out + (size_t)ob * Qp + row, acc[j]);
+            }
+        }
+    } else if (tid == 0) {
+        // a wait gave up: one more bounded wait for the MMAs in flight, then report
+        if (issued >= 0) mbar_wait(&bars[issued & 1], (uint32_t)((issued >> 1) & 1));
+        atomicOr(err, s_abort);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols)
+                     : "memory");
+    }
+}
+
+}  // namespace tc
+}  // namespace kifmm

@@ -45,6 +45,8 @@ struct Plan {
     int64_t n_xpairs = 0;
     PairTiles u2u, m2l, l2l;
     int max_trg_leaf = 0;
+    int tile_cap = kPairTile;       // pairs per translation tile
+    DBuf<int> err;                  // device error word (bounded waits that gave up)
 
     // per-matvec buffers
     DBuf<double> u_d, d_d, res_d, q_d;

@@ -76,6 +76,7 @@ def test_fmm_matches_oracle(geom, kernel, prec, p, tol):
     plan = Plan(tree, kernel=kernel, p=p, precision=prec, src_nrm=nrm, trg_nrm=nrm)
     q = torch.from_numpy(sig).to(DEV) * w
     out = plan.matvec(q).cpu().numpy()
+    plan.check()                                   # no bounded device wait gave up
     err = rel(out, refs[kernel])
     print("%s %s %s p=%d rel-L2 %.3e" % (geom, kernel, prec, p, err))
     assert err < tol
