@@ -272,8 +272,31 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rate on GB300
+
+
+def _kernel_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1605_01715_gb300", "csrc", "pair_tc.cuh")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _m2l_traffic(pairs):
+    """DRAM bytes per M2L launch from the committed ncu record, if it is for this kernel source."""
+    path = os.path.join(ROOT, "profiles", "m2l_tc_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("kernel_sha") != _kernel_sha():
+        return None
+    return rec["dram_bytes_per_pair"] * pairs + rec["dram_bytes_fixed"]
+
+
 def roofline(phases, st, tst, args):
-    """Roofline of the dominant phase, from algorithmic work per launch and live event times."""
+    """Roofline of the dominant kernel from algorithmic work per launch and live event times."""
     pk, src = _peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0) * 1e6
     fp32_peak = 152 * 128 * 2 * sm_max / 1e12       # TFLOP/s, CUDA-core FMA at max SM clock
@@ -283,18 +306,28 @@ def roofline(phases, st, tst, args):
     dom = max(items, key=items.get)
     t = items[dom] * 1e-3
     mixed = args.precision == "mixed"
-    if dom in ("m2l_x", "u2u", "l2l"):
-        pairs = {"m2l_x": st["m2l_pairs"], "u2u": st["u2u_pairs"], "l2l": st["l2l_pairs"]}[dom]
-        flops = 2.0 * Q * Q * pairs
-        peak = fp32_peak if mixed else fp64_peak
-        return {"kernel": "k_pair_gemm (%s)" % dom, "bound": "alu", "achieved": flops / t / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
-                "peak_source": "152 SM x 128 FP32 lanes x 2 x %.0f MHz" % (sm_max / 1e6) if mixed else "FP64 nominal"}
+    if dom in ("m2l", "u2u", "l2l"):
+        pairs = {"m2l": st["m2l_pairs"], "u2u": st["u2u_pairs"], "l2l": st["l2l_pairs"]}[dom]
+        flops = 2.0 * Q * Q * pairs                  # algorithmic: one Q x Q operator per pair
+        if mixed:                                   # 3xTF32 on tcgen05: FP32-equivalent = TF32 / 3
+            peak = pk["bf16_tflops"] * TF32_PER_BF16 / 3.0
+            out = {"kernel": "k_pair_tc (%s, tcgen05 3xTF32)" % dom, "bound": "tensor",
+                   "peak_source": "%s bf16 burst %.0f x nominal TF32/BF16 %.3f / 3 (3xTF32)"
+                                  % (src, pk["bf16_tflops"], TF32_PER_BF16)}
+        else:
+            peak = fp64_peak
+            out = {"kernel": "k_%s_gemm<double>" % dom, "bound": "alu", "peak_source": "FP64 nominal"}
+        out.update({"achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "frac": flops / t / 1e12 / peak,
+                    "traffic": _m2l_traffic(pairs) if (mixed and dom == "m2l") else None,
+                    "work": "2*Q^2 flops x %d pairs, Q=%d" % (pairs, Q)})
+        return out
     if dom == "p2p":
         flops = 20.0 * tst["p2p_pairs"]            # ~20 FP32 ops per pair (FMA counted as 2)
         peak = fp32_peak if mixed else fp64_peak
         return {"kernel": "k_p2p", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None}
+                "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
+                "peak_source": "152 SM x 128 FP32 lanes x 2 x %.0f MHz" % (sm_max / 1e6)}
     if dom == "d2t":
         nbytes = (4 if mixed else 8) * (st["q_points"] + 8) * tst["n_src"]
         return {"kernel": "k_d2t", "bound": "hbm", "achieved": nbytes / t / 1e9, "peak": pk["hbm_gbs"],

@@ -172,8 +172,8 @@ int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);
 /*
  * Per-phase device times (milliseconds).  While enabled, every matvec records CUDA
  * events between its phases on its stream (no host synchronization).  A call with
- * phases != NULL (host, >= 8 doubles) waits for the recorded events and returns the
- * mean per matvec since the previous read: {gather, s2u, u2u, m2l+x, l2l, d2t, p2p,
+ * phases != NULL (host, >= 9 doubles) waits for the recorded events and returns the
+ * mean per matvec since the previous read: {gather, s2u, u2u, x, m2l, l2l, d2t, p2p,
  * total}; then recording is switched on (enable != 0) or off.
  */
 int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases);

@@ -239,9 +239,9 @@ class Plan:
         return _as_dict(st)
 
     def profile(self, enable=True):
-        ph = (ctypes.c_double * 8)()
+        ph = (ctypes.c_double * 9)()
         _check(lib().kifmm_plan_profile(self.handle, int(enable), ph))
-        names = ["gather", "s2u", "u2u", "m2l_x", "l2l", "d2t", "p2p", "total"]
+        names = ["gather", "s2u", "u2u", "x", "m2l", "l2l", "d2t", "p2p", "total"]
         return dict(zip(names, list(ph)))
 
     def bie_apply(self, area, eps_in, eps_out, curv, x, y=None, stream=None):

@@ -22,8 +22,10 @@
 namespace kifmm {
 
 int tc_tile_pairs(int Qp);
-int launch_pair_tc(const float* ops, int Q, int Qp, const int4* tiles, int ntiles, const int* pin, const int* pout,
-                   const float* in, float* out, int* err, cudaStream_t s);
+int tc_split_table(float* table, float* lo, size_t n, cudaStream_t s);
+int tc_make_map(CUtensorMap* map, const float* table, int nops, int Qp);
+int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int Q, int Qp, const int4* tiles,
+                   int ntiles, const int* pin, const int* pout, const float* in, float* out, int* err, cudaStream_t s);
 
 namespace {
 
@@ -537,6 +539,17 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_CHECK_CUDA(cudaMemsetAsync(P.m2l_f.p, 0, P.m2l_f.bytes(), s));
         KF_CHECK_CUDA(cudaMemsetAsync(P.l2l_f.p, 0, P.l2l_f.bytes(), s));
         KF_TRY(build_ops<float>(P, h, P.m2m_f.p, P.m2l_f.p, P.l2l_f.p, s));
+        // TF32 hi/lo split of every table and the TMA maps the tensor-core GEMM reads
+        DBuf<float>* hi[3] = {&P.m2m_f, &P.m2l_f, &P.l2l_f};
+        DBuf<float>* lo[3] = {&P.m2m_lo, &P.m2l_lo, &P.l2l_lo};
+        const int nops[3] = {8, kNumOffsets, 8};
+        for (int f = 0; f < 3; ++f) {
+            KF_TRY(lo[f]->alloc(hi[f]->n));
+            KF_TRY(tc_split_table(hi[f]->p, lo[f]->p, hi[f]->n, s));
+            KF_TRY(tc_make_map(&P.tmaps[f][0], hi[f]->p, nops[f], P.Qp));
+            KF_TRY(tc_make_map(&P.tmaps[f][1], lo[f]->p, nops[f], P.Qp));
+        }
+        KF_CHECK_CUDA(cudaStreamSynchronize(s));
     }
 
     // work lists (host bookkeeping over the tree's lists)
@@ -658,7 +671,8 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     for (size_t b : {P.m2m_d.bytes(), P.m2l_d.bytes(), P.l2l_d.bytes(), P.d2t_d.bytes(), P.m2m_f.bytes(),
                      P.m2l_f.bytes(), P.l2l_f.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
                      P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
-                     P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes()})
+                     P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(), P.m2m_lo.bytes(),
+                     P.m2l_lo.bytes(), P.l2l_lo.bytes()})
         P.device_bytes += (int64_t)b;
     return KIFMM_OK;
 }
@@ -679,9 +693,12 @@ int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, con
 template <>
 int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const float* ops,
                      const float* in, float* out, cudaStream_t s, int& launches) {
-    (void)which;
+
     if (t1 <= t0) return KIFMM_OK;
-    KF_TRY(launch_pair_tc(ops, P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p, pt.pout.p, in, out, P.err.p, s));
+    (void)ops;  // the tensor-core path reads the split tables through their TMA maps
+    const CUtensorMap* m = P.tmaps[which];
+    KF_TRY(launch_pair_tc(which, m[0], m[1], P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p, pt.pout.p, in, out,
+                          P.err.p, s));
     ++launches;
     return KIFMM_OK;
 }
@@ -707,7 +724,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     cudaEvent_t* slot = nullptr;
     if (P.profile) {
         if (P.slots_used == (int)P.ev_slots.size() && P.ev_slots.size() < 4096) {
-            std::vector<cudaEvent_t> e(8, nullptr);
+            std::vector<cudaEvent_t> e(kPhaseEvents, nullptr);
             for (auto& x : e) KF_CHECK_CUDA(cudaEventCreate(&x));
             P.ev_slots.push_back(e);
         }
@@ -757,8 +774,9 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         KF_CHECK_LAUNCH();
         ++launches;
     }
-    KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, s, launches));
     KF_TRY(mark(4));
+    KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, s, launches));
+    KF_TRY(mark(5));
     // L2L, coarsest children first (ADL: each level's potentials shifted to zero mean first)
     const bool center = P.kernel == KIFMM_KERNEL_ADL;
     for (int l = 2; l < T.nlev; ++l) {
@@ -772,13 +790,13 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
             ++launches;
         }
     }
-    KF_TRY(mark(5));
+    KF_TRY(mark(6));
     if (P.n_tleaf) {
         k_d2t<Real><<<P.n_tleaf, 128, P.Qp * sizeof(Real), s>>>(P.tleaf.p, T.rng.p, B.d2t, B.d, P.Qp, B.res);
         KF_CHECK_LAUNCH();
         ++launches;
     }
-    KF_TRY(mark(6));
+    KF_TRY(mark(7));
     if (P.n_tleaf) {
         int threads = std::min(256, std::max(32, (P.max_trg_leaf + 31) / 32 * 32));
         size_t smem = 6 * threads * sizeof(Real);
@@ -795,7 +813,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         KF_CHECK_LAUNCH();
         ++launches;
     }
-    KF_TRY(mark(7));
+    KF_TRY(mark(8));
     P.launches = launches;
     return KIFMM_OK;
 }
@@ -883,21 +901,22 @@ extern "C" int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases) {
     Plan& P = plan->P;
     if (phases) {
         // mean over the matvecs recorded since the last read:
-        // {gather, s2u, u2u, m2l+x, l2l, d2t, p2p, total}
-        for (int i = 0; i < 8; ++i) phases[i] = 0;
+        // {gather, s2u, u2u, x, m2l, l2l, d2t, p2p, total}
+        constexpr int L = kPhaseEvents - 1;
+        for (int i = 0; i <= L; ++i) phases[i] = 0;
         for (int k = 0; k < P.slots_used; ++k) {
             const std::vector<cudaEvent_t>& e = P.ev_slots[k];
-            KF_CHECK_CUDA(cudaEventSynchronize(e[7]));
+            KF_CHECK_CUDA(cudaEventSynchronize(e[L]));
             float ms;
-            for (int i = 0; i < 7; ++i) {
+            for (int i = 0; i < L; ++i) {
                 KF_CHECK_CUDA(cudaEventElapsedTime(&ms, e[i], e[i + 1]));
                 phases[i] += ms;
             }
-            KF_CHECK_CUDA(cudaEventElapsedTime(&ms, e[0], e[7]));
-            phases[7] += ms;
+            KF_CHECK_CUDA(cudaEventElapsedTime(&ms, e[0], e[L]));
+            phases[L] += ms;
         }
         if (P.slots_used)
-            for (int i = 0; i < 8; ++i) phases[i] /= P.slots_used;
+            for (int i = 0; i <= L; ++i) phases[i] /= P.slots_used;
         P.slots_used = 0;
     }
     P.profile = enable != 0;

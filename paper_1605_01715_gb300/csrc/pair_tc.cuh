@@ -15,13 +15,15 @@
 // the hi*hi products) in one of two TMEM buffers, and the threads fold every chunk's
 // partial into FP32 registers (round-to-nearest) while the next chunk multiplies.
 //
-// Shared-memory operands use the canonical K-major layout without swizzle: 8-row x
-// 16-byte core matrices; core matrices adjacent in K are kLBO = 128 B apart, adjacent
-// 8-row groups kSBO = (KC/4)*128 B apart.  Every mbarrier wait is bounded; on a
-// timeout the CTA records an error, waits (bounded) once more, frees its TMEM and
-// returns without writing.
+// Operands: the operator rows come pre-split (hi and lo tables) by TMA, one 32-column
+// box per table and chunk, into the canonical K-major 128-byte-swizzled layout (rows
+// of 128 B, 16-byte chunks XOR-permuted by row within 1024-byte atoms); the gathered
+// input vectors are split by the threads and stored in the same layout.  Every
+// mbarrier wait is bounded; on a timeout the CTA records an error, waits (bounded)
+// once more for work in flight, frees its TMEM and returns without writing.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,9 +32,10 @@ namespace tc {
 
 constexpr int kKC = 32;             // K elements per pipeline stage (4 MMA k-steps)
 constexpr int kThreads = 256;
-constexpr uint32_t kLBO = 128;                   // bytes between K-adjacent core matrices
-constexpr uint32_t kSBO = (kKC / 4) * 128;       // bytes between 8-row groups
-constexpr int kSlabBytes = 128 * kKC * 4;        // one 128-row operand slab of one chunk: 8 KB
+constexpr uint32_t kRowBytes = kKC * 4;          // 128 B: one swizzle row
+constexpr uint32_t kSBO = 8 * kRowBytes;         // 1024 B between 8-row groups
+constexpr int kSlabBytes = 128 * kKC * 4;        // one 128-row operand slab of one chunk: 16 KB
+static_assert(kRowBytes == 128, "the 128-byte swizzle needs 32 TF32 per row");
 constexpr long long kSpinLimit = 1LL << 26;
 
 // Tile shape: SLABS x 128 operator rows by N pairs; two accumulator buffers fill the
@@ -48,7 +51,6 @@ struct Shape {
     static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
     static constexpr int kStages = 2;
     static constexpr int kSmemBytes = kStages * kStageBytes + 1024;
-    static constexpr int kAVec = kRows * (kKC / 4) / kThreads;   // float4 of A per thread per chunk
     static constexpr int kBVec = N * (kKC / 4) / kThreads;       // float4 of B per thread per chunk
     static_assert(2 * SLABS * N == 512, "two accumulator buffers fill TMEM");
     static_assert(N % 128 == 0 && N <= 256, "N must be 128 or 256");
@@ -58,14 +60,31 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// K-major, 128-byte swizzle: 8-row groups kSBO apart, leading offset unused (1),
+// descriptor version 1, layout type 2 (SWIZZLE_128B).  Tiles are 1024-byte aligned;
+// a K step inside the 128-byte row advances the start address by 32 bytes.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)1 << 16;
     d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    // base offset 0, LBO mode 0, layout type 0 (no swizzle)
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 2-D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // kind::tf32 instruction descriptor: D FP32, A/B TF32, both K-major, M x N.
@@ -163,32 +182,36 @@ __device__ __forceinline__ void split_tf32(float4 x, float4& hi, float4& lo) {
     lo.w = tf32_rna(x.w - hi.w);
 }
 
-// Byte offset of (row r, k-quad kq) inside one operand slab (K-major, no swizzle).
-__device__ __forceinline__ uint32_t slab_off(int r, int kq) {
-    return (uint32_t)((r >> 3) * kSBO + kq * kLBO + (r & 7) * 16);
+// Byte offset of (row r, 16-byte chunk c) in a K-major 128-byte-swizzled tile.
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
+    return (uint32_t)(r * kRowBytes + ((c ^ (r & 7)) << 4));
 }
 
-// Element e of a chunk's float4 grid -> (row r, k-quad kq).  Eight consecutive threads
-// take eight consecutive rows of one k-quad, so each 8-thread shared-memory store
-// phase writes 128 contiguous bytes (no bank conflicts); a warp reads 64 contiguous
-// bytes from each of 8 rows in global memory.
-__device__ __forceinline__ void chunk_coord(int e, int& r, int& kq) {
+// Element e of a chunk's float4 grid -> (row r, chunk c).  Eight consecutive threads
+// take eight consecutive rows of one chunk: after the swizzle their 16-byte stores
+// hit eight different bank groups; a warp reads 64 contiguous bytes from each of 8
+// rows in global memory.
+__device__ __forceinline__ void chunk_coord(int e, int& r, int& c) {
     constexpr int KQ = kKC / 4;
     const int w = e % (8 * KQ);
     r = (e / (8 * KQ)) * 8 + (w & 7);
-    kq = w >> 3;
+    c = w >> 3;
 }
 
 // grid.x = ntiles * mgroups (row group fastest).  tiles[t] = (op, first pair, count, 0).
+// map_hi / map_lo: 2-D tensor maps of the split operator tables, rows = op * Qp + row,
+// box = 32 columns x kRows rows, 128-byte swizzle.
 template <int SLABS, int N>
-__global__ void __launch_bounds__(kThreads, 1)
-k_pair_tc(const float* __restrict__ ops, int Q, int Qp, int mgroups, const int4* __restrict__ tiles,
-          const int* __restrict__ pin, const int* __restrict__ pout, const float* __restrict__ in,
-          float* __restrict__ out, int* __restrict__ err) {
+__device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CUtensorMap& map_lo, int Q, int Qp,
+                                             int mgroups, const int4* __restrict__ tiles,
+                                             const int* __restrict__ pin, const int* __restrict__ pout,
+                                             const float* __restrict__ in, float* __restrict__ out,
+                                             int* __restrict__ err) {
     using S = Shape<SLABS, N>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    __shared__ uint64_t bars[2];          // one per accumulator buffer (and smem stage)
+    __shared__ uint64_t full_bar[2];      // TMA of stage s landed
+    __shared__ uint64_t mma_bar[2];       // MMAs of accumulator buffer b (and stage b) done
     __shared__ uint32_t tmem_base;
     __shared__ int s_in[N], s_out[N];
     __shared__ int s_abort;
@@ -196,19 +219,31 @@ k_pair_tc(const float* __restrict__ ops, int Q, int Qp, int mgroups, const int4*
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile_id = blockIdx.x / mgroups, mg = blockIdx.x % mgroups;
     const int4 t = tiles[tile_id];
-    const float* Op = ops + (size_t)t.x * Qp * Qp;
     const int cnt = t.z;
     const int m0 = mg * S::kRows;
+    const int arow = t.x * Qp + m0;       // first operator row of this CTA in the table
+    const int nchunks = (Qp + kKC - 1) / kKC;  // Qp is a multiple of 16; the tail is zero-filled
 
     for (int j = tid; j < N; j += kThreads) {
         s_in[j] = j < cnt ? pin[t.y + j] : -1;
         s_out[j] = j < cnt ? pout[t.y + j] : -1;
     }
+    auto stage_base = [&](int st) -> unsigned char* { return base + st * S::kStageBytes; };
+    auto issue_tma = [&](int c) {
+        unsigned char* sb = stage_base(c & 1);
+        mbar_expect_tx(&full_bar[c & 1], 2u * S::kABytes);
+        tma_load_2d(smem_u32(sb), &map_hi, c * kKC, arow, &full_bar[c & 1]);
+        tma_load_2d(smem_u32(sb + S::kABytes), &map_lo, c * kKC, arow, &full_bar[c & 1]);
+    };
     if (tid == 0) {
         s_abort = 0;
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full_bar[i], 1);
+            mbar_init(&mma_bar[i], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        issue_tma(0);
+        if (nchunks > 1) issue_tma(1);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -229,49 +264,31 @@ k_pair_tc(const float* __restrict__ ops, int Q, int Qp, int mgroups, const int4*
 #pragma unroll
     for (int j = 0; j < 128; ++j) acc[j] = 0.f;
 
-    float4 ra[S::kAVec], rb[S::kBVec];
-    auto load_chunk = [&](int c) {
+    float4 rb[S::kBVec];
+    auto load_b = [&](int c) {
         const int k0 = c * kKC;
 #pragma unroll
-        for (int i = 0; i < S::kAVec; ++i) {
-            int r, kq;
-            chunk_coord(tid + i * kThreads, r, kq);
-            int row = m0 + r, k = k0 + 4 * kq;   // a k-quad lies wholly inside or outside Qp
-            ra[i] = (row < Qp && k < Qp) ? *reinterpret_cast<const float4*>(Op + (size_t)row * Qp + k)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
         for (int i = 0; i < S::kBVec; ++i) {
-            int r, kq;
-            chunk_coord(tid + i * kThreads, r, kq);
-            int bi = s_in[r], k = k0 + 4 * kq;
+            int r, ch;
+            chunk_coord(tid + i * kThreads, r, ch);
+            int bi = s_in[r], k = k0 + 4 * ch;   // a k-quad lies wholly inside or outside Qp
             rb[i] = (bi >= 0 && k < Qp) ? *reinterpret_cast<const float4*>(in + (size_t)bi * Qp + k)
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
-    auto store_chunk = [&](unsigned char* sb) {
-#pragma unroll
-        for (int i = 0; i < S::kAVec; ++i) {
-            int r, kq;
-            chunk_coord(tid + i * kThreads, r, kq);
-            uint32_t o = (uint32_t)((r >> 7) * kSlabBytes) + slab_off(r & 127, kq);
-            float4 hi, lo;
-            split_tf32(ra[i], hi, lo);
-            *reinterpret_cast<float4*>(sb + o) = hi;
-            *reinterpret_cast<float4*>(sb + S::kABytes + o) = lo;
-        }
+    auto store_b = [&](unsigned char* sb) {
+        unsigned char* bh = sb + 2 * S::kABytes;
 #pragma unroll
         for (int i = 0; i < S::kBVec; ++i) {
-            int r, kq;
-            chunk_coord(tid + i * kThreads, r, kq);
-            uint32_t o = (uint32_t)((r >> 7) * kSlabBytes) + slab_off(r & 127, kq);
+            int r, ch;
+            chunk_coord(tid + i * kThreads, r, ch);
+            uint32_t o = sw128_off(r, ch);
             float4 hi, lo;
             split_tf32(rb[i], hi, lo);
-            *reinterpret_cast<float4*>(sb + 2 * S::kABytes + o) = hi;
-            *reinterpret_cast<float4*>(sb + 2 * S::kABytes + S::kBBytes + o) = lo;
+            *reinterpret_cast<float4*>(bh + o) = hi;
+            *reinterpret_cast<float4*>(bh + S::kBBytes + o) = lo;
         }
     };
-    // fold accumulator buffer b into the registers
     auto fold = [&](int b) {
         const uint32_t col = (uint32_t)(b * S::kBufCols + my_slab * N + my_col0);
 #pragma unroll
@@ -283,46 +300,62 @@ k_pair_tc(const float* __restrict__ ops, int Q, int Qp, int mgroups, const int4*
         }
     };
 
-    const int nchunks = (Qp + kKC - 1) / kKC;  // Qp is a multiple of 16; the tail is zero-filled
-    int issued = -1;               // last chunk whose MMAs were issued and committed (uniform)
-    load_chunk(0);
+    // thread 0 bookkeeping: last chunk whose MMAs were committed, last chunk whose TMA
+    // was issued / waited for, and whether a wait gave up
+    int issued = -1, tma_issued = nchunks > 1 ? 1 : 0, tma_waited = -1;
+    bool dead = false;
+    load_b(0);
     for (int c = 0; c < nchunks; ++c) {
         const int b = c & 1;
-        unsigned char* sb = base + b * S::kStageBytes;
-        // stage b and accumulator buffer b were last used by chunk c - 2, whose MMAs were
-        // waited for and whose buffer was folded in the previous iteration
-        store_chunk(sb);
-        if (c + 1 < nchunks) load_chunk(c + 1);   // in flight while this chunk multiplies
+        unsigned char* sb = stage_base(b);
+        // stage b / accumulator buffer b were last used by chunk c - 2: waited for and
+        // folded in the previous iteration
+        store_b(sb);
+        if (c + 1 < nchunks) load_b(c + 1);       // in flight while this chunk multiplies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
         __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a_hi = smem_u32(sb), a_lo = a_hi + S::kABytes;
-            const uint32_t b_hi = a_hi + 2 * S::kABytes, b_lo = b_hi + S::kBBytes;
+        if (tid == 0 && !dead) {
+            if (!mbar_wait(&full_bar[b], (uint32_t)((c >> 1) & 1))) {
+                dead = true;
+                s_abort = 1;
+            } else {
+                tma_waited = c;
+                tc_fence_after();
+                const uint32_t a_hi = smem_u32(sb), a_lo = a_hi + S::kABytes;
+                const uint32_t b_hi = a_hi + 2 * S::kABytes, b_lo = b_hi + S::kBBytes;
 #pragma unroll
-            for (int sl = 0; sl < SLABS; ++sl) {
-                const uint32_t d = tmem + (uint32_t)(b * S::kBufCols + sl * N);
-                const uint32_t ao = (uint32_t)(sl * kSlabBytes);
-                // small correction products first, then the hi*hi products
+                for (int sl = 0; sl < SLABS; ++sl) {
+                    const uint32_t d = tmem + (uint32_t)(b * S::kBufCols + sl * N);
+                    const uint32_t ao = (uint32_t)(sl * kSlabBytes);
+                    // small correction products first, then the hi*hi products
 #pragma unroll
-                for (int ks = 0; ks < kKC / 8; ++ks) {
-                    const uint32_t koff = ks * 2 * kLBO;  // 8 TF32 = two core matrices along K
-                    mma_tf32(d, smem_desc(a_hi + ao + koff), smem_desc(b_lo + koff), idesc, ks > 0 ? 1u : 0u);
-                    mma_tf32(d, smem_desc(a_lo + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
+                    for (int ks = 0; ks < kKC / 8; ++ks) {
+                        const uint32_t koff = ks * 32;  // 8 TF32 along K inside the swizzled row
+                        mma_tf32(d, smem_desc(a_hi + ao + koff), smem_desc(b_lo + koff), idesc, ks > 0 ? 1u : 0u);
+                        mma_tf32(d, smem_desc(a_lo + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
+                    }
+#pragma unroll
+                    for (int ks = 0; ks < kKC / 8; ++ks) {
+                        const uint32_t koff = ks * 32;
+                        mma_tf32(d, smem_desc(a_hi + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
+                    }
                 }
-#pragma unroll
-                for (int ks = 0; ks < kKC / 8; ++ks) {
-                    const uint32_t koff = ks * 2 * kLBO;
-                    mma_tf32(d, smem_desc(a_hi + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
-                }
+                mma_commit(&mma_bar[b]);
+                issued = c;
             }
-            mma_commit(&bars[b]);
         }
-        issued = c;
         if (c >= 1) {
             const int pc = c - 1;
-            if (tid == 0) s_abort = mbar_wait(&bars[pc & 1], (uint32_t)((pc >> 1) & 1)) ? 0 : 1;
+            if (tid == 0 && !dead) {
+                if (!mbar_wait(&mma_bar[pc & 1], (uint32_t)((pc >> 1) & 1))) {
+                    dead = true;
+                    s_abort = 1;
+                } else if (c + 1 < nchunks) {
+                    issue_tma(c + 1);              // its stage was read by chunk c - 1, now done
+                    tma_issued = c + 1;
+                }
+            }
             __syncthreads();
             if (s_abort) break;
             tc_fence_after();
@@ -331,14 +364,16 @@ k_pair_tc(const float* __restrict__ ops, int Q, int Qp, int mgroups, const int4*
         }
     }
     // the last chunk
-    if (tid == 0 && !s_abort) {
-        const int pc = issued;
-        if (pc >= 0 && !mbar_wait(&bars[pc & 1], (uint32_t)((pc >> 1) & 1))) s_abort = 2;
+    if (tid == 0 && !dead) {
+        if (issued != nchunks - 1 || !mbar_wait(&mma_bar[issued & 1], (uint32_t)((issued >> 1) & 1))) {
+            dead = true;
+            s_abort = 2;
+        }
     }
     __syncthreads();
     if (!s_abort) {
         tc_fence_after();
-        fold(issued & 1);
+        fold((nchunks - 1) & 1);          // uniform: every thread folds the last chunk's buffer
         const int row = m0 + my_slab * 128 + quarter * 32 + lane;
         if (row < Q) {
 #pragma unroll
@@ -348,8 +383,10 @@ k_pair_tc(const float* __restrict__ ops, int Q, int Qp, int mgroups, const int4*
             }
         }
     } else if (tid == 0) {
-        // a wait gave up: one more bounded wait for the MMAs in flight, then report
-        if (issued >= 0) mbar_wait(&bars[issued & 1], (uint32_t)((issued >> 1) & 1));
+        // a wait gave up: one more bounded wait for the work in flight, then report
+        if (issued >= 0) mbar_wait(&mma_bar[issued & 1], (uint32_t)((issued >> 1) & 1));
+        for (int ch = tma_waited + 1; ch <= tma_issued; ++ch)
+            mbar_wait(&full_bar[ch & 1], (uint32_t)((ch >> 1) & 1));
         atomicOr(err, s_abort);
     }
     tc_fence_before();
@@ -360,6 +397,21 @@ k_pair_tc(const float* __restrict__ ops, int Q, int Qp, int mgroups, const int4*
                      : "memory");
     }
 }
+
+// One kernel name per translation so profiles tell them apart.
+#define KF_TC_KERNEL(NAME)                                                                                    \
+    template <int SLABS, int N>                                                                               \
+    __global__ void __launch_bounds__(kThreads, 1)                                                            \
+        NAME(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int Q,   \
+             int Qp, int mgroups, const int4* __restrict__ tiles, const int* __restrict__ pin,                \
+             const int* __restrict__ pout, const float* __restrict__ in, float* __restrict__ out,             \
+             int* __restrict__ err) {                                                                          \
+        pair_tc_body<SLABS, N>(map_hi, map_lo, Q, Qp, mgroups, tiles, pin, pout, in, out, err);                \
+    }
+KF_TC_KERNEL(k_u2u_tc)
+KF_TC_KERNEL(k_m2l_tc)
+KF_TC_KERNEL(k_l2l_tc)
+#undef KF_TC_KERNEL
 
 }  // namespace tc
 }  // namespace kifmm

@@ -2,6 +2,8 @@
 // and check-potential buffers for one (tree, kernel, order, precision).
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace kifmm {
@@ -15,6 +17,7 @@ struct PairTiles {
 };
 
 constexpr int kPairTile = 64;
+constexpr int kPhaseEvents = 9;     // events per profiled matvec (8 phases + total)
 
 // Device scratch of the boundary-integral operators and GMRES, kept between calls
 // (the Krylov basis stays resident for the next solve on the same plan).
@@ -28,9 +31,13 @@ struct Plan {
     double cutoff = 0;
     bool fp64 = true;
 
-    // operators (Real = double for FP64, float for mixed), each Qp x Qp row-major
+    // operators (Real = double for FP64, float for mixed), each Qp x Qp row-major;
+    // mixed: the *_f tables hold the TF32 "hi" parts, *_lo the TF32 remainders, and
+    // tmaps[family][0 = hi, 1 = lo] their TMA tensor maps (family 0 M2M', 1 M2L', 2 L2L')
     DBuf<double> m2m_d, m2l_d, l2l_d, d2t_d;
     DBuf<float> m2m_f, m2l_f, l2l_f, d2t_f;
+    DBuf<float> m2m_lo, m2l_lo, l2l_lo;
+    CUtensorMap tmaps[3][2];
     DBuf<double> surf_d;            // Q x 3 unit surface
     DBuf<float> surf_f;
 

@@ -92,6 +92,20 @@ def test_benchmark_geometry_meets_1e6():
     assert rel(plan.matvec(q).cpu().numpy(), refs["dl"]) <= 1e-6
 
 
+@pytest.mark.parametrize("p,tol", [(4, 3e-3), (6, 3e-5), (8, 2e-6), (12, 1e-6)])
+def test_mixed_orders(p, tol):
+    """Every order in the mixed form (odd and even K-chunk counts of the tensor-core GEMM)."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    m, h, (xyz, w, nrm), sig, refs = case("sphere")
+    plan = Plan(Tree(xyz, max_leaf=40), kernel="sl", p=p, precision="mixed")
+    q = torch.from_numpy(sig).to(DEV) * w
+    out = plan.matvec(q).cpu().numpy()
+    plan.check()
+    err = rel(out, refs["sl"])
+    print("sphere sl mixed p=%d rel-L2 %.3e" % (p, err))
+    assert err < tol
+
+
 @pytest.mark.parametrize("max_leaf", [1, 7, 200])
 def test_leaf_sizes_and_repeat(max_leaf):
     """Extreme leaf capacities; a second matvec on the same plan gives the same answer."""
