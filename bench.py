@@ -250,6 +250,8 @@ def run_kifmm(args):
             "clocks": clk.summary()}
     line["roofline"] = roofline(phases, st, tst, args)
 
+    if args.solves > 0:
+        line["solve"] = solve_latency(args, device)
     if rank == 0 and not args.no_cpu_baseline:
         idx, ref, dt, cores = oracle_sample(wl, m, q.cpu().numpy(), args.cpu_sample)
         got = out.cpu().numpy()[idx]
@@ -261,6 +263,42 @@ def run_kifmm(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def solve_latency(args, device):
+    """p50/p99 wall time of full GMRES polarization solves (64-sphere pack, mixed matvec,
+    FP64 Krylov) with the plan, tree and Krylov basis resident between solves."""
+    import torch
+
+    from paper_1605_01715_gb300 import Plan, Tree, kifmm_polarization_rhs
+    wl, m, xyz, w, nrm, _ = make_inputs("polar_64", device)
+    n = m.n
+    eps = torch.from_numpy(wl["contrast"][m.body] * wl["eps_out"]).to(device)
+    curv = torch.from_numpy(1.0 / m.sph[:, 3]).to(device)
+    t0 = time.perf_counter()
+    tree = Tree(xyz, max_leaf=wl["max_leaf"])
+    plan = Plan(tree, kernel="adl", p=wl["p"], precision=args.precision, trg_nrm=nrm)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    b = kifmm_polarization_rhs(nrm, eps, wl["eps_out"], wl["e0"])
+    x = torch.zeros(n, dtype=torch.float64, device=device)
+    times, iters, rres = [], [], []
+    for k in range(args.solves + 1):          # the first solve warms up
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it, rr, rc = plan.bie_solve(w, eps, wl["eps_out"], curv, b, x=x, tol=1e-6, restart=50, max_iter=500)
+        torch.cuda.synchronize()
+        if k:
+            times.append((time.perf_counter() - t0) * 1e3)
+            iters.append(it)
+            rres.append(rr)
+    plan.check()
+    ts = np.array(times)
+    return {"workload": "polar_64", "n_unknowns": n, "tol": 1e-6, "restart": 50, "solves": len(times),
+            "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+            "iterations": int(np.median(iters)), "true_rel_residual": float(max(rres)),
+            "setup_ms": t_setup * 1e3, "ms_per_iteration": float(np.median(ts) / max(1, np.median(iters)))}
 
 
 def _peaks():
@@ -349,6 +387,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solves", type=int, default=5, help="timed polarization solves (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
