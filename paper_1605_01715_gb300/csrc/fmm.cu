@@ -22,10 +22,12 @@
 namespace kifmm {
 
 int tc_tile_pairs(int Qp);
-int tc_split_table(float* table, float* lo, size_t n, cudaStream_t s);
-int tc_make_map(CUtensorMap* map, const float* table, int nops, int Qp);
-int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int Q, int Qp, const int4* tiles,
-                   int ntiles, const int* pin, const int* pout, const float* in, float* out, int* err, cudaStream_t s);
+int tc_split_table(const float* table, __half* hi, __half* lo, size_t n, int* texp, cudaStream_t s);
+int tc_box_exp(const float* v, int Q, int Qp, int b0, int b1, int* e, cudaStream_t s);
+int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Qp);
+int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
+                   const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp, const float* in,
+                   float* out, int* err, cudaStream_t s);
 
 namespace {
 
@@ -539,17 +541,20 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_CHECK_CUDA(cudaMemsetAsync(P.m2l_f.p, 0, P.m2l_f.bytes(), s));
         KF_CHECK_CUDA(cudaMemsetAsync(P.l2l_f.p, 0, P.l2l_f.bytes(), s));
         KF_TRY(build_ops<float>(P, h, P.m2m_f.p, P.m2l_f.p, P.l2l_f.p, s));
-        // TF32 hi/lo split of every table and the TMA maps the tensor-core GEMM reads
-        DBuf<float>* hi[3] = {&P.m2m_f, &P.m2l_f, &P.l2l_f};
-        DBuf<float>* lo[3] = {&P.m2m_lo, &P.m2l_lo, &P.l2l_lo};
+        // scaled FP16 hi/lo split of every table and the TMA maps the tensor-core GEMM
+        // reads; the FP32 builds are not needed afterwards
+        DBuf<float>* f32[3] = {&P.m2m_f, &P.m2l_f, &P.l2l_f};
         const int nops[3] = {8, kNumOffsets, 8};
         for (int f = 0; f < 3; ++f) {
-            KF_TRY(lo[f]->alloc(hi[f]->n));
-            KF_TRY(tc_split_table(hi[f]->p, lo[f]->p, hi[f]->n, s));
-            KF_TRY(tc_make_map(&P.tmaps[f][0], hi[f]->p, nops[f], P.Qp));
-            KF_TRY(tc_make_map(&P.tmaps[f][1], lo[f]->p, nops[f], P.Qp));
+            KF_TRY(P.tab_h[f].alloc(f32[f]->n));
+            KF_TRY(P.tab_l[f].alloc(f32[f]->n));
+            KF_TRY(tc_split_table(f32[f]->p, P.tab_h[f].p, P.tab_l[f].p, f32[f]->n, &P.texp[f], s));
+            KF_TRY(tc_make_map(&P.tmaps[f][0], P.tab_h[f].p, nops[f], P.Qp));
+            KF_TRY(tc_make_map(&P.tmaps[f][1], P.tab_l[f].p, nops[f], P.Qp));
         }
         KF_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int f = 0; f < 3; ++f) f32[f]->release();
+        KF_TRY(P.bexp.alloc(T.nbox));
     }
 
     // work lists (host bookkeeping over the tree's lists)
@@ -671,8 +676,9 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     for (size_t b : {P.m2m_d.bytes(), P.m2l_d.bytes(), P.l2l_d.bytes(), P.d2t_d.bytes(), P.m2m_f.bytes(),
                      P.m2l_f.bytes(), P.l2l_f.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
                      P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
-                     P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(), P.m2m_lo.bytes(),
-                     P.m2l_lo.bytes(), P.l2l_lo.bytes()})
+                     P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(), P.tab_h[0].bytes(),
+                     P.tab_h[1].bytes(), P.tab_h[2].bytes(), P.tab_l[0].bytes(), P.tab_l[1].bytes(),
+                     P.tab_l[2].bytes(), P.bexp.bytes()})
         P.device_bytes += (int64_t)b;
     return KIFMM_OK;
 }
@@ -687,26 +693,29 @@ enum { kU2U = 0, kM2L = 1, kL2L = 2 };
 
 template <typename Real>
 int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const Real* ops, const Real* in,
-              Real* out, cudaStream_t s, int& launches);
+              Real* out, int b0, int b1, cudaStream_t s, int& launches);
 
-// Mixed precision: 3xTF32 on the tensor cores (tcgen05).
+// Mixed precision: two-term FP16 on the tensor cores (tcgen05).  [b0, b1): the boxes
+// whose input vectors this launch reads; their scales are taken first.
 template <>
 int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const float* ops,
-                     const float* in, float* out, cudaStream_t s, int& launches) {
-
+                     const float* in, float* out, int b0, int b1, cudaStream_t s, int& launches) {
     if (t1 <= t0) return KIFMM_OK;
     (void)ops;  // the tensor-core path reads the split tables through their TMA maps
+    KF_TRY(tc_box_exp(in, P.Q, P.Qp, b0, b1, P.bexp.p, s));
     const CUtensorMap* m = P.tmaps[which];
-    KF_TRY(launch_pair_tc(which, m[0], m[1], P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p, pt.pout.p, in, out,
-                          P.err.p, s));
-    ++launches;
+    KF_TRY(launch_pair_tc(which, m[0], m[1], P.texp[which], P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p,
+                          pt.pout.p, P.bexp.p, in, out, P.err.p, s));
+    launches += 2;
     return KIFMM_OK;
 }
 
 // FP64: CUDA-core blocked GEMM.
 template <>
 int run_pairs<double>(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const double* ops,
-                      const double* in, double* out, cudaStream_t s, int& launches) {
+                      const double* in, double* out, int b0, int b1, cudaStream_t s, int& launches) {
+    (void)b0;
+    (void)b1;
     using Real = double;
     if (t1 <= t0) return KIFMM_OK;
     auto kern = which == kU2U ? k_u2u_gemm<Real> : which == kM2L ? k_m2l_gemm<Real> : k_l2l_gemm<Real>;
@@ -758,7 +767,8 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_TRY(mark(2));
     // U2U, deepest parents first
     for (int l = T.nlev - 1; l >= 2; --l)
-        KF_TRY(run_pairs<Real>(P, kU2U, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, B.u, B.u, s,
+        KF_TRY(run_pairs<Real>(P, kU2U, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, B.u, B.u,
+                               T.level_off[std::min(l + 1, T.nlev)], T.level_off[std::min(l + 2, T.nlev)], s,
                                launches));
     KF_TRY(mark(3));
     // X list, then V list
@@ -775,13 +785,15 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         ++launches;
     }
     KF_TRY(mark(4));
-    KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, s, launches));
+    KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, T.level_off[std::min(2, T.nlev)],
+                           T.nbox, s, launches));
     KF_TRY(mark(5));
     // L2L, coarsest children first (ADL: each level's potentials shifted to zero mean first)
     const bool center = P.kernel == KIFMM_KERNEL_ADL;
     for (int l = 2; l < T.nlev; ++l) {
         if (l >= 3)
-            KF_TRY(run_pairs<Real>(P, kL2L, P.l2l, P.l2l.level_tile[l], P.l2l.level_tile[l + 1], B.l2l, B.d, B.d, s,
+            KF_TRY(run_pairs<Real>(P, kL2L, P.l2l, P.l2l.level_tile[l], P.l2l.level_tile[l + 1], B.l2l, B.d, B.d,
+                                   T.level_off[l - 1], T.level_off[l], s,
                                    launches));
         int nl = T.level_off[l + 1] - T.level_off[l];
         if (center && nl > 0) {

@@ -1,5 +1,7 @@
-// Host side of the tcgen05 translation GEMM (see pair_tc.cuh): TF32 splitting of the
-// operator tables, their TMA tensor maps, and the launcher.
+// Host side of the tcgen05 translation GEMM (see pair_tc.cuh): scaling and FP16
+// hi/lo splitting of the operator tables, their TMA tensor maps, the per-box scale of
+// the input vectors, and the launcher.
+#include <cmath>
 #include <mutex>
 
 #include "common.cuh"
@@ -9,14 +11,50 @@ namespace kifmm {
 
 namespace {
 
-// hi = nearest TF32 of x (written over x), lo = nearest TF32 of x - hi.
-__global__ void k_split_table(float* __restrict__ hi, float* __restrict__ lo, size_t n) {
+// max |x| of a non-negative-compared float array (bit pattern of |x| orders like the value)
+__global__ void k_absmax(const float* __restrict__ x, size_t n, unsigned int* __restrict__ out) {
+    __shared__ unsigned int red[256];
+    unsigned int m = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(x[i])));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(out, red[0]);
+}
+
+// hi = nearest FP16 of x * scale, lo = nearest FP16 of the remainder.
+__global__ void k_split_table(const float* __restrict__ x, __half* __restrict__ hi, __half* __restrict__ lo,
+                              size_t n, float scale) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float x = hi[i];
-    float h = tc::tf32_rna(x);
+    float v = x[i] * scale;
+    __half h = __float2half_rn(v);
     hi[i] = h;
-    lo[i] = tc::tf32_rna(x - h);
+    lo[i] = __float2half_rn(v - __half2float(h));
+}
+
+// e[b] = kScaleTop - floor(log2 max_k |v[b][k]|): the power of two bringing box b's
+// vector into [2^14, 2^15).  0 for an all-zero vector.
+__global__ void k_box_exp(const float* __restrict__ v, int Q, int Qp, int b0, int* __restrict__ e) {
+    __shared__ float red[128];
+    const int b = b0 + blockIdx.x;
+    float m = 0.f;
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) m = fmaxf(m, fabsf(v[(size_t)b * Qp + k]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int ex = 0;
+        if (red[0] > 0.f) ex = tc::kScaleTop - ilogbf(red[0]);
+        e[b] = max(-100, min(100, ex));
+    }
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -47,24 +85,45 @@ int get_encoder(EncodeTiled* fn) {
 int tc_rows(int Qp) { return Qp <= 128 ? 128 : 256; }
 int tc_tile_pairs(int Qp) { return Qp <= 128 ? 256 : 128; }
 
-// Split an operator table (nops x Qp x Qp FP32) into TF32 hi (in place) and lo parts.
-int tc_split_table(float* table, float* lo, size_t n, cudaStream_t s) {
+// Scale an FP32 operator table by 2^texp (largest entry into [2^14, 2^15)) and split it
+// into FP16 hi and lo tables.  Synchronizes the stream (texp is needed on the host).
+int tc_split_table(const float* table, __half* hi, __half* lo, size_t n, int* texp, cudaStream_t s) {
+    *texp = 0;
     if (!n) return KIFMM_OK;
-    k_split_table<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(table, lo, n);
+    DBuf<unsigned int> mx;
+    KF_TRY(mx.alloc(1));
+    KF_CHECK_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned int), s));
+    k_absmax<<<1024, 256, 0, s>>>(table, n, mx.p);
+    KF_CHECK_LAUNCH();
+    unsigned int hm = 0;
+    KF_CHECK_CUDA(cudaMemcpyAsync(&hm, mx.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
+    KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    float m;
+    memcpy(&m, &hm, sizeof(m));
+    if (m > 0.f) *texp = tc::kScaleTop - std::ilogb(m);
+    k_split_table<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(table, hi, lo, n, std::ldexp(1.0f, *texp));
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }
 
-// 2-D tiled map over rows (op * Qp + row) x columns (Qp), box 32 columns x tc_rows(Qp)
-// rows, 128-byte swizzle, zero fill outside.
-int tc_make_map(CUtensorMap* map, const float* table, int nops, int Qp) {
+// Per-box input scales of boxes [b0, b1) of a check-potential buffer.
+int tc_box_exp(const float* v, int Q, int Qp, int b0, int b1, int* e, cudaStream_t s) {
+    if (b1 <= b0) return KIFMM_OK;
+    k_box_exp<<<b1 - b0, 128, 0, s>>>(v, Q, Qp, b0, e);
+    KF_CHECK_LAUNCH();
+    return KIFMM_OK;
+}
+
+// 2-D tiled map over rows (op * Qp + row) x columns (Qp) of an FP16 table, box kKC
+// columns x tc_rows(Qp) rows, 128-byte swizzle, zero fill outside.
+int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Qp) {
     EncodeTiled enc;
     KF_TRY(get_encoder(&enc));
     cuuint64_t dims[2] = {(cuuint64_t)Qp, (cuuint64_t)nops * (cuuint64_t)Qp};
-    cuuint64_t strides[1] = {(cuuint64_t)Qp * sizeof(float)};
+    cuuint64_t strides[1] = {(cuuint64_t)Qp * sizeof(__half)};
     cuuint32_t box[2] = {(cuuint32_t)tc::kKC, (cuuint32_t)tc_rows(Qp)};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(table), dims, strides, box, estr,
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(table), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -75,25 +134,28 @@ int tc_make_map(CUtensorMap* map, const float* table, int nops, int Qp) {
 }
 
 template <int SLABS, int N>
-static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo, int Q, int Qp, const int4* tiles,
-                        int ntiles, const int* pin, const int* pout, const float* in, float* out, int* err,
-                        cudaStream_t s) {
+static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
+                        const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
+                        const float* in, float* out, int* err, cudaStream_t s) {
     using S = tc::Shape<SLABS, N>;
     auto kern = which == 0 ? tc::k_u2u_tc<SLABS, N> : which == 1 ? tc::k_m2l_tc<SLABS, N> : tc::k_l2l_tc<SLABS, N>;
     // set on every launch: the attribute belongs to the current device's context
     KF_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes));
     const int mgroups = (Qp + S::kRows - 1) / S::kRows;
-    kern<<<ntiles * mgroups, tc::kThreads, S::kSmemBytes, s>>>(hi, lo, Q, Qp, mgroups, tiles, pin, pout, in, out, err);
+    kern<<<ntiles * mgroups, tc::kThreads, S::kSmemBytes, s>>>(hi, lo, Q, Qp, mgroups, tiles, pin, pout, bexp, texp,
+                                                                in, out, err);
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }
 
 // which: 0 = U2U (M2M'), 1 = M2L', 2 = L2L'.
-int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int Q, int Qp, const int4* tiles,
-                   int ntiles, const int* pin, const int* pout, const float* in, float* out, int* err, cudaStream_t s) {
+int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
+                   const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp, const float* in,
+                   float* out, int* err, cudaStream_t s) {
     if (ntiles <= 0) return KIFMM_OK;
-    if (Qp <= 128) return launch_shape<1, 256>(which, hi, lo, Q, Qp, tiles, ntiles, pin, pout, in, out, err, s);
-    return launch_shape<2, 128>(which, hi, lo, Q, Qp, tiles, ntiles, pin, pout, in, out, err, s);
+    if (Qp <= 128)
+        return launch_shape<1, 256>(which, hi, lo, texp, Q, Qp, tiles, ntiles, pin, pout, bexp, in, out, err, s);
+    return launch_shape<2, 128>(which, hi, lo, texp, Q, Qp, tiles, ntiles, pin, pout, bexp, in, out, err, s);
 }
 
 }  // namespace kifmm

@@ -6,8 +6,11 @@
 // for all pairs j of the tile as D(128 x N) = A(128 x K) B(N x K)^T with A = the
 // operator rows and B = the gathered input vectors, accumulated in TMEM (FP32).
 //
-// 3xTF32: x = x_hi + x_lo (both the nearest TF32 values); D += A_hi B_hi + A_hi B_lo +
-// A_lo B_hi (the dropped A_lo B_lo term is ~2^-22 relative).
+// Two-term FP16: every operand is scaled by a power of two into [2^14, 2^15) at its
+// largest entry and written as x = x_hi + x_lo with x_hi, x_lo the nearest FP16 values
+// (22 significant bits); D += A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo
+// term is ~2^-22 relative) with kind::f16 MMAs, and the epilogue undoes both scales.
+// Operator tables have one scale each (texp); input vectors one per box (bexp).
 //
 // Accumulation: the tensor core adds into its FP32 accumulator with truncation, so a
 // long K loop into one accumulator drifts by ~1 ulp of the running sum per MMA.  Each
@@ -15,27 +18,29 @@
 // the hi*hi products) in one of two TMEM buffers, and the threads fold every chunk's
 // partial into FP32 registers (round-to-nearest) while the next chunk multiplies.
 //
-// Operands: the operator rows come pre-split (hi and lo tables) by TMA, one 32-column
-// box per table and chunk, into the canonical K-major 128-byte-swizzled layout (rows
-// of 128 B, 16-byte chunks XOR-permuted by row within 1024-byte atoms); the gathered
-// input vectors are split by the threads and stored in the same layout.  Every
+// Operands: the operator rows come pre-split (FP16 hi and lo tables) by TMA, one
+// 64-column box per table and chunk, into the canonical K-major 128-byte-swizzled
+// layout (rows of 128 B, 16-byte chunks XOR-permuted by row within 1024-byte atoms);
+// the gathered input vectors are scaled and split by the threads into the same layout.  Every
 // mbarrier wait is bounded; on a timeout the CTA records an error, waits (bounded)
 // once more for work in flight, frees its TMEM and returns without writing.
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace kifmm {
 namespace tc {
 
-constexpr int kKC = 32;             // K elements per pipeline stage (4 MMA k-steps)
+constexpr int kKC = 64;             // K elements (FP16) per pipeline stage (4 MMA k-steps of 16)
 constexpr int kThreads = 256;
-constexpr uint32_t kRowBytes = kKC * 4;          // 128 B: one swizzle row
+constexpr uint32_t kRowBytes = kKC * 2;          // 128 B: one swizzle row
 constexpr uint32_t kSBO = 8 * kRowBytes;         // 1024 B between 8-row groups
-constexpr int kSlabBytes = 128 * kKC * 4;        // one 128-row operand slab of one chunk: 16 KB
-static_assert(kRowBytes == 128, "the 128-byte swizzle needs 32 TF32 per row");
+constexpr int kSlabBytes = 128 * kRowBytes;      // one 128-row operand slab of one chunk: 16 KB
+constexpr int kScaleTop = 14;                    // operands scaled into [2^14, 2^15)
+static_assert(kRowBytes == 128, "the 128-byte swizzle needs 64 FP16 per row");
 constexpr long long kSpinLimit = 1LL << 26;
 
 // Tile shape: SLABS x 128 operator rows by N pairs; two accumulator buffers fill the
@@ -51,7 +56,7 @@ struct Shape {
     static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
     static constexpr int kStages = 2;
     static constexpr int kSmemBytes = kStages * kStageBytes + 1024;
-    static constexpr int kBVec = N * (kKC / 4) / kThreads;       // float4 of B per thread per chunk
+    static constexpr int kBVec = N * (kKC / 8) / kThreads;       // 8-element groups of B per thread per chunk
     static_assert(2 * SLABS * N == 512, "two accumulator buffers fill TMEM");
     static_assert(N % 128 == 0 && N <= 256, "N must be 128 or 256");
 };
@@ -87,9 +92,9 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// kind::tf32 instruction descriptor: D FP32, A/B TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// kind::f16 instruction descriptor: D FP32, A/B FP16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -120,11 +125,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
@@ -163,23 +168,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Round to the nearest TF32 value (ties away from zero); the result is exact in TF32.
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
+// 2^e as a float (e in [-126, 127]).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
-// x = hi + lo with hi, lo nearest TF32 values: |x - hi - lo| <= 2^-22 |x|.
-__device__ __forceinline__ void split_tf32(float4 x, float4& hi, float4& lo) {
-    hi.x = tf32_rna(x.x);
-    hi.y = tf32_rna(x.y);
-    hi.z = tf32_rna(x.z);
-    hi.w = tf32_rna(x.w);
-    lo.x = tf32_rna(x.x - hi.x);
-    lo.y = tf32_rna(x.y - hi.y);
-    lo.z = tf32_rna(x.z - hi.z);
-    lo.w = tf32_rna(x.w - hi.w);
+// Eight scaled values -> FP16 hi and lo parts, packed (x * scale = hi + lo to ~2^-22).
+__device__ __forceinline__ void split_f16x8(float4 a, float4 b, float scale, uint4& hi, uint4& lo) {
+    float x[8] = {a.x * scale, a.y * scale, a.z * scale, a.w * scale,
+                  b.x * scale, b.y * scale, b.z * scale, b.w * scale};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __half h0 = __float2half_rn(x[2 * i]), h1 = __float2half_rn(x[2 * i + 1]);
+        __half l0 = __float2half_rn(x[2 * i] - __half2float(h0));
+        __half l1 = __float2half_rn(x[2 * i + 1] - __half2float(h1));
+        h[i] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+        l[i] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // Byte offset of (row r, 16-byte chunk c) in a K-major 128-byte-swizzled tile.
@@ -187,26 +193,27 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int c) {
     return (uint32_t)(r * kRowBytes + ((c ^ (r & 7)) << 4));
 }
 
-// Element e of a chunk's float4 grid -> (row r, chunk c).  Eight consecutive threads
-// take eight consecutive rows of one chunk: after the swizzle their 16-byte stores
-// hit eight different bank groups; a warp reads 64 contiguous bytes from each of 8
-// rows in global memory.
+// Element e of a chunk's grid of 16-byte (8 x FP16) groups -> (row r, chunk c).  Eight
+// consecutive threads take eight consecutive rows of one chunk: after the swizzle
+// their 16-byte stores hit eight different bank groups; a warp reads 128 contiguous
+// bytes (FP32 source) from each of 8 rows in global memory.
 __device__ __forceinline__ void chunk_coord(int e, int& r, int& c) {
-    constexpr int KQ = kKC / 4;
+    constexpr int KQ = kKC / 8;
     const int w = e % (8 * KQ);
     r = (e / (8 * KQ)) * 8 + (w & 7);
     c = w >> 3;
 }
 
 // grid.x = ntiles * mgroups (row group fastest).  tiles[t] = (op, first pair, count, 0).
-// map_hi / map_lo: 2-D tensor maps of the split operator tables, rows = op * Qp + row,
-// box = 32 columns x kRows rows, 128-byte swizzle.
+// map_hi / map_lo: 2-D tensor maps of the split FP16 operator tables (scaled by 2^texp),
+// rows = op * Qp + row, box = 64 columns x kRows rows, 128-byte swizzle.  bexp[box]:
+// the power of two that brings the input vector of a box into FP16 range.
 template <int SLABS, int N>
-__device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CUtensorMap& map_lo, int Q, int Qp,
-                                             int mgroups, const int4* __restrict__ tiles,
+__device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CUtensorMap& map_lo, int texp, int Q,
+                                             int Qp, int mgroups, const int4* __restrict__ tiles,
                                              const int* __restrict__ pin, const int* __restrict__ pout,
-                                             const float* __restrict__ in, float* __restrict__ out,
-                                             int* __restrict__ err) {
+                                             const int* __restrict__ bexp, const float* __restrict__ in,
+                                             float* __restrict__ out, int* __restrict__ err) {
     using S = Shape<SLABS, N>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -214,6 +221,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
     __shared__ uint64_t mma_bar[2];       // MMAs of accumulator buffer b (and stage b) done
     __shared__ uint32_t tmem_base;
     __shared__ int s_in[N], s_out[N];
+    __shared__ float s_bscale[N], s_oscale[N];   // input scale, output unscale per pair
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -225,8 +233,12 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
     const int nchunks = (Qp + kKC - 1) / kKC;  // Qp is a multiple of 16; the tail is zero-filled
 
     for (int j = tid; j < N; j += kThreads) {
-        s_in[j] = j < cnt ? pin[t.y + j] : -1;
+        const int bi = j < cnt ? pin[t.y + j] : -1;
+        s_in[j] = bi;
         s_out[j] = j < cnt ? pout[t.y + j] : -1;
+        const int e = bi >= 0 ? bexp[bi] : 0;
+        s_bscale[j] = pow2f(e);
+        s_oscale[j] = pow2f(-(e + texp));
     }
     auto stage_base = [&](int st) -> unsigned char* { return base + st * S::kStageBytes; };
     auto issue_tma = [&](int c) {
@@ -255,7 +267,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    constexpr uint32_t idesc = idesc_tf32(128, N);
+    constexpr uint32_t idesc = idesc_f16(128, N);
 
     // this warp's accumulator columns: lane quarter q, slab my_slab, columns [my_col0, +128)
     const int quarter = warp & 3, half = warp >> 2;
@@ -264,16 +276,22 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
 #pragma unroll
     for (int j = 0; j < 128; ++j) acc[j] = 0.f;
 
-    float4 rb[S::kBVec];
+    // staged B: scaled, split and packed at load time (8 FP16 per 16-byte group)
+    uint4 rhi[S::kBVec], rlo[S::kBVec];
     auto load_b = [&](int c) {
         const int k0 = c * kKC;
 #pragma unroll
         for (int i = 0; i < S::kBVec; ++i) {
             int r, ch;
             chunk_coord(tid + i * kThreads, r, ch);
-            int bi = s_in[r], k = k0 + 4 * ch;   // a k-quad lies wholly inside or outside Qp
-            rb[i] = (bi >= 0 && k < Qp) ? *reinterpret_cast<const float4*>(in + (size_t)bi * Qp + k)
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+            int bi = s_in[r], k = k0 + 8 * ch;   // an 8-group lies wholly inside or outside Qp
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (bi >= 0 && k < Qp) {
+                const float4* src = reinterpret_cast<const float4*>(in + (size_t)bi * Qp + k);
+                a = src[0];
+                b = src[1];
+            }
+            split_f16x8(a, b, s_bscale[r], rhi[i], rlo[i]);
         }
     };
     auto store_b = [&](unsigned char* sb) {
@@ -282,11 +300,9 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
         for (int i = 0; i < S::kBVec; ++i) {
             int r, ch;
             chunk_coord(tid + i * kThreads, r, ch);
-            uint32_t o = sw128_off(r, ch);
-            float4 hi, lo;
-            split_tf32(rb[i], hi, lo);
-            *reinterpret_cast<float4*>(bh + o) = hi;
-            *reinterpret_cast<float4*>(bh + S::kBBytes + o) = lo;
+            uint32_t o = (uint32_t)((r >> 7) * kSlabBytes) + sw128_off(r & 127, ch);
+            *reinterpret_cast<uint4*>(bh + o) = rhi[i];
+            *reinterpret_cast<uint4*>(bh + S::kBBytes + o) = rlo[i];
         }
     };
     auto fold = [&](int b) {
@@ -330,15 +346,15 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
                     const uint32_t ao = (uint32_t)(sl * kSlabBytes);
                     // small correction products first, then the hi*hi products
 #pragma unroll
-                    for (int ks = 0; ks < kKC / 8; ++ks) {
-                        const uint32_t koff = ks * 32;  // 8 TF32 along K inside the swizzled row
-                        mma_tf32(d, smem_desc(a_hi + ao + koff), smem_desc(b_lo + koff), idesc, ks > 0 ? 1u : 0u);
-                        mma_tf32(d, smem_desc(a_lo + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
+                    for (int ks = 0; ks < kKC / 16; ++ks) {
+                        const uint32_t koff = ks * 32;  // 16 FP16 along K inside the swizzled row
+                        mma_f16(d, smem_desc(a_hi + ao + koff), smem_desc(b_lo + koff), idesc, ks > 0 ? 1u : 0u);
+                        mma_f16(d, smem_desc(a_lo + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
                     }
 #pragma unroll
-                    for (int ks = 0; ks < kKC / 8; ++ks) {
+                    for (int ks = 0; ks < kKC / 16; ++ks) {
                         const uint32_t koff = ks * 32;
-                        mma_tf32(d, smem_desc(a_hi + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
+                        mma_f16(d, smem_desc(a_hi + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
                     }
                 }
                 mma_commit(&mma_bar[b]);
@@ -379,7 +395,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
 #pragma unroll
             for (int j = 0; j < 128; ++j) {
                 int ob = s_out[my_col0 + j];
-                if (ob >= 0) atomicAdd(out + (size_t)ob * Qp + row, acc[j]);
+                if (ob >= 0) atomicAdd(out + (size_t)ob * Qp + row, acc[j] * s_oscale[my_col0 + j]);
             }
         }
     } else if (tid == 0) {
@@ -404,9 +420,9 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
     __global__ void __launch_bounds__(kThreads, 1)                                                            \
         NAME(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int Q,   \
              int Qp, int mgroups, const int4* __restrict__ tiles, const int* __restrict__ pin,                \
-             const int* __restrict__ pout, const float* __restrict__ in, float* __restrict__ out,             \
-             int* __restrict__ err) {                                                                          \
-        pair_tc_body<SLABS, N>(map_hi, map_lo, Q, Qp, mgroups, tiles, pin, pout, in, out, err);                \
+             const int* __restrict__ pout, const int* __restrict__ bexp, int texp, const float* __restrict__ in, \
+             float* __restrict__ out, int* __restrict__ err) {                                                 \
+        pair_tc_body<SLABS, N>(map_hi, map_lo, texp, Q, Qp, mgroups, tiles, pin, pout, bexp, in, out, err);    \
     }
 KF_TC_KERNEL(k_u2u_tc)
 KF_TC_KERNEL(k_m2l_tc)
