@@ -47,39 +47,59 @@ def _dist():
 
 
 class ClockSampler:
-    """nvidia-smi SM clock / throttle-reason samples while the timed region runs."""
+    """SM clock / throttle-reason samples taken while the timed region runs.
 
-    def __init__(self, index=0):
-        self.index = index
-        self.samples = []
-        self._stop = threading.Event()
-        self._t = None
+    One `nvidia-smi -lms 50` loop runs for the whole window; each line it prints is
+    stamped on arrival and kept if it arrived between enter and exit."""
 
-    def _run(self):
-        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
-        while not self._stop.is_set():
-            try:
-                r = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                    "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                   timeout=5)
-                f = [x.strip() for x in r.stdout.strip().split(",")]
-                if len(f) >= 7:
-                    self.samples.append(f)
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+
+    def __init__(self, index=0, interval_ms=50):
+        self.index = index
+        self.interval_ms = interval_ms
+        self.samples = []
+        self._lines = []
+        self._proc = None
+        self._t = None
+        self._t0 = self._t1 = None
+
+    def _reader(self):
+        for ln in self._proc.stdout:
+            self._lines.append((time.monotonic(), ln))
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._reader, daemon=True)
+            self._t.start()
+            t_wait = time.monotonic() + 5.0           # the loop is printing before the window opens
+            while not self._lines and time.monotonic() < t_wait and self._proc.poll() is None:
+                time.sleep(0.01)
+        except Exception:
+            self._proc = None
+        self._t0 = time.monotonic()
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        if self._t:
-            self._t.join(timeout=10)
+        self._t1 = time.monotonic()
+        if self._proc is not None:
+            time.sleep(self.interval_ms * 1e-3)       # the sample due at the window's end
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+            if self._t:
+                self._t.join(timeout=5)
+        for t, ln in self._lines:
+            if self._t0 <= t <= self._t1 + self.interval_ms * 1e-3:
+                f = [x.strip() for x in ln.strip().split(",")]
+                if len(f) >= 7:
+                    self.samples.append(f)
 
     def summary(self):
         if not self.samples:
@@ -125,6 +145,9 @@ def oracle_sample(wl, m, q_host, n_sample, seed=12345):
     return idx, ref, dt, oracle.max_threads()
 
 
+REF_BUDGET_S = 120.0     # wall time the reference arm aims for
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -138,20 +161,25 @@ def run_reference(args):
         q = (nrm[0] * M[0] + nrm[1] * M[1] + nrm[2] * M[2]) * w
     else:
         q = wl.get("density", synth.uniform_density(m.n, 1000)) * w
-    times = []
-    for s in range(args.warmup + args.steps):
-        _, _, dt, cores = oracle_sample(wl, m, q, args.ref_sample, seed=100 + s)
+    # per-target time of the oracle; the sample per step is sized after the first warm-up
+    # step so the whole run stays within about two minutes whatever --steps is
+    nstep = args.warmup + args.steps
+    sample, per_target = args.ref_sample, []
+    for s in range(nstep):
+        _, _, dt, cores = oracle_sample(wl, m, q, sample, seed=100 + s)
         if s >= args.warmup:
-            times.append(dt)
-    per_step = float(np.mean(times))
-    value = args.ref_sample / per_step
+            per_target.append(dt / sample)
+        if s == 0:
+            sample = int(max(32, min(sample, sample * REF_BUDGET_S / (dt * nstep))))
+    value = 1.0 / float(np.mean(per_target))
+    per_step = sample / value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "n_targets": m.n,
-                                            "sample_targets_per_step": args.ref_sample},
+                                            "sample_targets_per_step": sample},
             "cpu_baseline": {"value": value, "unit": "targets/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d seeded targets x all %d sources per step" % (args.ref_sample, m.n)},
+                             "sample": "%d seeded targets x all %d sources per step" % (sample, m.n)},
             "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -310,9 +338,6 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rate on GB300
-
-
 def _kernel_sha():
     import hashlib
     path = os.path.join(ROOT, "paper_1605_01715_gb300", "csrc", "pair_tc.cuh")
@@ -347,11 +372,11 @@ def roofline(phases, st, tst, args):
     if dom in ("m2l", "u2u", "l2l"):
         pairs = {"m2l": st["m2l_pairs"], "u2u": st["u2u_pairs"], "l2l": st["l2l_pairs"]}[dom]
         flops = 2.0 * Q * Q * pairs                  # algorithmic: one Q x Q operator per pair
-        if mixed:                                   # 3xTF32 on tcgen05: FP32-equivalent = TF32 / 3
-            peak = pk["bf16_tflops"] * TF32_PER_BF16 / 3.0
-            out = {"kernel": "k_pair_tc (%s, tcgen05 3xTF32)" % dom, "bound": "tensor",
-                   "peak_source": "%s bf16 burst %.0f x nominal TF32/BF16 %.3f / 3 (3xTF32)"
-                                  % (src, pk["bf16_tflops"], TF32_PER_BF16)}
+        if mixed:                                   # two-term FP16 on tcgen05: 3 MMAs per product
+            peak = pk["bf16_tflops"] / 3.0
+            out = {"kernel": "k_%s_tc (tcgen05, two-term FP16)" % dom, "bound": "tensor",
+                   "peak_source": "%s bf16/fp16 dense burst %.0f / 3 (hi*hi + hi*lo + lo*hi)"
+                                  % (src, pk["bf16_tflops"])}
         else:
             peak = fp64_peak
             out = {"kernel": "k_%s_gemm<double>" % dom, "bound": "alu", "peak_source": "FP64 nominal"}
@@ -377,7 +402,7 @@ def roofline(phases, st, tst, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="kifmm", choices=["kifmm", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))

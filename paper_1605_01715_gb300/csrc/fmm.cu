@@ -23,11 +23,11 @@ namespace kifmm {
 
 int tc_tile_pairs(int Qp);
 int tc_split_table(const float* table, __half* hi, __half* lo, size_t n, int* texp, cudaStream_t s);
-int tc_box_exp(const float* v, int Q, int Qp, int b0, int b1, int* e, cudaStream_t s);
+int tc_box_split(const float* v, int Q, int Qp, int b0, int b1, __half* hi, __half* lo, int* e, cudaStream_t s);
 int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Qp);
 int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
-                   const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp, const float* in,
-                   float* out, int* err, cudaStream_t s);
+                   const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
+                   const __half* in_hi, const __half* in_lo, float* out, int* err, cudaStream_t s);
 
 namespace {
 
@@ -555,6 +555,8 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_CHECK_CUDA(cudaStreamSynchronize(s));
         for (int f = 0; f < 3; ++f) f32[f]->release();
         KF_TRY(P.bexp.alloc(T.nbox));
+        KF_TRY(P.vin_h.alloc((size_t)T.nbox * P.Qp));
+        KF_TRY(P.vin_l.alloc((size_t)T.nbox * P.Qp));
     }
 
     // work lists (host bookkeeping over the tree's lists)
@@ -678,7 +680,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                      P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
                      P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(), P.tab_h[0].bytes(),
                      P.tab_h[1].bytes(), P.tab_h[2].bytes(), P.tab_l[0].bytes(), P.tab_l[1].bytes(),
-                     P.tab_l[2].bytes(), P.bexp.bytes()})
+                     P.tab_l[2].bytes(), P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes()})
         P.device_bytes += (int64_t)b;
     return KIFMM_OK;
 }
@@ -702,10 +704,10 @@ int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int 
                      const float* in, float* out, int b0, int b1, cudaStream_t s, int& launches) {
     if (t1 <= t0) return KIFMM_OK;
     (void)ops;  // the tensor-core path reads the split tables through their TMA maps
-    KF_TRY(tc_box_exp(in, P.Q, P.Qp, b0, b1, P.bexp.p, s));
+    KF_TRY(tc_box_split(in, P.Q, P.Qp, b0, b1, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
     const CUtensorMap* m = P.tmaps[which];
     KF_TRY(launch_pair_tc(which, m[0], m[1], P.texp[which], P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p,
-                          pt.pout.p, P.bexp.p, in, out, P.err.p, s));
+                          pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, out, P.err.p, s));
     launches += 2;
     return KIFMM_OK;
 }

@@ -1,6 +1,6 @@
 // Host side of the tcgen05 translation GEMM (see pair_tc.cuh): scaling and FP16
-// hi/lo splitting of the operator tables, their TMA tensor maps, the per-box scale of
-// the input vectors, and the launcher.
+// hi/lo splitting of the operator tables, their TMA tensor maps, the per-box scaling and
+// splitting of the input vectors, and the launcher.
 #include <cmath>
 #include <mutex>
 
@@ -37,13 +37,17 @@ __global__ void k_split_table(const float* __restrict__ x, __half* __restrict__ 
     lo[i] = __float2half_rn(v - __half2float(h));
 }
 
-// e[b] = kScaleTop - floor(log2 max_k |v[b][k]|): the power of two bringing box b's
-// vector into [2^14, 2^15).  0 for an all-zero vector.
-__global__ void k_box_exp(const float* __restrict__ v, int Q, int Qp, int b0, int* __restrict__ e) {
+// Box b of [b0, b0 + gridDim.x): e[b] = kScaleTop - floor(log2 max_k |v[b][k]|), the
+// power of two bringing its vector into [2^14, 2^15) (0 for an all-zero vector), and
+// hi[b][k] + lo[b][k] = v[b][k] * 2^e[b] as two nearest FP16 values; columns past Q zero.
+__global__ void k_box_split(const float* __restrict__ v, int Q, int Qp, int b0, __half* __restrict__ hi,
+                            __half* __restrict__ lo, int* __restrict__ e) {
     __shared__ float red[128];
+    __shared__ float s_scale;
     const int b = b0 + blockIdx.x;
+    const float* vb = v + (size_t)b * Qp;
     float m = 0.f;
-    for (int k = threadIdx.x; k < Q; k += blockDim.x) m = fmaxf(m, fabsf(v[(size_t)b * Qp + k]));
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) m = fmaxf(m, fabsf(vb[k]));
     red[threadIdx.x] = m;
     __syncthreads();
     for (int o = 64; o > 0; o >>= 1) {
@@ -53,7 +57,17 @@ __global__ void k_box_exp(const float* __restrict__ v, int Q, int Qp, int b0, in
     if (threadIdx.x == 0) {
         int ex = 0;
         if (red[0] > 0.f) ex = tc::kScaleTop - ilogbf(red[0]);
-        e[b] = max(-100, min(100, ex));
+        ex = max(-100, min(100, ex));
+        e[b] = ex;
+        s_scale = tc::pow2f(ex);
+    }
+    __syncthreads();
+    const float sc = s_scale;
+    for (int k = threadIdx.x; k < Qp; k += blockDim.x) {
+        const float x = k < Q ? vb[k] * sc : 0.f;
+        const __half h = __float2half_rn(x);
+        hi[(size_t)b * Qp + k] = h;
+        lo[(size_t)b * Qp + k] = __float2half_rn(x - __half2float(h));
     }
 }
 
@@ -106,25 +120,25 @@ int tc_split_table(const float* table, __half* hi, __half* lo, size_t n, int* te
     return KIFMM_OK;
 }
 
-// Per-box input scales of boxes [b0, b1) of a check-potential buffer.
-int tc_box_exp(const float* v, int Q, int Qp, int b0, int b1, int* e, cudaStream_t s) {
+// Per-box scales and FP16 hi/lo splits of boxes [b0, b1) of a check-potential buffer.
+int tc_box_split(const float* v, int Q, int Qp, int b0, int b1, __half* hi, __half* lo, int* e, cudaStream_t s) {
     if (b1 <= b0) return KIFMM_OK;
-    k_box_exp<<<b1 - b0, 128, 0, s>>>(v, Q, Qp, b0, e);
+    k_box_split<<<b1 - b0, 128, 0, s>>>(v, Q, Qp, b0, hi, lo, e);
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }
 
-// 2-D tiled map over rows (op * Qp + row) x columns (Qp) of an FP16 table, box kKC
-// columns x tc_rows(Qp) rows, 128-byte swizzle, zero fill outside.
+// 2-D tiled map over rows (op * Qp + row) x columns (Qp) of an FP16 table, box kKS
+// columns x tc_rows(Qp) rows, 64-byte swizzle, zero fill outside.
 int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Qp) {
     EncodeTiled enc;
     KF_TRY(get_encoder(&enc));
     cuuint64_t dims[2] = {(cuuint64_t)Qp, (cuuint64_t)nops * (cuuint64_t)Qp};
     cuuint64_t strides[1] = {(cuuint64_t)Qp * sizeof(__half)};
-    cuuint32_t box[2] = {(cuuint32_t)tc::kKC, (cuuint32_t)tc_rows(Qp)};
+    cuuint32_t box[2] = {(cuuint32_t)tc::kKS, (cuuint32_t)tc_rows(Qp)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(table), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d table", (int)r, nops * Qp, Qp);
@@ -136,26 +150,36 @@ int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Qp) {
 template <int SLABS, int N>
 static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
                         const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
-                        const float* in, float* out, int* err, cudaStream_t s) {
+                        const __half* in_hi, const __half* in_lo, float* out, int* err, cudaStream_t s) {
     using S = tc::Shape<SLABS, N>;
     auto kern = which == 0 ? tc::k_u2u_tc<SLABS, N> : which == 1 ? tc::k_m2l_tc<SLABS, N> : tc::k_l2l_tc<SLABS, N>;
     // set on every launch: the attribute belongs to the current device's context
     KF_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes));
     const int mgroups = (Qp + S::kRows - 1) / S::kRows;
-    kern<<<ntiles * mgroups, tc::kThreads, S::kSmemBytes, s>>>(hi, lo, Q, Qp, mgroups, tiles, pin, pout, bexp, texp,
-                                                                in, out, err);
+    const int nitems = ntiles * mgroups;
+    // persistent: one CTA per SM (one fits by shared memory), each walking its share of
+    // the work items
+    int dev = 0, nsm = 0;
+    KF_CHECK_CUDA(cudaGetDevice(&dev));
+    KF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = nitems < nsm ? nitems : nsm;
+    kern<<<grid, tc::kThreads, S::kSmemBytes, s>>>(hi, lo, Q, Qp, mgroups, nitems, tiles, pin, pout, bexp, texp,
+                                                    in_hi, in_lo, out, err);
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }
 
-// which: 0 = U2U (M2M'), 1 = M2L', 2 = L2L'.
+// which: 0 = U2U (M2M'), 1 = M2L', 2 = L2L'.  in_hi / in_lo: the split input vectors
+// (tc_box_split) of every box a pair reads.
 int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
-                   const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp, const float* in,
-                   float* out, int* err, cudaStream_t s) {
+                   const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
+                   const __half* in_hi, const __half* in_lo, float* out, int* err, cudaStream_t s) {
     if (ntiles <= 0) return KIFMM_OK;
     if (Qp <= 128)
-        return launch_shape<1, 256>(which, hi, lo, texp, Q, Qp, tiles, ntiles, pin, pout, bexp, in, out, err, s);
-    return launch_shape<2, 128>(which, hi, lo, texp, Q, Qp, tiles, ntiles, pin, pout, bexp, in, out, err, s);
+        return launch_shape<1, 256>(which, hi, lo, texp, Q, Qp, tiles, ntiles, pin, pout, bexp, in_hi, in_lo, out,
+                                    err, s);
+    return launch_shape<2, 128>(which, hi, lo, texp, Q, Qp, tiles, ntiles, pin, pout, bexp, in_hi, in_lo, out, err,
+                                s);
 }
 
 }  // namespace kifmm

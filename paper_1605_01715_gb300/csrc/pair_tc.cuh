@@ -1,29 +1,37 @@
-// Grouped translation GEMM on the 5th-generation tensor cores (tcgen05), 3xTF32.
+// Grouped translation GEMM on the 5th-generation tensor cores (tcgen05), two-term FP16.
 //
-// Every tile of the work list shares one Qp x Qp operator Op (M2M', M2L' or L2L') and
-// holds up to kTcN (input box, output box) pairs; the CTA computes one 128-row slab of
+// A work item is one tile of up to N (input box, output box) pairs that share one
+// Qp x Qp operator Op (M2M', M2L' or L2L') and one group of 128 * SLABS operator rows:
 //   out[pout[j]][row] += sum_k Op[row][k] * in[pin[j]][k]
-// for all pairs j of the tile as D(128 x N) = A(128 x K) B(N x K)^T with A = the
-// operator rows and B = the gathered input vectors, accumulated in TMEM (FP32).
+// computed as D(128 x N) = A(128 x K) B(N x K)^T per 128-row slab, with A = operator
+// rows and B = the gathered input vectors, accumulated in TMEM.
 //
 // Two-term FP16: every operand is scaled by a power of two into [2^14, 2^15) at its
 // largest entry and written as x = x_hi + x_lo with x_hi, x_lo the nearest FP16 values
 // (22 significant bits); D += A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo
 // term is ~2^-22 relative) with kind::f16 MMAs, and the epilogue undoes both scales.
-// Operator tables have one scale each (texp); input vectors one per box (bexp).
+// Operator tables have one scale each (texp); input vectors one per box (bexp), and
+// both come pre-split: the operators once at setup, the box vectors right before the
+// launch (one pass over the input buffer).
 //
 // Accumulation: the tensor core adds into its FP32 accumulator with truncation, so a
-// long K loop into one accumulator drifts by ~1 ulp of the running sum per MMA.  Each
-// K-chunk of 32 therefore starts a fresh accumulator (correction products first, then
-// the hi*hi products) in one of two TMEM buffers, and the threads fold every chunk's
-// partial into FP32 registers (round-to-nearest) while the next chunk multiplies.
+// long K loop into one accumulator drifts by ~1 ulp of the running sum per MMA.  Every
+// 64 columns of K therefore start a fresh accumulator (correction products first, then
+// the hi*hi products) in one of two TMEM buffers, and the fold warps add each partial
+// into FP32 registers (round-to-nearest) while the other buffer fills.
 //
-// Operands: the operator rows come pre-split (FP16 hi and lo tables) by TMA, one
-// 64-column box per table and chunk, into the canonical K-major 128-byte-swizzled
-// layout (rows of 128 B, 16-byte chunks XOR-permuted by row within 1024-byte atoms);
-// the gathered input vectors are scaled and split by the threads into the same layout.  Every
-// mbarrier wait is bounded; on a timeout the CTA records an error, waits (bounded)
-// once more for work in flight, frees its TMEM and returns without writing.
+// Schedule: persistent, one CTA per SM walking the items blockIdx.x + k * gridDim.x,
+// with the warps split into roles joined only by mbarriers:
+//   warp 0      TMA of the operator rows (hi and lo tables, one 32-column box each)
+//   warp 1      MMA issue (one thread); its commits free ring stages and fill accumulators
+//   warps 2-3   cp.async of the input rows (16-byte copies, straight into the layout)
+//   warps 4-11  fold of each accumulator into registers, then the scatter epilogue
+// over a ring of kStages K-stages of 32 columns in the canonical K-major 64-byte-swizzled
+// layout (rows of 64 B, 16-byte chunks XOR-permuted by row within 512-byte atoms).  The
+// MMAs of the next item run while the fold warps scatter the previous one.
+// Every wait is bounded; a wait that runs out raises an abort flag that stops the other
+// roles, each of which then waits (bounded) for its own copies or MMAs in flight; the CTA
+// records the error, frees its TMEM and returns.
 #pragma once
 
 #include <cuda.h>
@@ -34,47 +42,59 @@
 namespace kifmm {
 namespace tc {
 
-constexpr int kKC = 64;             // K elements (FP16) per pipeline stage (4 MMA k-steps of 16)
-constexpr int kThreads = 256;
-constexpr uint32_t kRowBytes = kKC * 2;          // 128 B: one swizzle row
-constexpr uint32_t kSBO = 8 * kRowBytes;         // 1024 B between 8-row groups
-constexpr int kSlabBytes = 128 * kRowBytes;      // one 128-row operand slab of one chunk: 16 KB
-constexpr int kScaleTop = 14;                    // operands scaled into [2^14, 2^15)
-static_assert(kRowBytes == 128, "the 128-byte swizzle needs 64 FP16 per row");
+constexpr int kKS = 32;                 // K elements (FP16) per ring stage: 2 MMA k-steps of 16
+constexpr int kFoldStages = 2;          // ring stages per accumulator (64 columns of K)
+constexpr int kStages = 4;              // ring depth
+constexpr int kBLag = 2;                // stages of input copies a producer thread keeps in flight
+// An accumulator holds its stages until its last one arrives; the producers must then
+// still be able to fill that stage without waiting on the accumulator itself.
+static_assert(kFoldStages + kBLag <= kStages, "ring too shallow for the fold group and the copy lag");
+constexpr int kWarps = 12;
+constexpr int kThreads = kWarps * 32;
+constexpr int kProdWarp0 = 2, kProdThreads = 64;     // input-row producers
+constexpr int kFoldWarp0 = 4, kFoldThreads = 256;    // fold / epilogue
+constexpr int kFoldBar = 1;                          // named barrier of the fold warps
+constexpr uint32_t kRowBytes = kKS * 2;              // 64 B: one swizzle row
+constexpr uint32_t kSBO = 8 * kRowBytes;             // 512 B between 8-row groups
+constexpr int kSlabBytes = 128 * kRowBytes;          // one 128-row slab of one stage: 8 KB
+constexpr int kScaleTop = 14;                        // operands scaled into [2^14, 2^15)
+static_assert(kRowBytes == 64, "the 64-byte swizzle needs 32 FP16 per row");
+static_assert(kFoldThreads == (kWarps - kFoldWarp0) * 32 && kProdThreads == (kFoldWarp0 - kProdWarp0) * 32,
+              "role split");
 constexpr long long kSpinLimit = 1LL << 26;
 
 // Tile shape: SLABS x 128 operator rows by N pairs; two accumulator buffers fill the
-// 512 TMEM columns (2 * SLABS * N = 512).  Each warp owns one lane quarter and 128
+// 512 TMEM columns (2 * SLABS * N = 512).  Each fold warp owns one lane quarter and 128
 // accumulator columns, held as FP32 registers.
 template <int SLABS, int N>
 struct Shape {
     static constexpr int kRows = SLABS * 128;
     static constexpr int kTmemCols = 512;
     static constexpr int kBufCols = SLABS * N;                 // one accumulator buffer
-    static constexpr int kABytes = SLABS * kSlabBytes;        // per hi or lo copy
-    static constexpr int kBBytes = (N / 128) * kSlabBytes;     // per hi or lo copy (N multiple of 128)
+    static constexpr int kABytes = SLABS * kSlabBytes;        // per hi or lo table, one stage
+    static constexpr int kBBytes = N * (int)kRowBytes;         // per hi or lo table, one stage
     static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-    static constexpr int kStages = 2;
     static constexpr int kSmemBytes = kStages * kStageBytes + 1024;
-    static constexpr int kBVec = N * (kKC / 8) / kThreads;       // 8-element groups of B per thread per chunk
+    static constexpr int kBRows = N / 16;                      // input rows per producer thread
     static_assert(2 * SLABS * N == 512, "two accumulator buffers fill TMEM");
     static_assert(N % 128 == 0 && N <= 256, "N must be 128 or 256");
+    static_assert(kStageBytes % 1024 == 0, "stages stay 1024-byte aligned");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// K-major, 128-byte swizzle: 8-row groups kSBO apart, leading offset unused (1),
-// descriptor version 1, layout type 2 (SWIZZLE_128B).  Tiles are 1024-byte aligned;
-// a K step inside the 128-byte row advances the start address by 32 bytes.
+// K-major, 64-byte swizzle: 8-row groups kSBO apart, leading offset unused (1),
+// descriptor version 1, layout type 4 (SWIZZLE_64B).  Tiles are 1024-byte aligned; a K
+// step of 16 inside the 64-byte row advances the start address by 32 bytes.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
     d |= (uint64_t)1 << 16;
     d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)4 << 61;
     return d;
 }
 
@@ -122,6 +142,38 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// Bounded wait that also gives up once another role has raised *abort; a timeout
+// raises it.  Returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (i > 64) __nanosleep(32);
+    }
+    *abort = 1;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Named barrier over the n threads of one role (id 0 is __syncthreads); the second
+// form also returns whether pred held in any of them.
+__device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ bool bar_named_or(int id, int n, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "bar.red.or.pred q, %1, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(id), "r"((uint32_t)pred), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -152,110 +204,73 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // 2^e as a float (e in [-126, 127]).
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
-// Eight scaled values -> FP16 hi and lo parts, packed (x * scale = hi + lo to ~2^-22).
-__device__ __forceinline__ void split_f16x8(float4 a, float4 b, float scale, uint4& hi, uint4& lo) {
-    float x[8] = {a.x * scale, a.y * scale, a.z * scale, a.w * scale,
-                  b.x * scale, b.y * scale, b.z * scale, b.w * scale};
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        __half h0 = __float2half_rn(x[2 * i]), h1 = __float2half_rn(x[2 * i + 1]);
-        __half l0 = __float2half_rn(x[2 * i] - __half2float(h0));
-        __half l1 = __float2half_rn(x[2 * i + 1] - __half2float(h1));
-        h[i] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-        l[i] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
-// Byte offset of (row r, 16-byte chunk c) in a K-major 128-byte-swizzled tile.
-__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
-    return (uint32_t)(r * kRowBytes + ((c ^ (r & 7)) << 4));
+// Byte offset of (row r, 16-byte chunk c) in a K-major 64-byte-swizzled tile: the chunk
+// index is XORed with bits 7-8 of the row's byte offset.
+__device__ __forceinline__ uint32_t sw64_off(int r, int c) {
+    return (uint32_t)(r * kRowBytes + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
-// Element e of a chunk's grid of 16-byte (8 x FP16) groups -> (row r, chunk c).  Eight
-// consecutive threads take eight consecutive rows of one chunk: after the swizzle
-// their 16-byte stores hit eight different bank groups; a warp reads 128 contiguous
-// bytes (FP32 source) from each of 8 rows in global memory.
-__device__ __forceinline__ void chunk_coord(int e, int& r, int& c) {
-    constexpr int KQ = kKC / 8;
-    const int w = e % (8 * KQ);
-    r = (e / (8 * KQ)) * 8 + (w & 7);
-    c = w >> 3;
-}
-
-// grid.x = ntiles * mgroups (row group fastest).  tiles[t] = (op, first pair, count, 0).
-// map_hi / map_lo: 2-D tensor maps of the split FP16 operator tables (scaled by 2^texp),
-// rows = op * Qp + row, box = 64 columns x kRows rows, 128-byte swizzle.  bexp[box]:
-// the power of two that brings the input vector of a box into FP16 range.
+// tiles[t] = (op, first pair, count, 0); work item w = (tile w / mgroups, row group
+// w % mgroups).  map_hi / map_lo: 2-D tensor maps of the split FP16 operator tables
+// (scaled by 2^texp), rows = op * Qp + row, box = 32 columns x kRows rows, 64-byte
+// swizzle.  in_hi / in_lo: the input vectors of all boxes scaled by 2^bexp[box] and
+// split, Qp FP16 per box.
 template <int SLABS, int N>
 __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CUtensorMap& map_lo, int texp, int Q,
-                                             int Qp, int mgroups, const int4* __restrict__ tiles,
+                                             int Qp, int mgroups, int nitems, const int4* __restrict__ tiles,
                                              const int* __restrict__ pin, const int* __restrict__ pout,
-                                             const int* __restrict__ bexp, const float* __restrict__ in,
-                                             float* __restrict__ out, int* __restrict__ err) {
+                                             const int* __restrict__ bexp, const __half* __restrict__ in_hi,
+                                             const __half* __restrict__ in_lo, float* __restrict__ out,
+                                             int* __restrict__ err) {
     using S = Shape<SLABS, N>;
+    const int G = gridDim.x;
+    const int K = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + G - 1) / G : 0;  // items of this CTA
+    if (K == 0) return;                   // uniform: nothing allocated yet
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    __shared__ uint64_t full_bar[2];      // TMA of stage s landed
-    __shared__ uint64_t mma_bar[2];       // MMAs of accumulator buffer b (and stage b) done
+    __shared__ uint64_t tma_full[kStages];    // operator rows of a stage landed (TMA bytes)
+    __shared__ uint64_t b_full[kStages];      // input rows of a stage landed (producer arrivals)
+    __shared__ uint64_t empty[kStages];       // MMAs reading a stage done
+    __shared__ uint64_t acc_full[2];          // accumulator buffer complete
+    __shared__ uint64_t acc_empty[2];         // accumulator buffer folded
+    __shared__ uint64_t drain_bar;            // all MMAs of the CTA done
     __shared__ uint32_t tmem_base;
-    __shared__ int s_in[N], s_out[N];
-    __shared__ float s_bscale[N], s_oscale[N];   // input scale, output unscale per pair
+    __shared__ int s_out[N];
+    __shared__ float s_oscale[N];             // output unscale per pair
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile_id = blockIdx.x / mgroups, mg = blockIdx.x % mgroups;
-    const int4 t = tiles[tile_id];
-    const int cnt = t.z;
-    const int m0 = mg * S::kRows;
-    const int arow = t.x * Qp + m0;       // first operator row of this CTA in the table
-    const int nchunks = (Qp + kKC - 1) / kKC;  // Qp is a multiple of 16; the tail is zero-filled
+    const int nst = (Qp + kKS - 1) / kKS;                     // stages per item (tail zero-filled)
+    const int nfg = (nst + kFoldStages - 1) / kFoldStages;   // accumulators per item
+    volatile int* abort = &s_abort;
+    auto stage_u32 = [&](int s) -> uint32_t { return smem_u32(base) + (uint32_t)(s * S::kStageBytes); };
 
-    for (int j = tid; j < N; j += kThreads) {
-        const int bi = j < cnt ? pin[t.y + j] : -1;
-        s_in[j] = bi;
-        s_out[j] = j < cnt ? pout[t.y + j] : -1;
-        const int e = bi >= 0 ? bexp[bi] : 0;
-        s_bscale[j] = pow2f(e);
-        s_oscale[j] = pow2f(-(e + texp));
-    }
-    auto stage_base = [&](int st) -> unsigned char* { return base + st * S::kStageBytes; };
-    auto issue_tma = [&](int c) {
-        unsigned char* sb = stage_base(c & 1);
-        mbar_expect_tx(&full_bar[c & 1], 2u * S::kABytes);
-        tma_load_2d(smem_u32(sb), &map_hi, c * kKC, arow, &full_bar[c & 1]);
-        tma_load_2d(smem_u32(sb + S::kABytes), &map_lo, c * kKC, arow, &full_bar[c & 1]);
-    };
     if (tid == 0) {
         s_abort = 0;
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&full_bar[i], 1);
-            mbar_init(&mma_bar[i], 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&tma_full[i], 1);
+            mbar_init(&b_full[i], kProdThreads);
+            mbar_init(&empty[i], 1);
         }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], kFoldThreads);
+        }
+        mbar_init(&drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        issue_tma(0);
-        if (nchunks > 1) issue_tma(1);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -267,146 +282,204 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    constexpr uint32_t idesc = idesc_f16(128, N);
 
-    // this warp's accumulator columns: lane quarter q, slab my_slab, columns [my_col0, +128)
-    const int quarter = warp & 3, half = warp >> 2;
-    const int my_slab = (half * 128) / N, my_col0 = (half * 128) % N;
-    float acc[128];
-#pragma unroll
-    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
-
-    // staged B: scaled, split and packed at load time (8 FP16 per 16-byte group)
-    uint4 rhi[S::kBVec], rlo[S::kBVec];
-    auto load_b = [&](int c) {
-        const int k0 = c * kKC;
-#pragma unroll
-        for (int i = 0; i < S::kBVec; ++i) {
-            int r, ch;
-            chunk_coord(tid + i * kThreads, r, ch);
-            int bi = s_in[r], k = k0 + 8 * ch;   // an 8-group lies wholly inside or outside Qp
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-            if (bi >= 0 && k < Qp) {
-                const float4* src = reinterpret_cast<const float4*>(in + (size_t)bi * Qp + k);
-                a = src[0];
-                b = src[1];
+    if (warp == 0) {
+        // ---- operator rows by TMA ----
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (int k = 0; k < K && ok; ++k) {
+                const int w = (int)blockIdx.x + k * G;
+                const int arow = tiles[w / mgroups].x * Qp + (w % mgroups) * S::kRows;
+                for (int i = 0; i < nst; ++i, ++g) {
+                    const int s = g % kStages;
+                    if (g >= kStages && !mbar_wait_ab(&empty[s], (uint32_t)(((g / kStages) - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&tma_full[s], 2u * S::kABytes);
+                    tma_load_2d(stage_u32(s), &map_hi, i * kKS, arow, &tma_full[s]);
+                    tma_load_2d(stage_u32(s) + S::kABytes, &map_lo, i * kKS, arow, &tma_full[s]);
+                }
             }
-            split_f16x8(a, b, s_bscale[r], rhi[i], rlo[i]);
+            // every issued load has landed before the CTA can end (not cut short by an abort)
+            for (int s = 0; s < kStages && s < g; ++s) {
+                const int last = s + ((g - 1 - s) / kStages) * kStages;
+                if (!mbar_wait(&tma_full[s], (uint32_t)((last / kStages) & 1))) *abort = 1;
+            }
         }
-    };
-    auto store_b = [&](unsigned char* sb) {
-        unsigned char* bh = sb + 2 * S::kABytes;
+    } else if (warp == 1) {
+        // ---- MMA issue ----
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_f16(128, N);
+            bool ok = true, any = false;
+            int g = 0;
+            for (int k = 0; k < K && ok; ++k) {
+                for (int i = 0; i < nst; ++i, ++g) {
+                    const int s = g % kStages;
+                    const int f = k * nfg + i / kFoldStages, b = f & 1;
+                    const bool first = i % kFoldStages == 0;
+                    const bool last = i % kFoldStages == kFoldStages - 1 || i == nst - 1;
+                    if (first && f >= 2 && !mbar_wait_ab(&acc_empty[b], (uint32_t)(((f >> 1) - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                    if (!mbar_wait_ab(&tma_full[s], ph, abort) || !mbar_wait_ab(&b_full[s], ph, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // the small correction products of this stage now; the hi*hi products of
+                    // every stage of the accumulator last, once all its stages are resident
+                    // (the same order as one 64-column K step: fewer truncating adds at the
+                    // accumulator's full magnitude)
+                    const uint32_t a_hi = stage_u32(s), a_lo = a_hi + S::kABytes;
+                    const uint32_t b_hi = a_hi + 2 * S::kABytes, b_lo = b_hi + S::kBBytes;
 #pragma unroll
-        for (int i = 0; i < S::kBVec; ++i) {
-            int r, ch;
-            chunk_coord(tid + i * kThreads, r, ch);
-            uint32_t o = (uint32_t)((r >> 7) * kSlabBytes) + sw128_off(r & 127, ch);
-            *reinterpret_cast<uint4*>(bh + o) = rhi[i];
-            *reinterpret_cast<uint4*>(bh + S::kBBytes + o) = rlo[i];
+                    for (int sl = 0; sl < SLABS; ++sl) {
+                        const uint32_t d = tmem + (uint32_t)(b * S::kBufCols + sl * N);
+                        const uint32_t ao = (uint32_t)(sl * kSlabBytes);
+#pragma unroll
+                        for (int ks = 0; ks < kKS / 16; ++ks) {
+                            const uint32_t koff = ks * 32;  // 16 FP16 along K inside the swizzled row
+                            mma_f16(d, smem_desc(a_hi + ao + koff), smem_desc(b_lo + koff), idesc,
+                                    (first && ks == 0) ? 0u : 1u);
+                            mma_f16(d, smem_desc(a_lo + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
+                        }
+                    }
+                    any = true;
+                    if (last) {
+                        const int g0 = g - i % kFoldStages;   // first stage of this accumulator
+                        for (int gg = g0; gg <= g; ++gg) {
+                            const uint32_t ah = stage_u32(gg % kStages), bh = ah + 2 * S::kABytes;
+#pragma unroll
+                            for (int sl = 0; sl < SLABS; ++sl) {
+                                const uint32_t d = tmem + (uint32_t)(b * S::kBufCols + sl * N);
+                                const uint32_t ao = (uint32_t)(sl * kSlabBytes);
+#pragma unroll
+                                for (int ks = 0; ks < kKS / 16; ++ks) {
+                                    const uint32_t koff = ks * 32;
+                                    mma_f16(d, smem_desc(ah + ao + koff), smem_desc(bh + koff), idesc, 1u);
+                                }
+                            }
+                        }
+                        for (int gg = g0; gg <= g; ++gg) mma_commit(&empty[gg % kStages]);
+                        mma_commit(&acc_full[b]);
+                    }
+                }
+            }
+            // every MMA (and the arrivals it owes) is done before the CTA can end
+            if (any) {
+                mma_commit(&drain_bar);
+                if (!mbar_wait(&drain_bar, 0)) *abort = 1;
+            }
         }
-    };
-    auto fold = [&](int b) {
-        const uint32_t col = (uint32_t)(b * S::kBufCols + my_slab * N + my_col0);
+    } else if (warp < kFoldWarp0) {
+        // ---- input rows by cp.async: thread pt copies 16-byte chunk pt % 4 of rows
+        // pt / 4 + 16 j, so four neighbouring threads read one 64-byte row slice ----
+        const int pt = tid - kProdWarp0 * 32, rr = pt >> 2, c = pt & 3;
+        int bi[S::kBRows];
+        int g = 0;
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) {
+            const int w = (int)blockIdx.x + k * G;
+            const int4 t = tiles[w / mgroups];
 #pragma unroll
-        for (int j0 = 0; j0 < 128; j0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)j0, v);
+            for (int j = 0; j < S::kBRows; ++j) {
+                const int r = j * 16 + rr;
+                bi[j] = r < t.z ? pin[t.y + r] : -1;
+            }
+            for (int i = 0; i < nst; ++i, ++g) {
+                const int s = g % kStages;
+                if (g >= kStages && !mbar_wait_ab(&empty[s], (uint32_t)(((g / kStages) - 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t bh = stage_u32(s) + 2 * S::kABytes;
+                const int kk = i * kKS + 8 * c;          // an 8-group lies wholly inside or outside Qp
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j0 + j] += v[j];
+                for (int j = 0; j < S::kBRows; ++j) {
+                    const bool v = bi[j] >= 0 && kk < Qp;
+                    const size_t off = v ? (size_t)bi[j] * Qp + kk : 0;
+                    const uint32_t o = sw64_off(j * 16 + rr, c);
+                    cp_async16(bh + o, in_hi + off, v ? 16u : 0u);
+                    cp_async16(bh + S::kBBytes + o, in_lo + off, v ? 16u : 0u);
+                }
+                cp_async_commit();
+                if (g >= kBLag) {
+                    // stage g - kBLag: this thread's copies have landed; hand them to the
+                    // tensor core's (async) proxy and arrive
+                    cp_async_wait<kBLag>();
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(&b_full[(g - kBLag) % kStages]);
+                }
+            }
         }
-    };
-
-    // thread 0 bookkeeping: last chunk whose MMAs were committed, last chunk whose TMA
-    // was issued / waited for, and whether a wait gave up
-    int issued = -1, tma_issued = nchunks > 1 ? 1 : 0, tma_waited = -1;
-    bool dead = false;
-    load_b(0);
-    for (int c = 0; c < nchunks; ++c) {
-        const int b = c & 1;
-        unsigned char* sb = stage_base(b);
-        // stage b / accumulator buffer b were last used by chunk c - 2: waited for and
-        // folded in the previous iteration
-        store_b(sb);
-        if (c + 1 < nchunks) load_b(c + 1);       // in flight while this chunk multiplies
+        cp_async_wait<0>();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0 && !dead) {
-            if (!mbar_wait(&full_bar[b], (uint32_t)((c >> 1) & 1))) {
-                dead = true;
-                s_abort = 1;
-            } else {
-                tma_waited = c;
+        if (ok)
+            for (int gg = g > kBLag ? g - kBLag : 0; gg < g; ++gg) mbar_arrive(&b_full[gg % kStages]);
+    } else {
+        // ---- fold and epilogue: lane quarter warp % 4 (the TMEM lanes this warp may
+        // read), slab my_slab, accumulator columns [my_col0, +128) ----
+        const int fw = warp - kFoldWarp0, ft = tid - kFoldWarp0 * 32;
+        const int quarter = warp & 3, half = fw >> 2;
+        const int my_slab = (half * 128) / N, my_col0 = (half * 128) % N;
+        float acc[128];
+        auto load_meta = [&](int k) {
+            const int w = (int)blockIdx.x + k * G;
+            const int4 t = tiles[w / mgroups];
+            for (int j = ft; j < N; j += kFoldThreads) {
+                const int bi = j < t.z ? pin[t.y + j] : -1;
+                s_out[j] = j < t.z ? pout[t.y + j] : -1;
+                s_oscale[j] = pow2f(-((bi >= 0 ? bexp[bi] : 0) + texp));
+            }
+        };
+        load_meta(0);
+        bar_named(kFoldBar, kFoldThreads);
+        for (int k = 0; k < K; ++k) {
+            const int w = (int)blockIdx.x + k * G;
+#pragma unroll
+            for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+            bool ok = true;
+            for (int j = 0; j < nfg; ++j) {
+                const int f = k * nfg + j, b = f & 1;
+                if (!mbar_wait_ab(&acc_full[b], (uint32_t)((f >> 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
-                const uint32_t a_hi = smem_u32(sb), a_lo = a_hi + S::kABytes;
-                const uint32_t b_hi = a_hi + 2 * S::kABytes, b_lo = b_hi + S::kBBytes;
+                const uint32_t col = (uint32_t)(b * S::kBufCols + my_slab * N + my_col0);
 #pragma unroll
-                for (int sl = 0; sl < SLABS; ++sl) {
-                    const uint32_t d = tmem + (uint32_t)(b * S::kBufCols + sl * N);
-                    const uint32_t ao = (uint32_t)(sl * kSlabBytes);
-                    // small correction products first, then the hi*hi products
+                for (int j0 = 0; j0 < 128; j0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)j0, v);
 #pragma unroll
-                    for (int ks = 0; ks < kKC / 16; ++ks) {
-                        const uint32_t koff = ks * 32;  // 16 FP16 along K inside the swizzled row
-                        mma_f16(d, smem_desc(a_hi + ao + koff), smem_desc(b_lo + koff), idesc, ks > 0 ? 1u : 0u);
-                        mma_f16(d, smem_desc(a_lo + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
-                    }
-#pragma unroll
-                    for (int ks = 0; ks < kKC / 16; ++ks) {
-                        const uint32_t koff = ks * 32;
-                        mma_f16(d, smem_desc(a_hi + ao + koff), smem_desc(b_hi + koff), idesc, 1u);
-                    }
+                    for (int jj = 0; jj < 16; ++jj) acc[j0 + jj] += v[jj];
                 }
-                mma_commit(&mma_bar[b]);
-                issued = c;
+                tc_fence_before();
+                mbar_arrive(&acc_empty[b]);
             }
-        }
-        if (c >= 1) {
-            const int pc = c - 1;
-            if (tid == 0 && !dead) {
-                if (!mbar_wait(&mma_bar[pc & 1], (uint32_t)((pc >> 1) & 1))) {
-                    dead = true;
-                    s_abort = 1;
-                } else if (c + 1 < nchunks) {
-                    issue_tma(c + 1);              // its stage was read by chunk c - 1, now done
-                    tma_issued = c + 1;
+            if (bar_named_or(kFoldBar, kFoldThreads, !ok)) break;   // uniform across the fold warps
+            const int row = (w % mgroups) * S::kRows + my_slab * 128 + quarter * 32 + lane;
+            if (row < Q) {
+#pragma unroll
+                for (int j = 0; j < 128; ++j) {
+                    const int ob = s_out[my_col0 + j];
+                    if (ob >= 0) atomicAdd(out + (size_t)ob * Qp + row, acc[j] * s_oscale[my_col0 + j]);
                 }
             }
-            __syncthreads();
-            if (s_abort) break;
-            tc_fence_after();
-            fold(pc & 1);
-            tc_fence_before();
-        }
-    }
-    // the last chunk
-    if (tid == 0 && !dead) {
-        if (issued != nchunks - 1 || !mbar_wait(&mma_bar[issued & 1], (uint32_t)((issued >> 1) & 1))) {
-            dead = true;
-            s_abort = 2;
-        }
-    }
-    __syncthreads();
-    if (!s_abort) {
-        tc_fence_after();
-        fold((nchunks - 1) & 1);          // uniform: every thread folds the last chunk's buffer
-        const int row = m0 + my_slab * 128 + quarter * 32 + lane;
-        if (row < Q) {
-#pragma unroll
-            for (int j = 0; j < 128; ++j) {
-                int ob = s_out[my_col0 + j];
-                if (ob >= 0) atomicAdd(out + (size_t)ob * Qp + row, acc[j] * s_oscale[my_col0 + j]);
+            if (k + 1 < K) {
+                bar_named(kFoldBar, kFoldThreads);   // every fold thread is done with item k's table
+                load_meta(k + 1);
+                bar_named(kFoldBar, kFoldThreads);
             }
         }
-    } else if (tid == 0) {
-        // a wait gave up: one more bounded wait for the work in flight, then report
-        if (issued >= 0) mbar_wait(&mma_bar[issued & 1], (uint32_t)((issued >> 1) & 1));
-        for (int ch = tma_waited + 1; ch <= tma_issued; ++ch)
-            mbar_wait(&full_bar[ch & 1], (uint32_t)((ch >> 1) & 1));
-        atomicOr(err, s_abort);
     }
     tc_fence_before();
     __syncthreads();
+    if (tid == 0 && s_abort) atomicOr(err, 1);
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols)
@@ -415,14 +488,16 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
 }
 
 // One kernel name per translation so profiles tell them apart.
-#define KF_TC_KERNEL(NAME)                                                                                    \
-    template <int SLABS, int N>                                                                               \
-    __global__ void __launch_bounds__(kThreads, 1)                                                            \
-        NAME(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int Q,   \
-             int Qp, int mgroups, const int4* __restrict__ tiles, const int* __restrict__ pin,                \
-             const int* __restrict__ pout, const int* __restrict__ bexp, int texp, const float* __restrict__ in, \
-             float* __restrict__ out, int* __restrict__ err) {                                                 \
-        pair_tc_body<SLABS, N>(map_hi, map_lo, texp, Q, Qp, mgroups, tiles, pin, pout, bexp, in, out, err);    \
+#define KF_TC_KERNEL(NAME)                                                                                      \
+    template <int SLABS, int N>                                                                                 \
+    __global__ void __launch_bounds__(kThreads, 1)                                                              \
+        NAME(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int Q,     \
+             int Qp, int mgroups, int nitems, const int4* __restrict__ tiles, const int* __restrict__ pin,      \
+             const int* __restrict__ pout, const int* __restrict__ bexp, int texp,                               \
+             const __half* __restrict__ in_hi, const __half* __restrict__ in_lo, float* __restrict__ out,        \
+             int* __restrict__ err) {                                                                            \
+        pair_tc_body<SLABS, N>(map_hi, map_lo, texp, Q, Qp, mgroups, nitems, tiles, pin, pout, bexp, in_hi,     \
+                               in_lo, out, err);                                                                 \
     }
 KF_TC_KERNEL(k_u2u_tc)
 KF_TC_KERNEL(k_m2l_tc)

@@ -35,13 +35,15 @@ struct Plan {
     // operators (Real = double for FP64, float for mixed), each Qp x Qp row-major;
     // mixed: the translation tables live as scaled FP16 hi/lo pairs (tab_h/tab_l per
     // family 0 M2M', 1 M2L', 2 L2L'; the FP32 builds are released), texp their scales,
-    // tmaps[family][0 = hi, 1 = lo] their TMA tensor maps, bexp the per-box input scales
+    // tmaps[family][0 = hi, 1 = lo] their TMA tensor maps; bexp the per-box input scales
+    // and vin_h/vin_l the scaled, split input vectors of a translation (nbox x Qp each)
     DBuf<double> m2m_d, m2l_d, l2l_d, d2t_d;
     DBuf<float> m2m_f, m2l_f, l2l_f, d2t_f;
     DBuf<__half> tab_h[3], tab_l[3];
     int texp[3] = {0, 0, 0};
     CUtensorMap tmaps[3][2];
     DBuf<int> bexp;
+    DBuf<__half> vin_h, vin_l;
     DBuf<double> surf_d;            // Q x 3 unit surface
     DBuf<float> surf_f;
 
