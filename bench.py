@@ -132,15 +132,26 @@ def make_inputs(name, device):
 
 
 def oracle_sample(wl, m, q_host, n_sample, seed=12345):
-    """Time the FP64 oracle on a seeded sample of targets (the CPU baseline)."""
+    """Time the FP64 oracle on a seeded sample of targets (the CPU baseline).  In a
+    forest of instances a target sums over its own instance's sources only."""
     import oracle
     from oracle.quadrature import quadrature_points
     xyz, w, nrm = quadrature_points(m.tri, m.sph)
     idx = np.sort(np.random.default_rng(seed).choice(m.n, size=min(n_sample, m.n), replace=False))
     kern = wl["kernel"]
+    off = wl.get("instances")
+    if off is None:
+        off = np.array([0, m.n], dtype=np.int64)
+    which = np.searchsorted(off, idx, side="right") - 1
+    ref = np.empty(idx.size)
     t0 = time.perf_counter()
-    ref = oracle.direct(kern, xyz, xyz, q_host, src_nrm=nrm if kern == "dl" else None,
-                        trg_nrm=nrm if kern == "adl" else None, idx=idx)
+    for i in np.unique(which):
+        a, b = int(off[i]), int(off[i + 1])
+        sel = which == i
+        sl = slice(a, b)
+        ref[sel] = oracle.direct(kern, xyz[:, sl], xyz[:, sl], q_host[sl],
+                                 src_nrm=nrm[:, sl] if kern == "dl" else None,
+                                 trg_nrm=nrm[:, sl] if kern == "adl" else None, idx=idx[sel] - a)
     dt = time.perf_counter() - t0
     return idx, ref, dt, oracle.max_threads()
 
@@ -179,7 +190,8 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": args.workload, "n_targets": m.n,
                                             "sample_targets_per_step": sample},
             "cpu_baseline": {"value": value, "unit": "targets/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d seeded targets x all %d sources per step" % (sample, m.n)},
+                             "sample": "%d seeded targets x all %d sources%s per step"
+                                       % (sample, m.n, " of their instance" if "instances" in wl else "")},
             "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -195,10 +207,17 @@ def run_kifmm(args):
     torch.cuda.set_device(device)
     from paper_1605_01715_gb300 import Plan, Tree
     wl, m, xyz, w, nrm, q = make_inputs(args.workload, device)
+    inst = wl.get("instances")
     p = args.p or wl["p"]
     max_leaf = args.max_leaf or wl["max_leaf"]
+    tune = None
+    if inst is not None and not args.no_autotune and not (args.p and args.max_leaf):
+        from paper_1605_01715_gb300.autotune import autotune
+        tune = autotune(xyz, q, wl["kernel"], inst, nrm=nrm if wl["kernel"] != "sl" else None,
+                        log=lambda msg: print(msg, file=sys.stderr, flush=True))
+        p, max_leaf = args.p or tune["p"], args.max_leaf or tune["max_leaf"]
     t0 = time.perf_counter()
-    tree = Tree(xyz, max_leaf=max_leaf)
+    tree = Tree(xyz, max_leaf=max_leaf, instances=inst)
     torch.cuda.synchronize()
     t_tree = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -208,13 +227,17 @@ def run_kifmm(args):
     n = m.n
     out = torch.empty(n, dtype=torch.float64, device=device)
     stream = torch.cuda.current_stream()
+    # a batch of instances replays one captured graph per matvec; single instances
+    # launch directly, with the library's phase events inside the timed region
+    use_graph = inst is not None or args.graph
+    matvec = plan.matvec_graph if use_graph else plan.matvec
 
     for _ in range(args.warmup):
-        plan.matvec(q, out)
+        matvec(q, out)
     torch.cuda.synchronize()
 
-    # device-timed region (per-phase CUDA events recorded by the library on the same stream)
-    plan.profile(True)
+    # device-timed region
+    plan.profile(not use_graph)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if ws > 1:
         torch.distributed.barrier()
@@ -222,12 +245,18 @@ def run_kifmm(args):
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            plan.matvec(q, out)
+            matvec(q, out)
         ev1.record(stream)
         torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     phases = plan.profile(False)
+    if use_graph:                                  # phase breakdown from direct launches
+        plan.profile(True)
+        for _ in range(min(args.steps, 10)):
+            plan.matvec(q, out)
+        torch.cuda.synchronize()
+        phases = plan.profile(False)
     ms = ev0.elapsed_time(ev1) / args.steps
     ms_t = torch.tensor([ms], device=device)
     if ws > 1:
@@ -241,14 +270,14 @@ def run_kifmm(args):
     q_dev = torch.empty_like(q)
     for _ in range(2):
         q_dev.copy_(q_host, non_blocking=True)
-        plan.matvec(q_dev, out)
+        matvec(q_dev, out)
         out_host.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         q_dev.copy_(q_host, non_blocking=True)
-        plan.matvec(q_dev, out)
+        matvec(q_dev, out)
         out_host.copy_(out, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -270,12 +299,18 @@ def run_kifmm(args):
                        "l2": "no flush: per-step working set %.2f GB > 129 MB L2" % (st["device_bytes"] / 1e9),
                        "tree": {k: tst[k] for k in ("n_boxes", "n_leaves", "n_levels", "n_v", "n_w", "n_x",
                                                      "p2p_pairs")},
-                       "tree_build_ms": t_tree * 1e3, "setup_ms": t_setup * 1e3},
+                       "tree_build_ms": t_tree * 1e3, "setup_ms": t_setup * 1e3,
+                       "instances": 1 if inst is None else int(len(inst) - 1), "graph": bool(use_graph)},
             "phases_ms": phases,
             "e2e": {"value": n * ws / (ms_e2e * 1e-3), "unit": "targets/s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n},
             "gpu_launches": st["launches_per_matvec"] * args.steps,
             "clocks": clk.summary()}
+    if tune is not None:
+        line["config"]["autotune"] = {k: tune[k] for k in ("p", "max_leaf", "est_err", "subset_points",
+                                                           "subset_instances", "tune_s")}
+        line["config"]["autotune"]["errors"] = {str(k): v for k, v in tune["errors"].items()}
+        line["config"]["autotune"]["times_ms"] = {str(k): v for k, v in tune["times_ms"].items()}
     line["roofline"] = roofline(phases, st, tst, args)
 
     if args.solves > 0:
@@ -284,7 +319,8 @@ def run_kifmm(args):
         idx, ref, dt, cores = oracle_sample(wl, m, q.cpu().numpy(), args.cpu_sample)
         got = out.cpu().numpy()[idx]
         line["cpu_baseline"] = {"value": idx.size / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d seeded targets x all %d sources (FP64 direct sum)" % (idx.size, n)}
+                                "sample": "%d seeded targets x all %d sources of their instance (FP64 direct sum)"
+                      % (idx.size, n)}
         line["rel_err_sampled"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -412,6 +448,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="batch workloads: take p / leaf from the workload")
+    ap.add_argument("--graph", action="store_true", help="time captured-graph matvecs (always for batches)")
     ap.add_argument("--solves", type=int, default=5, help="timed polarization solves (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -93,12 +93,36 @@ int kifmm_tree_build(const double* src_xyz, int64_t n_src,
                      const double* trg_xyz, int64_t n_trg,
                      int max_leaf, void* stream, kifmm_tree* out);
 
+/*
+ * Forest of independent instances in one tree (no counterpart in the paper, which
+ * evaluates one boundary at a time): instance i is input points
+ * [inst_off[i], inst_off[i+1]) and is both the sources and the targets of its own sum;
+ * no instance sees another.  Each instance is translated (never scaled, so the sums,
+ * the 1e-5 exclusion radius and the accuracy are those of the instance alone) into its
+ * own cell of a 2^L x 2^L x 2^L grid, 8^L >= n_inst, with cells as wide as the widest
+ * instance plus 1 %; the grid cells are the boxes of level L and no interaction list
+ * crosses them.  Plans, matvecs and solves on the returned tree then run every FMM
+ * phase as one launch for all instances, with inputs and outputs in the
+ * concatenated input order.
+ *   xyz       device, 3*n FP64 SoA, instances back to back.   1 <= n < 2^31.
+ *   inst_off  host, n_inst+1 int64: 0 = inst_off[0] < inst_off[1] < ... = n.
+ *   n_inst    1..KIFMM_MAX_INSTANCES.
+ *   max_leaf, stream, out  as for kifmm_tree_build.
+ * Errors: INVALID_ARG (sizes, offsets, empty instance, non-finite coordinates), OOM,
+ * CUDA.
+ */
+#define KIFMM_MAX_INSTANCES 32768
+int kifmm_forest_build(const double* xyz, int64_t n, const int64_t* inst_off, int n_inst,
+                       int max_leaf, void* stream, kifmm_tree* out);
+
 typedef struct {
     int64_t n_src, n_trg;
     int32_t n_boxes, n_leaves, n_levels, max_leaf;
     int64_t n_u, n_v, n_w, n_x;       /* total interaction-list entries           */
     int64_t p2p_pairs;                /* sum over target leaves of n_trg * U/W sources */
     double  root_center[3], root_half;
+    int32_t n_instances;              /* 1, or the forest's instance count          */
+    int32_t forest_level;             /* -1, or the level whose boxes are instances */
 } kifmm_tree_stats;
 
 /* Fill *stats (host).  Errors: INVALID_ARG. */
@@ -158,6 +182,18 @@ int kifmm_fmm_setup(kifmm_tree tree, int kernel, int p, int precision, double pi
  * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA.
  */
 int kifmm_fmm_matvec(kifmm_plan plan, const double* q, double* out, void* stream);
+
+/*
+ * The same matvec replayed from a CUDA graph (no counterpart in the paper): the
+ * first call for a given (q, out) pair captures one matvec's launches on a private
+ * stream and instantiates them; every call then launches the graph on `stream`, so
+ * a matvec costs one launch on the host whatever the tree's depth.  The graph reads
+ * q and writes out by address: refill q in place between calls.  A call with other
+ * pointers captures again.  Profiling events are not recorded inside the graph.
+ * Errors: INVALID_ARG, CUDA (capture or instantiation failed; the plan stays usable
+ * through kifmm_fmm_matvec).
+ */
+int kifmm_fmm_matvec_graph(kifmm_plan plan, const double* q, double* out, void* stream);
 
 typedef struct {
     int32_t kernel, p, q_points, precision;

@@ -13,6 +13,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,7 +42,8 @@ class TreeStats(ctypes.Structure):
                 ("n_levels", ctypes.c_int32), ("max_leaf", ctypes.c_int32),
                 ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64), ("n_w", ctypes.c_int64),
                 ("n_x", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
-                ("root_center", ctypes.c_double * 3), ("root_half", ctypes.c_double)]
+                ("root_center", ctypes.c_double * 3), ("root_half", ctypes.c_double),
+                ("n_instances", ctypes.c_int32), ("forest_level", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -68,6 +70,7 @@ _SIGS = {
     "kifmm_version": ([], ctypes.c_char_p),
     "kifmm_quadrature_points": ([_P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "kifmm_tree_build": ([_P, _I64, _P, _I64, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "kifmm_forest_build": ([_P, _I64, _P, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "kifmm_tree_get_stats": ([_P, ctypes.POINTER(TreeStats)], ctypes.c_int),
     "kifmm_tree_export": ([_P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "kifmm_tree_export_list": ([_P, ctypes.c_int, _P, _P], ctypes.c_int),
@@ -75,6 +78,7 @@ _SIGS = {
     "kifmm_fmm_setup": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                          ctypes.POINTER(_P)], ctypes.c_int),
     "kifmm_fmm_matvec": ([_P, _P, _P, _P], ctypes.c_int),
+    "kifmm_fmm_matvec_graph": ([_P, _P, _P, _P], ctypes.c_int),
     "kifmm_plan_get_stats": ([_P, ctypes.POINTER(PlanStats)], ctypes.c_int),
     "kifmm_plan_profile": ([_P, ctypes.c_int, _P], ctypes.c_int),
     "kifmm_plan_check": ([_P], ctypes.c_int),
@@ -148,15 +152,26 @@ def kifmm_quadrature_points(tri, sph, stream=None):
 
 
 class Tree:
-    """Owns a kifmm_tree handle (kifmm_tree_build / kifmm_tree_destroy)."""
+    """Owns a kifmm_tree handle (kifmm_tree_build / kifmm_forest_build /
+    kifmm_tree_destroy).  ``instances``: offsets (n_inst + 1 ints, 0 ... n) of
+    independent instances stored back to back in ``src_xyz`` -- a forest, where each
+    instance is its own sources and targets (``trg_xyz`` must then be None)."""
 
-    def __init__(self, src_xyz, trg_xyz=None, max_leaf=64, stream=None):
+    def __init__(self, src_xyz, trg_xyz=None, max_leaf=64, stream=None, instances=None):
         h = ctypes.c_void_p()
         ns = src_xyz.shape[-1]
-        nt = trg_xyz.shape[-1] if trg_xyz is not None else 0
-        _check(lib().kifmm_tree_build(_dev(src_xyz, 3 * ns, "src_xyz"), ns,
-                                      _dev(trg_xyz, 3 * nt, "trg_xyz"), nt, int(max_leaf),
-                                      _stream(stream), ctypes.byref(h)))
+        if instances is not None:
+            if trg_xyz is not None:
+                raise ValueError("a forest's targets are its sources")
+            off = np.ascontiguousarray(instances, dtype=np.int64)
+            _check(lib().kifmm_forest_build(_dev(src_xyz, 3 * ns, "src_xyz"), ns, off.ctypes.data,
+                                            int(off.size - 1), int(max_leaf), _stream(stream),
+                                            ctypes.byref(h)))
+        else:
+            nt = trg_xyz.shape[-1] if trg_xyz is not None else 0
+            _check(lib().kifmm_tree_build(_dev(src_xyz, 3 * ns, "src_xyz"), ns,
+                                          _dev(trg_xyz, 3 * nt, "trg_xyz"), nt, int(max_leaf),
+                                          _stream(stream), ctypes.byref(h)))
         self.handle = h
         self._lib = lib()
 
@@ -227,6 +242,13 @@ class Plan:
             out = torch.empty(self.n_trg, dtype=torch.float64, device=q.device)
         _check(lib().kifmm_fmm_matvec(self.handle, _dev(q, self.n_src, "q"), _dev(out, self.n_trg, "out"),
                                       _stream(stream)))
+        return out
+
+    def matvec_graph(self, q, out, stream=None):
+        """kifmm_fmm_matvec_graph: replay a captured matvec reading ``q`` and writing
+        ``out`` by address (both must stay allocated; refill ``q`` in place)."""
+        _check(lib().kifmm_fmm_matvec_graph(self.handle, _dev(q, self.n_src, "q"),
+                                            _dev(out, self.n_trg, "out"), _stream(stream)))
         return out
 
     def check(self):

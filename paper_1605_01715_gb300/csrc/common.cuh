@@ -115,6 +115,8 @@ struct Tree {
     int64_t ns = 0, nt = 0;
     bool same = true;                   // targets are the sources
     int max_leaf = 0;
+    int forest_level = -1;              // forest: level whose boxes are the instances
+    std::vector<int64_t> inst_off;      // forest: instance i owns input points [inst_off[i], inst_off[i+1])
     double root_c[3] = {0, 0, 0};
     double root_h = 0;                  // half-width of the root cube
     int nbox = 0, nlev = 0, nleaf = 0;

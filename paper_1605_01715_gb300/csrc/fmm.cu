@@ -890,6 +890,49 @@ extern "C" int kifmm_fmm_matvec(kifmm_plan plan, const double* q, double* out, v
     return plan_matvec(plan->P, q, out, (cudaStream_t)stream);
 }
 
+extern "C" int kifmm_fmm_matvec_graph(kifmm_plan plan, const double* q, double* out, void* stream) {
+    clear_error();
+    KF_ARG(plan && q && out, "NULL plan, q or out");
+    Plan& P = plan->P;
+    if (!P.gexec || P.g_q != q || P.g_out != out) {
+        if (P.gexec) {
+            KF_CHECK_CUDA(cudaGraphExecDestroy(P.gexec));
+            P.gexec = nullptr;
+        }
+        if (!P.cap_stream) KF_CHECK_CUDA(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+        // capture the launches of one matvec (no profiling events inside the graph)
+        const bool prof = P.profile;
+        const int launches = P.launches;
+        P.profile = false;
+        KF_CHECK_CUDA(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = plan_matvec(P, q, out, P.cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(P.cap_stream, &g);
+        P.profile = prof;
+        P.launches = launches;
+        if (rc != KIFMM_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (rc == KIFMM_OK) {
+                set_error("matvec capture failed: %s", cudaGetErrorString(ce));
+                rc = KIFMM_ERR_CUDA;
+            }
+            cudaGetLastError();
+            return rc;
+        }
+        cudaError_t ie = cudaGraphInstantiate(&P.gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            P.gexec = nullptr;
+            set_error("matvec graph instantiation failed: %s", cudaGetErrorString(ie));
+            return KIFMM_ERR_CUDA;
+        }
+        P.g_q = q;
+        P.g_out = out;
+    }
+    KF_CHECK_CUDA(cudaGraphLaunch(P.gexec, (cudaStream_t)stream));
+    return KIFMM_OK;
+}
+
 extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     clear_error();
     KF_ARG(plan && st, "NULL plan or stats");

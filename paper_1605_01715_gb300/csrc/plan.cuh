@@ -74,10 +74,19 @@ struct Plan {
     int launches = 0;
     int64_t device_bytes = 0;
 
+    // captured matvec (kifmm_fmm_matvec_graph): the executable graph, the q / out it
+    // was captured for, and the private stream it was captured on
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const double* g_q = nullptr;
+    double* g_out = nullptr;
+
     ~Plan() {
         for (auto& sl : ev_slots)
             for (auto e : sl)
                 if (e) cudaEventDestroy(e);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };
 

@@ -107,7 +107,7 @@ __device__ inline int64_t lower_bound_u64(const uint64_t* a, int64_t lo, int64_t
 }
 
 // One thread per (box of this level, octant): child ranges and a non-empty flag.
-__global__ void k_split_count(int off, int nlevbox, int level, int max_leaf, bool same,
+__global__ void k_split_count(int off, int nlevbox, int level, int max_leaf, int force_level, bool same,
                               const uint64_t* __restrict__ skey, const uint64_t* __restrict__ tkey,
                               const uint64_t* __restrict__ code, const int64_t* __restrict__ rng,
                               int* __restrict__ leaf, int* __restrict__ flag,
@@ -116,7 +116,9 @@ __global__ void k_split_count(int off, int nlevbox, int level, int max_leaf, boo
     if (g >= nlevbox * 8) return;
     int b = off + g / 8, oct = g % 8;
     int64_t sb = rng[4 * b], se = rng[4 * b + 1], tb = rng[4 * b + 2], te = rng[4 * b + 3];
-    bool split = (max(se - sb, te - tb) > max_leaf) && (level < kMaxDepth);
+    // a forest splits every box above its instance level, whatever it holds
+    bool split = (max(se - sb, te - tb) > max_leaf || level < force_level) && (se > sb || te > tb) &&
+                 (level < kMaxDepth);
     if (oct == 0) leaf[b] = split ? 0 : 1;
     if (!split) {
         flag[g] = 0;
@@ -173,8 +175,51 @@ __global__ void k_split_emit(int off, int nlevbox, int level, int next_off,
     for (int k = 0; k < 8; ++k) child[8 * c + k] = -1;
 }
 
+// Forest set-up: bounding box of each instance (one block per instance), then every
+// point shifted by its instance's translation into the grid cell it owns.
+__global__ void k_inst_bbox(const double* __restrict__ xyz, int64_t n, const int64_t* __restrict__ off,
+                            double* __restrict__ out) {
+    __shared__ double red[6][128];
+    const int i = blockIdx.x;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t k = off[i] + threadIdx.x; k < off[i + 1]; k += blockDim.x)
+        for (int d = 0; d < 3; ++d) {
+            const double v = xyz[d * n + k];
+            lo[d] = fmin(lo[d], v);
+            hi[d] = fmax(hi[d], v);
+        }
+    for (int d = 0; d < 3; ++d) {
+        red[d][threadIdx.x] = lo[d];
+        red[3 + d][threadIdx.x] = hi[d];
+    }
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int d = 0; d < 3; ++d) {
+                red[d][threadIdx.x] = fmin(red[d][threadIdx.x], red[d][threadIdx.x + o]);
+                red[3 + d][threadIdx.x] = fmax(red[3 + d][threadIdx.x], red[3 + d][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[6 * i + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_inst_shift(const double* __restrict__ xyz, int64_t n, const int64_t* __restrict__ off,
+                             int ninst, const double* __restrict__ shift, double* __restrict__ out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int lo = 0, hi = ninst;                 // instance i with off[i] <= k < off[i + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    for (int d = 0; d < 3; ++d) out[d * n + k] = xyz[d * n + k] + shift[3 * lo + d];
+}
+
 struct ListCtx {
     LevelTable lt;
+    int forest_level;                   // -1: one instance; else instances own the boxes of this level
     const int* lvl;
     const int* coord;
     const int* parent;
@@ -211,6 +256,15 @@ __device__ inline bool adjacent(const ListCtx& c, int a, int b) {
     return true;
 }
 
+// Same instance: both boxes lie under one box of the forest level (always true for a
+// single-instance tree; boxes above the forest level belong to no instance).
+__device__ inline bool same_inst(const ListCtx& c, int a, int b) {
+    if (c.forest_level < 0) return true;
+    int la = c.lvl[a], lb = c.lvl[b];
+    if (la < c.forest_level || lb < c.forest_level) return false;
+    return (c.code[a] >> (3 * (la - c.forest_level))) == (c.code[b] >> (3 * (lb - c.forest_level)));
+}
+
 __device__ inline bool has_src(const ListCtx& c, int b) { return c.rng[4 * b + 1] > c.rng[4 * b]; }
 __device__ inline bool has_trg(const ListCtx& c, int b) { return c.rng[4 * b + 3] > c.rng[4 * b + 2]; }
 
@@ -231,7 +285,7 @@ __global__ void k_lists(ListCtx c, int nbox, int mode, ListOut o, int* err) {
     };
     int l = c.lvl[b];
     int bx = c.coord[3 * b], by = c.coord[3 * b + 1], bz = c.coord[3 * b + 2];
-    if (has_trg(c, b)) {
+    if (has_trg(c, b) && l >= c.forest_level) {
         // V list
         if (l >= 2) {
             int p = c.parent[b];
@@ -240,7 +294,7 @@ __global__ void k_lists(ListCtx c, int nbox, int mode, ListOut o, int* err) {
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dz = -1; dz <= 1; ++dz) {
                         int C = find_box(c, l - 1, px + dx, py + dy, pz + dz);
-                        if (C < 0 || c.leaf[C]) continue;
+                        if (C < 0 || c.leaf[C] || !same_inst(c, C, b)) continue;
                         for (int k = 0; k < 8; ++k) {
                             int A = c.child[8 * C + k];
                             if (A < 0 || !has_src(c, A)) continue;
@@ -261,7 +315,7 @@ __global__ void k_lists(ListCtx c, int nbox, int mode, ListOut o, int* err) {
                         for (int dz = -1; dz <= 1; ++dz) {
                             if (!dx && !dy && !dz) continue;
                             int A = find_box(c, lp, ax + dx, ay + dy, az + dz);
-                            if (A < 0 || !c.leaf[A] || !has_src(c, A)) continue;
+                            if (A < 0 || !c.leaf[A] || !has_src(c, A) || !same_inst(c, A, b)) continue;
                             if (adjacent(c, A, p) && !adjacent(c, A, b)) emit(3, A);
                         }
             }
@@ -274,7 +328,7 @@ __global__ void k_lists(ListCtx c, int nbox, int mode, ListOut o, int* err) {
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dz = -1; dz <= 1; ++dz) {
                         int C = find_box(c, l, bx + dx, by + dy, bz + dz);
-                        if (C < 0) continue;
+                        if (C < 0 || !same_inst(c, C, b)) continue;
                         if (c.leaf[C]) {
                             if (has_src(c, C)) emit(0, C);
                         } else {
@@ -315,7 +369,7 @@ __global__ void k_lists(ListCtx c, int nbox, int mode, ListOut o, int* err) {
                         for (int dz = -1; dz <= 1; ++dz) {
                             if (!dx && !dy && !dz) continue;
                             int A = find_box(c, lp, ax + dx, ay + dy, az + dz);
-                            if (A < 0 || !c.leaf[A] || !has_src(c, A)) continue;
+                            if (A < 0 || !c.leaf[A] || !has_src(c, A) || !same_inst(c, A, b)) continue;
                             if (adjacent(c, A, b)) emit(0, A);
                         }
             }
@@ -397,22 +451,30 @@ int bbox(const double* xyz, int64_t n, double lo[3], double hi[3], cudaStream_t 
     return KIFMM_OK;
 }
 
+// root_c / root_h: an explicit root cube (a forest's grid), or NULL to enclose the
+// points; forest_level: the level whose boxes are the instances (-1: one instance).
 int build(Tree& T, const double* src, int64_t ns, const double* trg, int64_t nt, int max_leaf,
-          cudaStream_t s) {
+          cudaStream_t s, const double* root_c = nullptr, double root_h = 0, int forest_level = -1) {
     T.ns = ns;
     T.same = (trg == nullptr);
     T.nt = T.same ? ns : nt;
     T.max_leaf = max_leaf;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    KF_TRY(bbox(src, ns, lo, hi, s));
-    if (!T.same) KF_TRY(bbox(trg, nt, lo, hi, s));
-    double ext = 0;
-    for (int d = 0; d < 3; ++d) {
-        T.root_c[d] = 0.5 * (lo[d] + hi[d]);
-        ext = std::max(ext, hi[d] - lo[d]);
+    T.forest_level = forest_level;
+    if (root_c) {
+        for (int d = 0; d < 3; ++d) T.root_c[d] = root_c[d];
+        T.root_h = root_h;
+    } else {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        KF_TRY(bbox(src, ns, lo, hi, s));
+        if (!T.same) KF_TRY(bbox(trg, nt, lo, hi, s));
+        double ext = 0;
+        for (int d = 0; d < 3; ++d) {
+            T.root_c[d] = 0.5 * (lo[d] + hi[d]);
+            ext = std::max(ext, hi[d] - lo[d]);
+        }
+        if (ext <= 0) ext = 1.0;
+        T.root_h = 0.5 * ext * (1.0 + 1e-6);
     }
-    if (ext <= 0) ext = 1.0;
-    T.root_h = 0.5 * ext * (1.0 + 1e-6);
     double x0[3] = {T.root_c[0] - T.root_h, T.root_c[1] - T.root_h, T.root_c[2] - T.root_h};
     double inv_cell = (double)(1u << kKeyBits) / (2.0 * T.root_h);
 
@@ -456,7 +518,7 @@ int build(Tree& T, const double* src, int64_t ns, const double* trg, int64_t nt,
         KF_TRY(grow(pos, 8 * (size_t)nl, 0, s));
         KF_TRY(grow(crng, 32 * (size_t)nl, 0, s));
         int g = 8 * nl;
-        k_split_count<<<div_up(g, 256), 256, 0, s>>>(off, nl, l, max_leaf, T.same, T.skey.p, tkey,
+        k_split_count<<<div_up(g, 256), 256, 0, s>>>(off, nl, l, max_leaf, forest_level, T.same, T.skey.p, tkey,
                                                       T.code.p, T.rng.p, T.leaf.p, flag.p, crng.p);
         KF_CHECK_LAUNCH();
         KF_TRY(exclusive_scan_int(flag.p, pos.p, g, s, tmp));
@@ -496,6 +558,7 @@ int build(Tree& T, const double* src, int64_t ns, const double* trg, int64_t nt,
     for (int l = 0; l <= T.nlev; ++l) c.lt.off[l] = T.level_off[l];
     for (int l = T.nlev + 1; l < kMaxDepth + 3; ++l) c.lt.off[l] = T.nbox;
     c.lt.nlev = T.nlev;
+    c.forest_level = forest_level;
     c.lvl = T.lvl.p;
     c.coord = T.coord.p;
     c.parent = T.parent.p;
@@ -580,6 +643,58 @@ int build(Tree& T, const double* src, int64_t ns, const double* trg, int64_t nt,
     return KIFMM_OK;
 }
 
+// Forest of independent instances (sources = targets): instance i's points are
+// translated, unscaled, into cell i (Morton order) of a 2^L x 2^L x 2^L grid whose cells
+// are as wide as the widest instance (plus a margin); the octree over the grid has the
+// cells as its level-L boxes and its lists never cross cells, so every FMM phase runs
+// once for all instances and no instance sees another.
+int build_forest(Tree& T, const double* xyz, int64_t n, const int64_t* h_off, int ninst, int max_leaf,
+                 cudaStream_t s) {
+    int L = 0;
+    while ((1LL << (3 * L)) < ninst) ++L;
+    DBuf<int64_t> off;
+    DBuf<double> bb, shift, moved;
+    KF_TRY(off.alloc(ninst + 1));
+    KF_TRY(bb.alloc(6 * (size_t)ninst));
+    KF_TRY(shift.alloc(3 * (size_t)ninst));
+    KF_TRY(moved.alloc(3 * (size_t)n));
+    KF_CHECK_CUDA(cudaMemcpyAsync(off.p, h_off, (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    k_inst_bbox<<<ninst, 128, 0, s>>>(xyz, n, off.p, bb.p);
+    KF_CHECK_LAUNCH();
+    std::vector<double> h_bb(6 * (size_t)ninst), h_shift(3 * (size_t)ninst);
+    KF_CHECK_CUDA(cudaMemcpyAsync(h_bb.data(), bb.p, h_bb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    double ext = 0;
+    for (int i = 0; i < ninst; ++i)
+        for (int d = 0; d < 3; ++d) {
+            if (!(h_bb[6 * i + d] <= h_bb[6 * i + 3 + d])) {
+                set_error("instance %d has non-finite coordinates", i);
+                return KIFMM_ERR_INVALID_ARG;
+            }
+            ext = std::max(ext, h_bb[6 * i + 3 + d] - h_bb[6 * i + d]);
+        }
+    const double cell = (ext > 0 ? ext : 1.0) * 1.01;   // every instance strictly inside its cell
+    for (int i = 0; i < ninst; ++i) {
+        int c[3] = {0, 0, 0};
+        for (int k = 0; k < L; ++k) {
+            c[0] |= ((i >> (3 * k + 2)) & 1) << k;
+            c[1] |= ((i >> (3 * k + 1)) & 1) << k;
+            c[2] |= ((i >> (3 * k)) & 1) << k;
+        }
+        for (int d = 0; d < 3; ++d)
+            h_shift[3 * i + d] = (c[d] + 0.5) * cell - 0.5 * (h_bb[6 * i + d] + h_bb[6 * i + 3 + d]);
+    }
+    KF_CHECK_CUDA(cudaMemcpyAsync(shift.p, h_shift.data(), h_shift.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_inst_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, n, off.p, ninst, shift.p, moved.p);
+    KF_CHECK_LAUNCH();
+    const double half = 0.5 * cell * (double)(1 << L);
+    const double rc[3] = {half, half, half};
+    KF_TRY(build(T, moved.p, n, nullptr, 0, max_leaf, s, rc, half, L));
+    T.inst_off.assign(h_off, h_off + ninst + 1);
+    KF_CHECK_CUDA(cudaStreamSynchronize(s));   // the translated copy is freed on return
+    return KIFMM_OK;
+}
+
 }  // namespace
 
 }  // namespace kifmm
@@ -611,6 +726,33 @@ extern "C" int kifmm_tree_build(const double* src_xyz, int64_t n_src, const doub
     return KIFMM_OK;
 }
 
+extern "C" int kifmm_forest_build(const double* xyz, int64_t n, const int64_t* inst_off, int n_inst,
+                                  int max_leaf, void* stream, kifmm_tree* out) {
+    clear_error();
+    KF_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    KF_ARG(xyz != nullptr && inst_off != nullptr, "xyz or inst_off is NULL");
+    KF_ARG(n >= 1 && n < (1LL << 31), "n must be in [1, 2^31)");
+    KF_ARG(n_inst >= 1 && n_inst <= KIFMM_MAX_INSTANCES, "n_inst must be in [1, KIFMM_MAX_INSTANCES]");
+    KF_ARG(max_leaf >= 1 && max_leaf <= 1024, "max_leaf must be in [1, 1024]");
+    KF_ARG(inst_off[0] == 0 && inst_off[n_inst] == n, "inst_off must run from 0 to n");
+    for (int i = 0; i < n_inst; ++i) KF_ARG(inst_off[i + 1] > inst_off[i], "every instance needs a point");
+    cudaStream_t s = (cudaStream_t)stream;
+    kifmm_tree t = new (std::nothrow) kifmm_tree_s;
+    if (!t) {
+        set_error("host allocation failed");
+        return KIFMM_ERR_OOM;
+    }
+    cudaGetDevice(&t->t.device);
+    int rc = build_forest(t->t, xyz, n, inst_off, n_inst, max_leaf, s);
+    if (rc != KIFMM_OK) {
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return KIFMM_OK;
+}
+
 extern "C" int kifmm_tree_get_stats(kifmm_tree tree, kifmm_tree_stats* st) {
     clear_error();
     KF_ARG(tree && st, "NULL handle or stats");
@@ -628,6 +770,8 @@ extern "C" int kifmm_tree_get_stats(kifmm_tree tree, kifmm_tree_stats* st) {
     st->p2p_pairs = T.p2p_pairs;
     for (int d = 0; d < 3; ++d) st->root_center[d] = T.root_c[d];
     st->root_half = T.root_h;
+    st->n_instances = T.forest_level < 0 ? 1 : (int32_t)(T.inst_off.size() - 1);
+    st->forest_level = T.forest_level;
     return KIFMM_OK;
 }
 

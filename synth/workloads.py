@@ -11,6 +11,11 @@ Sizes follow the configurations the library is benchmarked and tested on:
 * ``polar_64``        64 spheres, radii U[0.5,1.5], centres in a 20^3 box with a
                       0.05 surface gap, f=23 (10,580 triangles each, 677,120
                       unknowns), contrast eps_in/eps_out U[2,20], E0 = z-hat.
+* ``batch_256``       256 independent instances of 1-64 spheres (radii U[0.5,1.5],
+                      packed at the density of polar_64), each of a total size
+                      log-uniform in 1k-200k triangles (about 10M in all),
+                      single-layer densities U[-1,1]; one forest.
+* ``batch_32``        the same recipe with 32 instances of 1k-50k (a quick case).
 """
 from __future__ import annotations
 
@@ -52,12 +57,47 @@ def _polar_64():
                 contrast=contrast, eps_out=1.0, e0=(0.0, 0.0, 1.0))
 
 
+def batch_instances(n_inst: int, lo: int, hi: int, seed: int):
+    """Meshes of ``n_inst`` sphere packs: sizes log-uniform in [lo, hi] triangles, 1-64
+    spheres each (f chosen so 20 f^2 per sphere meets the size), centres packed in a
+    box scaled to keep the sphere density of a 64-sphere 20^3 pack."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_inst))
+    nsph = rng.integers(1, 65, size=n_inst)
+    meshes = []
+    for i in range(n_inst):
+        f = max(1, int(round(np.sqrt(sizes[i] / (20.0 * nsph[i])))))
+        box = max(4.0, 20.0 * (nsph[i] / 64.0) ** (1.0 / 3.0))
+        c, r = sphere_pack(int(nsph[i]), 0.5, 1.5, box, 0.05, seed=seed + 1 + i)
+        meshes.append(pack_mesh(c, r, f))
+    return meshes
+
+
+def _batch(n_inst: int, lo: int, hi: int, seed: int):
+    ms = batch_instances(n_inst, lo, hi, seed)
+    off = np.concatenate([[0], np.cumsum([m.n for m in ms])]).astype(np.int64)
+    m = Mesh(np.concatenate([x.tri for x in ms]), np.concatenate([x.sph for x in ms]),
+             np.concatenate([x.body + 64 * i for i, x in enumerate(ms)]).astype(np.int32))
+    return dict(mesh=m, kernel="sl", p=8, max_leaf=64, instances=off,
+                density=uniform_density(m.n, seed + 999))
+
+
+def _batch_256():
+    return _batch(256, 1000, 200000, 4000)
+
+
+def _batch_32():
+    return _batch(32, 1000, 50000, 4100)
+
+
 WORKLOADS = {
     "sl_sphere_20k": _sl_sphere_20k,
     "demag_cube_1m": _demag_cube_1m,
     "demag_cube_270k": _demag_cube_270k,
     "demag_sphere_1m": _demag_sphere_1m,
     "polar_64": _polar_64,
+    "batch_256": _batch_256,
+    "batch_32": _batch_32,
 }
 
 
@@ -65,4 +105,4 @@ def workload(name: str) -> dict:
     return WORKLOADS[name]()
 
 
-__all__ = ["Mesh", "WORKLOADS", "workload", "uniform_density"]
+__all__ = ["Mesh", "WORKLOADS", "workload", "uniform_density", "batch_instances"]

@@ -53,3 +53,20 @@ def test_null_arguments_rejected_without_a_gpu(lib):
     assert lib.kifmm_fmm_matvec(None, None, None, None) == -1
     lib.kifmm_tree_destroy.argtypes = [ctypes.c_void_p]
     assert lib.kifmm_tree_destroy(None) == 0
+
+
+def test_forest_arguments_rejected_without_a_gpu(lib):
+    """kifmm_forest_build checks sizes and offsets on the host before any CUDA call."""
+    import numpy as np
+    out = ctypes.c_void_p()
+    f = lib.kifmm_forest_build
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    fake = ctypes.c_void_p(0x1000)             # never dereferenced: the checks fail first
+    for off, n in (([1, 10], 10), ([0, 5, 5, 10], 10), ([0, 4, 9], 10), ([0, 10], 11)):
+        a = np.asarray(off, dtype=np.int64)
+        assert f(fake, n, a.ctypes.data, len(off) - 1, 16, None, ctypes.byref(out)) == -1
+        assert not out.value
+    a = np.zeros(2, dtype=np.int64)
+    assert f(fake, 10, a.ctypes.data, 0, 16, None, ctypes.byref(out)) == -1        # no instances
+    assert f(None, 10, a.ctypes.data, 1, 16, None, ctypes.byref(out)) == -1        # NULL points
