@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <type_traits>
 
 #include "common.cuh"
 #include "operators.cuh"
@@ -323,7 +324,160 @@ __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ of
     }
 }
 
+// FP32 near field, one warp per target leaf.  Lanes form 4 source groups of 8: lane
+// (g, r) holds targets t0 + 8 i + r (i < T) of the current pass of at most 64 targets and
+// takes sources j = g, g + 4, ... of every 32 staged by the warp; the four partial sums
+// of a target meet by shuffles at the end.  Staged sources are float4 (position relative
+// to the leaf centre and q -- or q n_j for the double layer, spread over two float4), so
+// one shared-memory broadcast load feeds T pair evaluations.  Source positions come as
+// FP32 hi/lo pairs (split once per plan) and the offset from the leaf centre is formed
+// from them in FP32, to within 2 ulp of that offset, with no FP64 arithmetic per pair or
+// per staged source.
+constexpr int kP2PWarps = 8;
+
+template <int KIND, int T>
+__device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const int* __restrict__ idx,
+                                         const int64_t* __restrict__ rng, double cx, double cy, double cz,
+                                         const float* __restrict__ sxf, int64_t ns,
+                                         const double* __restrict__ txyz, int64_t nt,
+                                         const float* __restrict__ qs, const float* __restrict__ tnrm,
+                                         const float* __restrict__ res, const int64_t* __restrict__ tperm,
+                                         double* __restrict__ out, int64_t t0, int64_t te, float4* st) {
+    const int g = lane >> 3, r = lane & 7;
+    float tx[T], ty[T], tz[T], acc[T], nx[T], ny[T], nz[T];
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        int64_t t = t0 + 8 * i + r;
+        t = t < te ? t : t0;                      // padding slots evaluate a real target, unused
+        tx[i] = (float)(txyz[t] - cx);
+        ty[i] = (float)(txyz[nt + t] - cy);
+        tz[i] = (float)(txyz[2 * nt + t] - cz);
+        if (KIND == 2) {
+            nx[i] = tnrm[t];
+            ny[i] = tnrm[nt + t];
+            nz[i] = tnrm[2 * nt + t];
+        }
+        acc[i] = 0.f;
+    }
+    // the leaf centre as FP32 hi + lo; a source's offset from it is (yh - ch) + (yl - cl)
+    const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
+    const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
+    const float d2 = (float)(kDelta * kDelta);
+    // chunks of 32 sources over the leaf's source boxes, the next one prefetched into
+    // registers while the current one is evaluated
+    int e = e0;
+    int64_t j0 = 0, se = 0;
+    if (e < e1) {
+        const int a = idx[e];
+        j0 = rng[4 * a];
+        se = rng[4 * a + 1];
+    }
+    float ph[3], pl[3], pq[3];
+    auto fetch = [&](int64_t jb, int64_t je) {
+        const int64_t j = jb + lane;
+        if (j < je) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                ph[d] = sxf[d * ns + j];
+                pl[d] = sxf[(3 + d) * ns + j];
+            }
+            pq[0] = qs[j];
+            if (KIND == 1) {
+                pq[1] = qs[ns + j];
+                pq[2] = qs[2 * ns + j];
+            }
+        }
+    };
+    while (e < e1) {
+        fetch(j0, se);
+        const int64_t j = j0 + lane;
+        if (j < se) {
+            st[lane] = make_float4((ph[0] - chx) + (pl[0] - clx), (ph[1] - chy) + (pl[1] - cly),
+                                   (ph[2] - chz) + (pl[2] - clz), pq[0]);
+            if (KIND == 1) st[32 + lane] = make_float4(pq[1], pq[2], 0.f, 0.f);
+        }
+        const int cnt = (int)(se - j0 < 32 ? se - j0 : 32);
+        // advance to the next chunk and prefetch it
+        j0 += 32;
+        while (j0 >= se && ++e < e1) {
+            const int a = idx[e];
+            j0 = rng[4 * a];
+            se = rng[4 * a + 1];
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int jj = g; jj < cnt; jj += 4) {
+            const float4 sp = st[jj];
+            float4 sd = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (KIND == 1) sd = st[32 + jj];
+#pragma unroll
+            for (int i = 0; i < T; ++i) {
+                const float dx = tx[i] - sp.x, dy = ty[i] - sp.y, dz = tz[i] - sp.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float inv = rsqrtf(r2);
+                float v;
+                if (KIND == 0) v = sp.w * inv;
+                else if (KIND == 1) v = (sp.w * dx + sd.x * dy + sd.y * dz) * (inv * inv * inv);
+                else v = sp.w * (nx[i] * dx + ny[i] * dy + nz[i] * dz) * (inv * inv * inv);
+                acc[i] += (r2 >= d2) ? v : 0.f;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        float v = acc[i];
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        const int64_t t = t0 + 8 * i + r;
+        if (g == 0 && t < te) out[tperm[t]] = (double)(v + res[t]);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(32 * kP2PWarps)
+k_p2p_warp(const int* __restrict__ leaves, int nleaves, const int* __restrict__ off, const int* __restrict__ idx,
+           const int64_t* __restrict__ rng, const double* __restrict__ ctr, const float* __restrict__ sxf,
+           int64_t ns, const double* __restrict__ txyz, int64_t nt, const float* __restrict__ qs,
+           const float* __restrict__ tnrm, const float* __restrict__ res, const int64_t* __restrict__ tperm,
+           double* __restrict__ out) {
+    __shared__ float4 stage[kP2PWarps][KIND == 1 ? 64 : 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li = blockIdx.x * kP2PWarps + warp;
+    if (li >= nleaves) return;                    // whole warp; no block-wide barrier below
+    const int b = leaves[li];
+    const double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
+    const int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
+    const int e0 = off[li], e1 = off[li + 1];
+    float4* st = stage[warp];
+    for (int64_t t0 = tb; t0 < te; t0 += 64) {
+        const int n = (int)(te - t0 < 64 ? te - t0 : 64);
+        const int64_t tend = t0 + n;
+        switch ((n + 7) >> 3) {
+#define KF_PASS(TT)                                                                                  \
+    case TT:                                                                                         \
+        p2p_pass<KIND, TT>(lane, e0, e1, idx, rng, cx, cy, cz, sxf, ns, txyz, nt, qs, tnrm, res, tperm, \
+                           out, t0, tend, st);                                                       \
+        break;
+            KF_PASS(1) KF_PASS(2) KF_PASS(3) KF_PASS(4) KF_PASS(5) KF_PASS(6) KF_PASS(7) KF_PASS(8)
+#undef KF_PASS
+        }
+    }
+}
+
 // ---------------------------------------------------------------- set-up kernels
+// x = hi + lo with hi = fl32(x), lo = fl32(x - hi): 6 x n SoA (hi x|y|z, lo x|y|z).
+__global__ void k_split_xyz(const double* __restrict__ xyz, int64_t n, float* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int d = 0; d < 3; ++d) {
+        const double v = xyz[d * n + i];
+        const float h = (float)v;
+        out[d * n + i] = h;
+        out[(3 + d) * n + i] = (float)(v - (double)h);
+    }
+}
+
 __global__ void k_gather_nrm(const double* __restrict__ nrm, const int64_t* __restrict__ perm, int64_t n,
                              double* __restrict__ outd, float* __restrict__ outf) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -557,6 +711,9 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_TRY(P.bexp.alloc(T.nbox));
         KF_TRY(P.vin_h.alloc((size_t)T.nbox * P.Qp));
         KF_TRY(P.vin_l.alloc((size_t)T.nbox * P.Qp));
+        KF_TRY(P.sxf.alloc(6 * (size_t)T.ns));
+        k_split_xyz<<<div_up(T.ns, 256), 256, 0, s>>>(T.sxyz.p, T.ns, P.sxf.p);
+        KF_CHECK_LAUNCH();
     }
 
     // work lists (host bookkeeping over the tree's lists)
@@ -812,10 +969,28 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     }
     KF_TRY(mark(7));
     if (P.n_tleaf) {
-        int threads = std::min(256, std::max(32, (P.max_trg_leaf + 31) / 32 * 32));
-        size_t smem = 6 * threads * sizeof(Real);
         const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
         const int64_t* tperm = T.same ? T.sperm.p : T.tperm.p;
+        // FP32 with leaves of up to 64 targets: a warp per leaf; larger leaves (and FP64):
+        // a block per leaf, whose staged sources serve all of the leaf's targets at once
+        bool done = false;
+        if constexpr (std::is_same<Real, float>::value) {
+          if (P.max_trg_leaf <= 64) {
+            const unsigned grid = (unsigned)((P.n_tleaf + kP2PWarps - 1) / kP2PWarps);
+#define KF_P2PW(KIND)                                                                                     \
+    k_p2p_warp<KIND><<<grid, 32 * kP2PWarps, 0, s>>>(P.tleaf.p, P.n_tleaf, P.p2p_off.p, P.p2p_idx.p, T.rng.p, \
+                                                      T.ctr.p, P.sxf.p, T.ns, txyz, T.nt,                   \
+                                                      B.q, B.tnrm, B.res, tperm, out)
+            if (P.kernel == KIFMM_KERNEL_SL) KF_P2PW(0);
+            else if (P.kernel == KIFMM_KERNEL_DL) KF_P2PW(1);
+            else KF_P2PW(2);
+#undef KF_P2PW
+            done = true;
+          }
+        }
+        if (!done) {
+        int threads = std::min(256, std::max(32, (P.max_trg_leaf + 31) / 32 * 32));
+        size_t smem = 6 * threads * sizeof(Real);
 #define KF_P2P(KIND)                                                                                     \
     k_p2p<Real, KIND><<<P.n_tleaf, threads, smem, s>>>(P.tleaf.p, P.p2p_off.p, P.p2p_idx.p, T.rng.p,     \
                                                         T.ctr.p, T.sxyz.p, T.ns, txyz, T.nt, B.q, B.tnrm, \
@@ -824,6 +999,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         else if (P.kernel == KIFMM_KERNEL_DL) KF_P2P(1);
         else KF_P2P(2);
 #undef KF_P2P
+        }
         KF_CHECK_LAUNCH();
         ++launches;
     }

@@ -48,6 +48,7 @@ struct Plan {
     DBuf<float> surf_f;
 
     DBuf<double> snrm, tnrm_d;      // sorted normals (DL: sources; ADL: targets)
+    DBuf<float> sxf;                // mixed: sorted source coordinates as FP32 hi/lo pairs, 6 x ns SoA
     DBuf<float> tnrm_f;
 
     // work lists

@@ -143,3 +143,18 @@ def test_graph_matvec_matches_direct_launches():
     torch.cuda.synchronize()
     assert rel(out2, out) < 1e-6
     plan.check()
+
+
+def test_autotune_picks_an_order_that_meets_the_target():
+    """The autotuner's order, chosen without the oracle, meets its target against it."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    from paper_1605_01715_gb300.autotune import autotune
+    off, (xyz, w, nrm), sig, refs = forest_case()
+    q = torch.from_numpy(sig).to(DEV) * w
+    r = autotune(xyz, q, "sl", off, target=1e-6, leaf_sizes=(16, 32), stride=1, reps=2)
+    assert r["p"] in (4, 6, 8, 10) and r["max_leaf"] in (16, 32)
+    assert r["est_err"] <= 0.7e-6 and set(r["times_ms"]) == {16, 32}
+    tree = Tree(xyz, max_leaf=r["max_leaf"], instances=off)
+    out = Plan(tree, kernel="sl", p=r["p"], precision="mixed").matvec(q).cpu().numpy()
+    ref = refs["sl"]
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-6
