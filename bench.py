@@ -329,6 +329,56 @@ def run_kifmm(args):
     return 0
 
 
+def run_serve(args):
+    """Serving stream (Poisson arrivals, mixed polarization solves and demag
+    evaluations, 2k-500k unknowns): p50/p99 latency and throughput of the
+    continuous-batching server at each arrival rate, against serial FP64 solves of
+    the same requests.  One JSON line; value = throughput at the highest rate."""
+    import torch
+
+    from paper_1605_01715_gb300.serve import Request, Server, percentiles, serial_baseline
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    sweep = []
+    n_req = args.serve_requests
+    with ClockSampler(0) as clk:
+        for k, rate in enumerate(rates):
+            reqs = [Request(rid=i, **d) for i, d in enumerate(synth.serve_requests(n_req, rate, 5000 + k))]
+            server = Server(mem_budget=args.serve_mem_gb * (1 << 30), p=args.serve_p, precision=args.precision)
+            recs, tot = server.run(reqs)
+            lat = [r["latency"] for r in recs]
+            p50, p99 = percentiles(lat)
+            polar = [r for r in recs if r["kind"] == "polar"]
+            unknowns = sum(r["n"] for r in recs)
+            sweep.append({"rate_req_s": rate, "requests": len(recs), "p50_ms": p50 * 1e3, "p99_ms": p99 * 1e3,
+                          "throughput_req_s": len(recs) / tot["makespan_s"],
+                          "unknowns_per_s": unknowns / tot["makespan_s"], "makespan_s": tot["makespan_s"],
+                          "peak_live": tot["peak_live"], "rounds": tot["rounds"],
+                          "polar_max_true_rel_residual": max((r["rel_res"] for r in polar), default=None),
+                          "polar_failed": sum(1 for r in polar if r["status"] != 0)})
+            print("serve rate %g: p50 %.1f ms p99 %.1f ms, %.1f req/s" % (rate, p50 * 1e3, p99 * 1e3,
+                                                                    sweep[-1]["throughput_req_s"]),
+                  file=sys.stderr, flush=True)
+    base_reqs = [Request(rid=i, **d) for i, d in enumerate(synth.serve_requests(args.serve_serial, 1.0, 5999))]
+    st = serial_baseline(base_reqs, p=args.serve_p, precision="fp64")
+    serial = {"requests": len(st), "precision": "fp64", "mean_service_ms": float(np.mean(st)) * 1e3,
+              "throughput_req_s": len(st) / float(np.sum(st)),
+              "unknowns_per_s": sum(r.n for r in base_reqs) / float(np.sum(st))}
+    top = sweep[-1]
+    line = {"metric": "serving throughput (solve requests/s) with p50/p99 latency", "value": top["throughput_req_s"],
+            "unit": "requests/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
+            "ms_per_step": 1e3 / max(top["throughput_req_s"], 1e-9), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "serve_stream", "sizes": "log-uniform 2k-500k", "p": args.serve_p,
+                       "precision": args.precision, "mem_budget_gb": args.serve_mem_gb,
+                       "kinds": "half polarization GMRES(50) tol 1e-6, half demag phi2"},
+            "serve": sweep, "serial_fp64": serial, "clocks": clk.summary(),
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def solve_latency(args, device):
     """p50/p99 wall time of full GMRES polarization solves (64-sphere pack, mixed matvec,
     FP64 Krylov) with the plan, tree and Krylov basis resident between solves."""
@@ -450,12 +500,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batch workloads: take p / leaf from the workload")
     ap.add_argument("--graph", action="store_true", help="time captured-graph matvecs (always for batches)")
+    ap.add_argument("--serve", action="store_true", help="serving-stream sweep instead of the matvec bench")
+    ap.add_argument("--serve-rates", default="10,100,1000")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-serial", type=int, default=8)
+    ap.add_argument("--serve-p", type=int, default=10)
+    ap.add_argument("--serve-mem-gb", type=float, default=96.0)
     ap.add_argument("--solves", type=int, default=5, help="timed polarization solves (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_kifmm(args)
 
 

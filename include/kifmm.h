@@ -55,6 +55,7 @@ extern "C" {
 
 typedef struct kifmm_tree_s* kifmm_tree;
 typedef struct kifmm_plan_s* kifmm_plan;
+typedef struct kifmm_solver_s* kifmm_solver;
 
 /* Last error message of the calling thread ("" if none).  Owned by the library. */
 const char* kifmm_last_error(void);
@@ -253,6 +254,34 @@ int kifmm_bie_solve(kifmm_plan plan, const double* area, const double* eps_in, d
                     const double* curv, const double* b, double* x,
                     double tol, int restart, int max_iter,
                     int* iters, double* rel_res, void* stream);
+
+/*
+ * The same GMRES as kifmm_bie_solve, advanced one step at a time so that several
+ * solves can share the GPU (no counterpart in the paper, which solves one system at a
+ * time).  A step is one of: the norm of b, a restart (one matvec), one Arnoldi
+ * iteration (one matvec and two Gram-Schmidt passes), the final true residual (one
+ * matvec).
+ *   kifmm_solver_create: arguments as kifmm_bie_solve; area, eps_in, curv, b and x
+ *     must stay allocated until the solver is destroyed (x is updated in place).  The
+ *     solver owns its Krylov basis ((restart+1) n FP64), so several solvers may share
+ *     one plan -- but their steps must then not overlap on the GPU (the plan's
+ *     matvec buffers are shared): launch and finish them one after the other.
+ *   kifmm_solver_launch: enqueue the next step's device work on `stream`; returns
+ *     without waiting.
+ *   kifmm_solver_finish: wait for that work and advance on the host.  *done = 1 once
+ *     the solve has ended; *iters = Arnoldi iterations so far; *rel_res = the GMRES
+ *     residual estimate, or after the end the true relative residual.  Returns the
+ *     solve's status once it has ended (OK, NOT_CONVERGED, BREAKDOWN), else OK.
+ * Launch and finish alternate; solvers on different plans and streams may each be
+ * launched before any is finished, which overlaps their device work.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int kifmm_solver_create(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
+                        const double* curv, const double* b, double* x, double tol, int restart,
+                        int max_iter, kifmm_solver* out);
+int kifmm_solver_launch(kifmm_solver solver, void* stream);
+int kifmm_solver_finish(kifmm_solver solver, int* done, int* iters, double* rel_res);
+int kifmm_solver_destroy(kifmm_solver solver);
 
 /*
  * The polarization operator itself, y = A x (same definition as kifmm_bie_solve).

@@ -9,6 +9,7 @@ from .capi import (  # noqa: F401
     PRECISIONS,
     KifmmError,
     Plan,
+    Solver,
     Tree,
     exported_symbols,
     kifmm_polarization_rhs,

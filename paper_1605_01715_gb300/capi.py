@@ -84,6 +84,12 @@ _SIGS = {
     "kifmm_plan_check": ([_P], ctypes.c_int),
     "kifmm_plan_destroy": ([_P], ctypes.c_int),
     "kifmm_polarization_rhs": ([_P, _P, ctypes.c_double, _P, _I64, _P, _P], ctypes.c_int),
+    "kifmm_solver_create": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_double, ctypes.c_int,
+                             ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+    "kifmm_solver_launch": ([_P, _P], ctypes.c_int),
+    "kifmm_solver_finish": ([_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "kifmm_solver_destroy": ([_P], ctypes.c_int),
     "kifmm_bie_solve": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_double, ctypes.c_int,
                          ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "kifmm_bie_apply": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, _P], ctypes.c_int),
@@ -325,3 +331,46 @@ def kifmm_polarization_rhs(nrm, eps_in, eps_out, e0, out=None, stream=None):
     _check(lib().kifmm_polarization_rhs(_dev(nrm, 3 * n, "nrm"), _dev(eps_in, n, "eps_in"), float(eps_out), e, n,
                                         _dev(out, n, "b"), _stream(stream)))
     return out
+
+
+class Solver:
+    """A resumable polarization GMRES solve (kifmm_solver_*): ``launch`` enqueues the
+    next step on a stream, ``finish`` waits for it and advances.  The tensors passed in
+    are kept alive by the object; ``x`` is updated in place."""
+
+    def __init__(self, plan, area, eps_in, eps_out, curv, b, x=None, tol=1e-6, restart=50, max_iter=1000):
+        n = plan.n_trg
+        if x is None:
+            x = torch.zeros(n, dtype=torch.float64, device=b.device)
+        self._keep = (plan, area, eps_in, curv, b, x)
+        self.x = x
+        h = ctypes.c_void_p()
+        _check(lib().kifmm_solver_create(plan.handle, _dev(area, n, "area"), _dev(eps_in, n, "eps_in"),
+                                         float(eps_out), _dev(curv, n, "curv"), _dev(b, n, "b"),
+                                         _dev(x, n, "x"), float(tol), int(restart), int(max_iter),
+                                         ctypes.byref(h)))
+        self.handle = h
+        self._lib = lib()
+        self.done, self.iters, self.rel_res, self.status = False, 0, float("inf"), 0
+
+    def launch(self, stream=None):
+        _check(lib().kifmm_solver_launch(self.handle, _stream(stream)))
+
+    def finish(self):
+        d, it, rr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+        rc = lib().kifmm_solver_finish(self.handle, ctypes.byref(d), ctypes.byref(it), ctypes.byref(rr))
+        if rc not in (0, -4, -6):                  # OK, NOT_CONVERGED, BREAKDOWN end a solve
+            _check(rc)
+        self.done, self.iters, self.rel_res, self.status = bool(d.value), it.value, rr.value, rc
+        return self.done
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.kifmm_solver_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -14,6 +14,7 @@
 // Hessenberg least-squares problem runs on the host.
 #include <cmath>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -256,149 +257,304 @@ extern "C" int kifmm_demag_phi2_noalloc(kifmm_plan plan, const double* phi1, con
     return KIFMM_OK;
 }
 
-extern "C" int kifmm_bie_solve(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
-                               const double* curv, const double* b, double* x, double tol, int restart,
-                               int max_iter, int* iters, double* rel_res, void* stream) {
-    clear_error();
+// ---------------------------------------------------------------- resumable GMRES
+// Restarted GMRES(m) as a state machine, so several solves can advance in lockstep:
+// launch() enqueues the device work of the next step on a stream without waiting;
+// finish() waits for it, runs the host part (Givens rotations, convergence, restart)
+// and picks the next step.  Steps: the norm of b; a restart (r = b - A x, beta); one
+// Arnoldi step (A v_k, CGS2, ||w||); the final true residual.  Device work that needs a
+// host result (v_0 = r / beta, v_{k+1} = w / h_{k+1,k}, x += V y) is carried into the
+// next launch.
+namespace kifmm {
+
+struct Solver {
+    Plan& P;
+    const double *area, *eps_in, *curv, *b;
+    double* x;
+    double eps_out, tol;
+    int m, max_iter;
+    int64_t n;
+    // device: Krylov basis (m+1) x n, w, r, the area-weighted operand, dot partials, h
+    double *V = nullptr, *w = nullptr, *r = nullptr, *q = nullptr;
+    DBuf<double> own_V, own_w, own_r, own_q;
+    Gmres g;
+    double* hpin = nullptr;                 // pinned host copies: ha (m+2), hb (m+2), scalar
+    enum Step { kNormB, kRestart, kArnoldi, kFinal, kDone } step = kNormB;
+    // pending device work for the next launch
+    double scale_v0 = 0, scale_next = 0;
+    int pend_x = 0;                         // x += V[0..pend_x) y
+    bool zero_x = false;
+    // host state
+    std::vector<double> H, cs, sn, gv, y;
+    double bnorm = 0, rel = INFINITY, true_rel = 0;
+    int it = 0, k = 0;
+    int status = KIFMM_OK;                  // final status once step == kDone
+    cudaStream_t last = nullptr;
+
+    Solver(Plan& P_, const double* area_, const double* eps_in_, const double* curv_, double eps_out_,
+           const double* b_, double* x_, double tol_, int m_, int max_iter_)
+        : P(P_), area(area_), eps_in(eps_in_), curv(curv_), b(b_), x(x_), eps_out(eps_out_), tol(tol_),
+          m(m_), max_iter(max_iter_), n(P_.tree->t.nt), g{P_, area_, eps_in_, curv_, eps_out_, P_.tree->t.nt,
+                                                            nullptr, nullptr, {}, {}} {}
+    ~Solver() {
+        if (hpin) cudaFreeHost(hpin);
+    }
+
+    // own = false: use the plan's resident scratch (one solve at a time on that plan)
+    int init(bool own) {
+        if (own) {
+            KF_TRY(own_V.alloc((size_t)(m + 1) * n));
+            KF_TRY(own_w.alloc(n));
+            KF_TRY(own_r.alloc(n));
+            KF_TRY(own_q.alloc(n));
+            V = own_V.p, w = own_w.p, r = own_r.p, q = own_q.p;
+        } else {
+            BieScratch& S = P.bie;
+            KF_TRY(ensure(S.q, n));
+            KF_TRY(ensure(S.krylov, (size_t)(m + 1) * n));
+            KF_TRY(ensure(S.w, n));
+            KF_TRY(ensure(S.r, n));
+            V = S.krylov.p, w = S.w.p, r = S.r.p, q = S.q.p;
+        }
+        g.qbuf = q;
+        KF_TRY(g.partial.alloc((size_t)kDotBlocks * (m + 1)));
+        KF_TRY(g.hdev.alloc(3 * (size_t)(m + 2)));
+        KF_CHECK_CUDA(cudaMallocHost(&hpin, (2 * (size_t)(m + 2) + 1) * sizeof(double)));
+        H.assign((size_t)(m + 1) * m, 0.0);
+        cs.assign(m, 0.0);
+        sn.assign(m, 0.0);
+        gv.assign(m + 1, 0.0);
+        y.assign(m, 0.0);
+        return KIFMM_OK;
+    }
+
+    double* hA() { return g.hdev.p; }
+    double* hB() { return g.hdev.p + (m + 2); }
+    double* hy() { return g.hdev.p + 2 * (m + 2); }
+
+    int flush_pending(cudaStream_t s) {
+        if (zero_x) {
+            KF_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+            zero_x = false;
+        }
+        if (pend_x > 0) {
+            // y was written to the pinned buffer by finish(); copy and update x
+            KF_CHECK_CUDA(cudaMemcpyAsync(hy(), hpin, pend_x * sizeof(double), cudaMemcpyHostToDevice, s));
+            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, pend_x, hy(), 1.0, n, x);
+            KF_CHECK_LAUNCH();
+            pend_x = 0;
+        }
+        if (scale_v0 != 0) {
+            k_axpby<<<div_up(n, 256), 256, 0, s>>>(scale_v0, V, 0.0, V, n, V);
+            KF_CHECK_LAUNCH();
+            scale_v0 = 0;
+        }
+        if (scale_next != 0) {
+            k_axpby<<<div_up(n, 256), 256, 0, s>>>(scale_next, w, 0.0, w, n, V + (size_t)k * n);
+            KF_CHECK_LAUNCH();
+            scale_next = 0;
+        }
+        return KIFMM_OK;
+    }
+
+    int launch(cudaStream_t s) {
+        if (step == kDone) return KIFMM_OK;
+        g.s = s;
+        last = s;
+        KF_TRY(flush_pending(s));
+        if (step == kNormB) {
+            KF_TRY(g.dots(b, 0, 1, b, hA()));
+            KF_CHECK_CUDA(cudaMemcpyAsync(hpin, hA(), sizeof(double), cudaMemcpyDeviceToHost, s));
+        } else if (step == kRestart || step == kFinal) {
+            // r = b - A x (restart: into v_0)
+            KF_TRY(g.apply(x, r));
+            double* dst = step == kRestart ? V : r;
+            k_axpby<<<div_up(n, 256), 256, 0, s>>>(1.0, b, -1.0, r, n, dst);
+            KF_CHECK_LAUNCH();
+            KF_TRY(g.dots(dst, 0, 1, dst, hA()));
+            KF_CHECK_CUDA(cudaMemcpyAsync(hpin, hA(), sizeof(double), cudaMemcpyDeviceToHost, s));
+        } else {  // kArnoldi: w = A v_k, two Gram-Schmidt passes against v_0..v_k, ||w||^2
+            KF_TRY(g.apply(V + (size_t)k * n, w));
+            KF_TRY(g.dots(V, n, k + 1, w, hA()));
+            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, k + 1, hA(), -1.0, n, w);
+            KF_CHECK_LAUNCH();
+            KF_TRY(g.dots(V, n, k + 1, w, hB()));
+            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, k + 1, hB(), -1.0, n, w);
+            KF_CHECK_LAUNCH();
+            KF_TRY(g.dots(w, 0, 1, w, hB() + (m + 1)));
+            KF_CHECK_CUDA(cudaMemcpyAsync(hpin, hA(), (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            KF_CHECK_CUDA(cudaMemcpyAsync(hpin + (m + 2), hB(), (m + 2) * sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
+        }
+        return KIFMM_OK;
+    }
+
+    // End of a cycle: back substitution, then x += V y at the next launch.
+    void end_cycle(int kdone) {
+        for (int i = kdone - 1; i >= 0; --i) {
+            double acc = gv[i];
+            for (int j = i + 1; j < kdone; ++j) acc -= H[(size_t)i * m + j] * y[j];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        for (int i = 0; i < kdone; ++i) hpin[i] = y[i];   // read by the next launch's copy
+        pend_x = kdone;
+    }
+
+    int finish() {
+        if (step == kDone) return KIFMM_OK;
+        KF_CHECK_CUDA(cudaStreamSynchronize(last));
+        if (step == kNormB) {
+            bnorm = std::sqrt(hpin[0]);
+            if (!(bnorm > 0)) {
+                zero_x = true;
+                rel = true_rel = 0;
+                step = kFinal;              // x = 0; the final residual is then exactly 0
+                return KIFMM_OK;
+            }
+            step = kRestart;
+            return KIFMM_OK;
+        }
+        if (step == kFinal) {
+            true_rel = bnorm > 0 ? std::sqrt(hpin[0]) / bnorm : 0.0;
+            if (status == KIFMM_OK && !(rel <= tol)) {
+                set_error("GMRES did not converge in %d iterations (residual estimate %.3e)", it, rel);
+                status = KIFMM_ERR_NOT_CONVERGED;
+            }
+            step = kDone;
+            return KIFMM_OK;
+        }
+        if (step == kRestart) {
+            const double beta = std::sqrt(hpin[0]);
+            rel = beta / bnorm;
+            if (!std::isfinite(beta)) return breakdown();
+            if (rel <= tol || it >= max_iter) {
+                step = kFinal;
+                return KIFMM_OK;
+            }
+            scale_v0 = 1.0 / beta;
+            std::fill(gv.begin(), gv.end(), 0.0);
+            gv[0] = beta;
+            k = 0;
+            step = kArnoldi;
+            return KIFMM_OK;
+        }
+        // kArnoldi: column k of H, the previous rotations, a new rotation
+        const double* ha = hpin;
+        const double* hb = hpin + (m + 2);
+        for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = ha[i] + hb[i];
+        const double hk1 = std::sqrt(hb[m + 1]);
+        H[(size_t)(k + 1) * m + k] = hk1;
+        if (!std::isfinite(hk1)) return breakdown();
+        for (int i = 0; i < k; ++i) {
+            const double a0 = H[(size_t)i * m + k], a1 = H[(size_t)(i + 1) * m + k];
+            H[(size_t)i * m + k] = cs[i] * a0 + sn[i] * a1;
+            H[(size_t)(i + 1) * m + k] = -sn[i] * a0 + cs[i] * a1;
+        }
+        const double a0 = H[(size_t)k * m + k], a1 = H[(size_t)(k + 1) * m + k];
+        const double den = std::hypot(a0, a1);
+        if (!(den > 0)) return breakdown();
+        cs[k] = a0 / den;
+        sn[k] = a1 / den;
+        H[(size_t)k * m + k] = den;
+        H[(size_t)(k + 1) * m + k] = 0;
+        gv[k + 1] = -sn[k] * gv[k];
+        gv[k] = cs[k] * gv[k];
+        ++it;
+        rel = std::fabs(gv[k + 1]) / bnorm;
+        if (rel <= tol || hk1 == 0 || k + 1 == m || it >= max_iter) {
+            end_cycle(k + 1);
+            step = (rel <= tol || it >= max_iter) ? kFinal : kRestart;
+            return KIFMM_OK;
+        }
+        if (hk1 > 0) scale_next = 1.0 / hk1;   // v_{k+1} = w / h_{k+1,k}
+        ++k;
+        return KIFMM_OK;
+    }
+
+    int breakdown() {
+        set_error("GMRES breakdown after %d iterations", it);
+        status = KIFMM_ERR_BREAKDOWN;
+        step = kFinal;
+        return KIFMM_OK;
+    }
+};
+
+}  // namespace kifmm
+
+struct kifmm_solver_s {
+    kifmm::Solver S;
+    template <class... A>
+    explicit kifmm_solver_s(A&&... a) : S(std::forward<A>(a)...) {}
+};
+
+static int solver_args(kifmm_plan plan, const double* area, const double* eps_in, const double* curv,
+                       const double* b, double* x, double tol, int restart, int max_iter) {
     KF_TRY(check_plan_for(plan, KIFMM_KERNEL_ADL));
     KF_ARG(area && eps_in && curv && b && x, "NULL pointer");
     KF_ARG(tol > 0 && tol < 1, "tol must be in (0, 1)");
     KF_ARG(restart >= 1 && restart <= 500, "restart must be in [1, 500]");
     KF_ARG(max_iter >= 1, "max_iter must be >= 1");
-    cudaStream_t s = (cudaStream_t)stream;
-    Plan& P = plan->P;
-    const int64_t n = P.tree->t.nt;
-    const int m = restart;
-    BieScratch& S = scratch_of(plan);
-    KF_TRY(ensure(S.q, n));
-    KF_TRY(ensure(S.krylov, (size_t)(m + 1) * n));
-    KF_TRY(ensure(S.w, n));
-    KF_TRY(ensure(S.r, n));
-    Gmres g{P, area, eps_in, curv, eps_out, n, s, S.q.p};
-    KF_TRY(g.partial.alloc((size_t)kDotBlocks * (m + 1)));
-    KF_TRY(g.hdev.alloc(3 * (size_t)(m + 2)));
-    double* V = S.krylov.p;
-    double* w = S.w.p;
-    double* hA = g.hdev.p;
-    double* hB = g.hdev.p + (m + 2);
-    double* hy = g.hdev.p + 2 * (m + 2);
+    return KIFMM_OK;
+}
 
-    double bn2 = 0;
-    KF_TRY(g.dots(b, 0, 1, b, hA));
-    KF_CHECK_CUDA(cudaMemcpyAsync(&bn2, hA, sizeof(double), cudaMemcpyDeviceToHost, s));
-    KF_CHECK_CUDA(cudaStreamSynchronize(s));
-    double bnorm = std::sqrt(bn2);
-    if (iters) *iters = 0;
-    if (rel_res) *rel_res = 0;
-    if (!(bnorm > 0)) {
-        KF_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
-        KF_CHECK_CUDA(cudaStreamSynchronize(s));
-        return KIFMM_OK;
+extern "C" int kifmm_bie_solve(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
+                               const double* curv, const double* b, double* x, double tol, int restart,
+                               int max_iter, int* iters, double* rel_res, void* stream) {
+    clear_error();
+    KF_TRY(solver_args(plan, area, eps_in, curv, b, x, tol, restart, max_iter));
+    cudaStream_t s = (cudaStream_t)stream;
+    Solver S(plan->P, area, eps_in, curv, eps_out, b, x, tol, restart, max_iter);
+    KF_TRY(S.init(false));
+    while (S.step != Solver::kDone) {
+        KF_TRY(S.launch(s));
+        KF_TRY(S.finish());
     }
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m), ha(m + 2), hb(m + 2);
-    int it = 0;
-    double rel = INFINITY;
-    bool converged = false, breakdown = false;
-    while (it < max_iter && !converged) {
-        // r = b - A x
-        KF_TRY(g.apply(x, S.r.p));
-        k_axpby<<<div_up(n, 256), 256, 0, s>>>(1.0, b, -1.0, S.r.p, n, V);
-        KF_CHECK_LAUNCH();
-        KF_TRY(g.dots(V, 0, 1, V, hA));
-        double beta2;
-        KF_CHECK_CUDA(cudaMemcpyAsync(&beta2, hA, sizeof(double), cudaMemcpyDeviceToHost, s));
-        KF_CHECK_CUDA(cudaStreamSynchronize(s));
-        double beta = std::sqrt(beta2);
-        rel = beta / bnorm;
-        if (!std::isfinite(beta)) {
-            breakdown = true;
-            break;
-        }
-        if (rel <= tol) {
-            converged = true;
-            break;
-        }
-        k_axpby<<<div_up(n, 256), 256, 0, s>>>(1.0 / beta, V, 0.0, V, n, V);
-        KF_CHECK_LAUNCH();
-        std::fill(gv.begin(), gv.end(), 0.0);
-        gv[0] = beta;
-        int kdone = 0;
-        for (int k = 0; k < m && it < max_iter; ++k) {
-            KF_TRY(g.apply(V + (size_t)k * n, w));
-            KF_TRY(g.dots(V, n, k + 1, w, hA));
-            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, k + 1, hA, -1.0, n, w);
-            KF_CHECK_LAUNCH();
-            KF_TRY(g.dots(V, n, k + 1, w, hB));
-            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, k + 1, hB, -1.0, n, w);
-            KF_CHECK_LAUNCH();
-            KF_TRY(g.dots(w, 0, 1, w, hB + (m + 1)));
-            KF_CHECK_CUDA(cudaMemcpyAsync(ha.data(), hA, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            KF_CHECK_CUDA(cudaMemcpyAsync(hb.data(), hB, (m + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            KF_CHECK_CUDA(cudaStreamSynchronize(s));
-            for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = ha[i] + hb[i];
-            double hk1 = std::sqrt(hb[m + 1]);
-            H[(size_t)(k + 1) * m + k] = hk1;
-            if (!std::isfinite(hk1)) {
-                breakdown = true;
-                break;
-            }
-            if (hk1 > 0) {
-                k_axpby<<<div_up(n, 256), 256, 0, s>>>(1.0 / hk1, w, 0.0, w, n, V + (size_t)(k + 1) * n);
-                KF_CHECK_LAUNCH();
-            }
-            for (int i = 0; i < k; ++i) {
-                double a0 = H[(size_t)i * m + k], a1 = H[(size_t)(i + 1) * m + k];
-                H[(size_t)i * m + k] = cs[i] * a0 + sn[i] * a1;
-                H[(size_t)(i + 1) * m + k] = -sn[i] * a0 + cs[i] * a1;
-            }
-            double a0 = H[(size_t)k * m + k], a1 = H[(size_t)(k + 1) * m + k];
-            double den = std::hypot(a0, a1);
-            if (!(den > 0)) {
-                breakdown = true;
-                break;
-            }
-            cs[k] = a0 / den;
-            sn[k] = a1 / den;
-            H[(size_t)k * m + k] = den;
-            H[(size_t)(k + 1) * m + k] = 0;
-            gv[k + 1] = -sn[k] * gv[k];
-            gv[k] = cs[k] * gv[k];
-            ++it;
-            kdone = k + 1;
-            rel = std::fabs(gv[k + 1]) / bnorm;
-            if (rel <= tol || hk1 == 0) break;
-        }
-        if (kdone > 0) {
-            for (int i = kdone - 1; i >= 0; --i) {
-                double acc = gv[i];
-                for (int j = i + 1; j < kdone; ++j) acc -= H[(size_t)i * m + j] * y[j];
-                y[i] = acc / H[(size_t)i * m + i];
-            }
-            KF_CHECK_CUDA(cudaMemcpyAsync(hy, y.data(), kdone * sizeof(double), cudaMemcpyHostToDevice, s));
-            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, kdone, hy, 1.0, n, x);
-            KF_CHECK_LAUNCH();
-            KF_CHECK_CUDA(cudaStreamSynchronize(s));
-        }
-        if (breakdown) break;
-        if (rel <= tol) converged = true;
+    if (iters) *iters = S.it;
+    if (rel_res) *rel_res = S.true_rel;
+    return S.status;
+}
+
+extern "C" int kifmm_solver_create(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
+                                   const double* curv, const double* b, double* x, double tol, int restart,
+                                   int max_iter, kifmm_solver* out) {
+    clear_error();
+    KF_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    KF_TRY(solver_args(plan, area, eps_in, curv, b, x, tol, restart, max_iter));
+    kifmm_solver sv =
+        new (std::nothrow) kifmm_solver_s(plan->P, area, eps_in, curv, eps_out, b, x, tol, restart, max_iter);
+    if (!sv) {
+        set_error("host allocation failed");
+        return KIFMM_ERR_OOM;
     }
-    // true residual
-    KF_TRY(g.apply(x, S.r.p));
-    k_axpby<<<div_up(n, 256), 256, 0, s>>>(1.0, b, -1.0, S.r.p, n, S.r.p);
-    KF_CHECK_LAUNCH();
-    KF_TRY(g.dots(S.r.p, 0, 1, S.r.p, hA));
-    double rr;
-    KF_CHECK_CUDA(cudaMemcpyAsync(&rr, hA, sizeof(double), cudaMemcpyDeviceToHost, s));
-    KF_CHECK_CUDA(cudaStreamSynchronize(s));
-    if (iters) *iters = it;
-    if (rel_res) *rel_res = std::sqrt(rr) / bnorm;
-    if (breakdown) {
-        set_error("GMRES breakdown after %d iterations", it);
-        return KIFMM_ERR_BREAKDOWN;
+    int rc = sv->S.init(true);
+    if (rc != KIFMM_OK) {
+        delete sv;
+        return rc;
     }
-    if (!converged) {
-        set_error("GMRES did not converge in %d iterations (residual estimate %.3e)", it, rel);
-        return KIFMM_ERR_NOT_CONVERGED;
-    }
+    *out = sv;
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_solver_launch(kifmm_solver solver, void* stream) {
+    clear_error();
+    KF_ARG(solver != nullptr, "NULL solver");
+    return solver->S.launch((cudaStream_t)stream);
+}
+
+extern "C" int kifmm_solver_finish(kifmm_solver solver, int* done, int* iters, double* rel_res) {
+    clear_error();
+    KF_ARG(solver != nullptr, "NULL solver");
+    KF_TRY(solver->S.finish());
+    const Solver& S = solver->S;
+    if (done) *done = S.step == Solver::kDone;
+    if (iters) *iters = S.it;
+    if (rel_res) *rel_res = S.step == Solver::kDone ? S.true_rel : S.rel;
+    return S.step == Solver::kDone ? S.status : KIFMM_OK;
+}
+
+extern "C" int kifmm_solver_destroy(kifmm_solver solver) {
+    clear_error();
+    delete solver;
     return KIFMM_OK;
 }

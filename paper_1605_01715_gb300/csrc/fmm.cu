@@ -13,6 +13,8 @@
 // Near-singular pairs (|r_i - r_j| < 1e-5) contribute nothing (Sec. III.A.1).
 #include <algorithm>
 #include <cmath>
+#include <memory>
+#include <mutex>
 #include <numeric>
 #include <type_traits>
 
@@ -644,6 +646,67 @@ int build_d2t(Plan& P, const HostPinv& h, const std::vector<int>& tleaf_of, Real
     return KIFMM_OK;
 }
 
+// The translation tables for P's key from the process-wide cache, or built now.  Entries
+// are weak: tables live as long as some plan holds them.
+int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
+    static std::mutex mu;
+    static std::vector<std::weak_ptr<OpTables>> cache;
+    int dev = 0;
+    KF_CHECK_CUDA(cudaGetDevice(&dev));
+    const bool centered = P.kernel == KIFMM_KERNEL_ADL;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto it = cache.begin(); it != cache.end();) {
+        std::shared_ptr<OpTables> t = it->lock();
+        if (!t) {
+            it = cache.erase(it);
+            continue;
+        }
+        if (t->device == dev && t->p == P.p && t->cutoff == P.cutoff && t->fp64 == P.fp64 &&
+            t->centered == centered) {
+            P.ops = t;
+            return KIFMM_OK;
+        }
+        ++it;
+    }
+    auto t = std::make_shared<OpTables>();
+    t->device = dev;
+    t->p = P.p;
+    t->cutoff = P.cutoff;
+    t->fp64 = P.fp64;
+    t->centered = centered;
+    const size_t QQ = (size_t)P.Qp * P.Qp;
+    if (P.fp64) {
+        KF_TRY(t->m2m_d.alloc(8 * QQ));
+        KF_TRY(t->m2l_d.alloc(kNumOffsets * QQ));
+        KF_TRY(t->l2l_d.alloc(8 * QQ));
+        KF_CHECK_CUDA(cudaMemsetAsync(t->m2m_d.p, 0, t->m2m_d.bytes(), s));
+        KF_CHECK_CUDA(cudaMemsetAsync(t->m2l_d.p, 0, t->m2l_d.bytes(), s));
+        KF_CHECK_CUDA(cudaMemsetAsync(t->l2l_d.p, 0, t->l2l_d.bytes(), s));
+        KF_TRY(build_ops<double>(P, h, t->m2m_d.p, t->m2l_d.p, t->l2l_d.p, s));
+    } else {
+        DBuf<float> f32[3];
+        const int nops[3] = {8, kNumOffsets, 8};
+        for (int f = 0; f < 3; ++f) {
+            KF_TRY(f32[f].alloc(nops[f] * QQ));
+            KF_CHECK_CUDA(cudaMemsetAsync(f32[f].p, 0, f32[f].bytes(), s));
+        }
+        KF_TRY(build_ops<float>(P, h, f32[0].p, f32[1].p, f32[2].p, s));
+        // scaled FP16 hi/lo split of every table and the TMA maps the tensor-core GEMM
+        // reads; the FP32 builds are not kept
+        for (int f = 0; f < 3; ++f) {
+            KF_TRY(t->tab_h[f].alloc(f32[f].n));
+            KF_TRY(t->tab_l[f].alloc(f32[f].n));
+            KF_TRY(tc_split_table(f32[f].p, t->tab_h[f].p, t->tab_l[f].p, f32[f].n, &t->texp[f], s));
+            KF_TRY(tc_make_map(&t->tmaps[f][0], t->tab_h[f].p, nops[f], P.Qp));
+            KF_TRY(tc_make_map(&t->tmaps[f][1], t->tab_l[f].p, nops[f], P.Qp));
+        }
+    }
+    KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    P.ops = t;
+    cache.push_back(t);
+    return KIFMM_OK;
+}
+
 int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s) {
     Tree& T = P.tree->t;
     const HostPinv& h = host_pinv(P.p, P.cutoff);
@@ -654,7 +717,6 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     P.tile_cap = P.fp64 ? kPairTile : tc_tile_pairs(P.Qp);
     KF_TRY(P.err.alloc(1));
     KF_CHECK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), s));
-    const size_t QQ = (size_t)P.Qp * P.Qp;
 
     // sorted normals
     if (P.kernel == KIFMM_KERNEL_DL) {
@@ -678,36 +740,9 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_TRY(P.surf_f.upload(sf, s));
     }
 
-    // operators
-    if (P.fp64) {
-        KF_TRY(P.m2m_d.alloc(8 * QQ));
-        KF_TRY(P.m2l_d.alloc(kNumOffsets * QQ));
-        KF_TRY(P.l2l_d.alloc(8 * QQ));
-        KF_CHECK_CUDA(cudaMemsetAsync(P.m2m_d.p, 0, P.m2m_d.bytes(), s));
-        KF_CHECK_CUDA(cudaMemsetAsync(P.m2l_d.p, 0, P.m2l_d.bytes(), s));
-        KF_CHECK_CUDA(cudaMemsetAsync(P.l2l_d.p, 0, P.l2l_d.bytes(), s));
-        KF_TRY(build_ops<double>(P, h, P.m2m_d.p, P.m2l_d.p, P.l2l_d.p, s));
-    } else {
-        KF_TRY(P.m2m_f.alloc(8 * QQ));
-        KF_TRY(P.m2l_f.alloc(kNumOffsets * QQ));
-        KF_TRY(P.l2l_f.alloc(8 * QQ));
-        KF_CHECK_CUDA(cudaMemsetAsync(P.m2m_f.p, 0, P.m2m_f.bytes(), s));
-        KF_CHECK_CUDA(cudaMemsetAsync(P.m2l_f.p, 0, P.m2l_f.bytes(), s));
-        KF_CHECK_CUDA(cudaMemsetAsync(P.l2l_f.p, 0, P.l2l_f.bytes(), s));
-        KF_TRY(build_ops<float>(P, h, P.m2m_f.p, P.m2l_f.p, P.l2l_f.p, s));
-        // scaled FP16 hi/lo split of every table and the TMA maps the tensor-core GEMM
-        // reads; the FP32 builds are not needed afterwards
-        DBuf<float>* f32[3] = {&P.m2m_f, &P.m2l_f, &P.l2l_f};
-        const int nops[3] = {8, kNumOffsets, 8};
-        for (int f = 0; f < 3; ++f) {
-            KF_TRY(P.tab_h[f].alloc(f32[f]->n));
-            KF_TRY(P.tab_l[f].alloc(f32[f]->n));
-            KF_TRY(tc_split_table(f32[f]->p, P.tab_h[f].p, P.tab_l[f].p, f32[f]->n, &P.texp[f], s));
-            KF_TRY(tc_make_map(&P.tmaps[f][0], P.tab_h[f].p, nops[f], P.Qp));
-            KF_TRY(tc_make_map(&P.tmaps[f][1], P.tab_l[f].p, nops[f], P.Qp));
-        }
-        KF_CHECK_CUDA(cudaStreamSynchronize(s));
-        for (int f = 0; f < 3; ++f) f32[f]->release();
+    // operators: shared tables of this key, built once
+    KF_TRY(get_tables(P, h, s));
+    if (!P.fp64) {
         KF_TRY(P.bexp.alloc(T.nbox));
         KF_TRY(P.vin_h.alloc((size_t)T.nbox * P.Qp));
         KF_TRY(P.vin_l.alloc((size_t)T.nbox * P.Qp));
@@ -832,12 +867,10 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     KF_CHECK_CUDA(cudaStreamSynchronize(s));
 
     P.device_bytes = 0;
-    for (size_t b : {P.m2m_d.bytes(), P.m2l_d.bytes(), P.l2l_d.bytes(), P.d2t_d.bytes(), P.m2m_f.bytes(),
-                     P.m2l_f.bytes(), P.l2l_f.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
+    for (size_t b : {(size_t)P.ops->bytes(), P.d2t_d.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
                      P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
-                     P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(), P.tab_h[0].bytes(),
-                     P.tab_h[1].bytes(), P.tab_h[2].bytes(), P.tab_l[0].bytes(), P.tab_l[1].bytes(),
-                     P.tab_l[2].bytes(), P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes()})
+                     P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(),
+                     P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes(), P.sxf.bytes()})
         P.device_bytes += (int64_t)b;
     return KIFMM_OK;
 }
@@ -862,8 +895,8 @@ int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int 
     if (t1 <= t0) return KIFMM_OK;
     (void)ops;  // the tensor-core path reads the split tables through their TMA maps
     KF_TRY(tc_box_split(in, P.Q, P.Qp, b0, b1, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
-    const CUtensorMap* m = P.tmaps[which];
-    KF_TRY(launch_pair_tc(which, m[0], m[1], P.texp[which], P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p,
+    const CUtensorMap* m = P.ops->tmaps[which];
+    KF_TRY(launch_pair_tc(which, m[0], m[1], P.ops->texp[which], P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p,
                           pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, out, P.err.p, s));
     launches += 2;
     return KIFMM_OK;
@@ -1012,11 +1045,11 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
 
 int plan_matvec(Plan& P, const double* q, double* out, cudaStream_t s) {
     if (P.fp64) {
-        Bufs<double> B{P.m2m_d.p, P.m2l_d.p, P.l2l_d.p, P.d2t_d.p, P.surf_d.p, P.tnrm_d.p,
+        Bufs<double> B{P.ops->m2m_d.p, P.ops->m2l_d.p, P.ops->l2l_d.p, P.d2t_d.p, P.surf_d.p, P.tnrm_d.p,
                        P.u_d.p,   P.d_d.p,   P.res_d.p, P.q_d.p};
         return matvec<double>(P, B, q, out, s);
     }
-    Bufs<float> B{P.m2m_f.p, P.m2l_f.p, P.l2l_f.p, P.d2t_f.p, P.surf_f.p, P.tnrm_f.p,
+    Bufs<float> B{nullptr, nullptr, nullptr, P.d2t_f.p, P.surf_f.p, P.tnrm_f.p,
                   P.u_f.p,   P.d_f.p,   P.res_f.p, P.q_f.p};
     return matvec<float>(P, B, q, out, s);
 }

@@ -5,6 +5,8 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 
+#include <memory>
+
 #include "common.cuh"
 
 namespace kifmm {
@@ -26,22 +28,37 @@ struct BieScratch {
     DBuf<double> q, krylov, w, r;
 };
 
+// Translation tables of one (device, order, cutoff, precision, ADL centring): shared by
+// every plan with that key, freed with the last of them.  FP64 form: m2m/m2l/l2l in
+// FP64.  Mixed form: FP16 hi/lo tables per family (0 M2M', 1 M2L', 2 L2L') scaled by
+// 2^texp, and their TMA tensor maps.
+struct OpTables {
+    int device = 0, p = 0;
+    double cutoff = 0;
+    bool fp64 = true, centered = false;
+    DBuf<double> m2m_d, m2l_d, l2l_d;
+    DBuf<__half> tab_h[3], tab_l[3];
+    int texp[3] = {0, 0, 0};
+    CUtensorMap tmaps[3][2];
+    int64_t bytes() const {
+        int64_t b = m2m_d.bytes() + m2l_d.bytes() + l2l_d.bytes();
+        for (int f = 0; f < 3; ++f) b += tab_h[f].bytes() + tab_l[f].bytes();
+        return b;
+    }
+};
+
 struct Plan {
     kifmm_tree_s* tree = nullptr;
     int kernel = 0, p = 0, Q = 0, Qp = 0, prec = 0;
     double cutoff = 0;
     bool fp64 = true;
 
-    // operators (Real = double for FP64, float for mixed), each Qp x Qp row-major;
-    // mixed: the translation tables live as scaled FP16 hi/lo pairs (tab_h/tab_l per
-    // family 0 M2M', 1 M2L', 2 L2L'; the FP32 builds are released), texp their scales,
-    // tmaps[family][0 = hi, 1 = lo] their TMA tensor maps; bexp the per-box input scales
-    // and vin_h/vin_l the scaled, split input vectors of a translation (nbox x Qp each)
-    DBuf<double> m2m_d, m2l_d, l2l_d, d2t_d;
-    DBuf<float> m2m_f, m2l_f, l2l_f, d2t_f;
-    DBuf<__half> tab_h[3], tab_l[3];
-    int texp[3] = {0, 0, 0};
-    CUtensorMap tmaps[3][2];
+    // translation tables (shared, see OpTables), each Qp x Qp row-major; D2T rows in
+    // the working precision; mixed: bexp the per-box input scales and vin_h/vin_l the
+    // scaled, split input vectors of a translation (nbox x Qp each)
+    std::shared_ptr<OpTables> ops;
+    DBuf<double> d2t_d;
+    DBuf<float> d2t_f;
     DBuf<int> bexp;
     DBuf<__half> vin_h, vin_l;
     DBuf<double> surf_d;            // Q x 3 unit surface

@@ -16,6 +16,8 @@ from .geometry import (  # noqa: F401
 )
 from .workloads import (  # noqa: F401
     WORKLOADS,
+    batch_instances,
+    serve_requests,
     workload,
     uniform_density,
 )

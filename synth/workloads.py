@@ -16,6 +16,10 @@ Sizes follow the configurations the library is benchmarked and tested on:
                       log-uniform in 1k-200k triangles (about 10M in all),
                       single-layer densities U[-1,1]; one forest.
 * ``batch_32``        the same recipe with 32 instances of 1k-50k (a quick case).
+
+``serve_requests`` draws a serving stream: Poisson arrivals at a given rate, sizes
+log-uniform in 2k-500k triangles, half polarization solves on sphere packs (1-64
+spheres, contrast U[2,20]) and half demag evaluations on a cube or a sphere.
 """
 from __future__ import annotations
 
@@ -90,6 +94,33 @@ def _batch_32():
     return _batch(32, 1000, 50000, 4100)
 
 
+def serve_requests(n_req: int, rate: float, seed: int, lo: int = 2000, hi: int = 500000,
+                   polar_frac: float = 0.5):
+    """Geometry and arrival time of each request of a serving stream (dicts; the
+    serving loop wraps them).  Arrivals: exponential gaps of mean 1/rate seconds."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_req))
+    out = []
+    for i in range(n_req):
+        if rng.uniform() < polar_frac:
+            ns = int(rng.integers(1, 65))
+            f = max(1, int(round(np.sqrt(sizes[i] / (20.0 * ns)))))
+            box = max(4.0, 20.0 * (ns / 64.0) ** (1.0 / 3.0))
+            c, r = sphere_pack(ns, 0.5, 1.5, box, 0.05, seed=seed + 1 + i)
+            m = pack_mesh(c, r, f)
+            contrast = rng.uniform(2.0, 20.0, size=ns)
+            out.append(dict(arrival=float(t[i]), kind="polar", tri=m.tri, sph=m.sph,
+                            eps_in=contrast[m.body] * 1.0, curv=1.0 / m.sph[:, 3], eps_out=1.0))
+        else:
+            if rng.uniform() < 0.5:
+                m = cube_surface(max(1, int(round(np.sqrt(sizes[i] / 12.0)))))
+            else:
+                m = geodesic_sphere(max(1, int(round(np.sqrt(sizes[i] / 20.0)))))
+            out.append(dict(arrival=float(t[i]), kind="demag", tri=m.tri, sph=m.sph))
+    return out
+
+
 WORKLOADS = {
     "sl_sphere_20k": _sl_sphere_20k,
     "demag_cube_1m": _demag_cube_1m,
@@ -105,4 +136,4 @@ def workload(name: str) -> dict:
     return WORKLOADS[name]()
 
 
-__all__ = ["Mesh", "WORKLOADS", "workload", "uniform_density", "batch_instances"]
+__all__ = ["Mesh", "WORKLOADS", "workload", "uniform_density", "batch_instances", "serve_requests"]
