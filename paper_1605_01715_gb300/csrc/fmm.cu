@@ -130,6 +130,110 @@ k_src2surf(const int* __restrict__ boxes, const int* __restrict__ off, const int
     }
 }
 
+// FP32 form: each thread owns exactly PER = ceil(Q / kSurfThreads) surface points (no
+// per-point branch); staged sources are float4 -- (x, y, z, q), and (q n_j) over two
+// float4 for dipoles -- built from FP32 hi/lo coordinates relative to the box centre,
+// so one broadcast load feeds PER evaluations.
+template <bool DIPOLE, int PER>
+__global__ void __launch_bounds__(kSurfThreads)
+k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx, double radius,
+         const int* __restrict__ lvl, const double* __restrict__ ctr, double root_h,
+         const int64_t* __restrict__ rng, const float* __restrict__ sxf, int64_t ns, const float* __restrict__ qs,
+         const float* __restrict__ surf, int Q, int Qp, float* __restrict__ outbuf) {
+    __shared__ float4 sp[kSurfThreads];
+    __shared__ float4 sd[DIPOLE ? kSurfThreads : 1];
+    const int b = boxes[blockIdx.x];
+    const double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
+    const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
+    const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
+    const float rf = (float)(radius * ldexp(root_h, -lvl[b]));
+    float px[PER], py[PER], pz[PER], acc[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int k = threadIdx.x + i * kSurfThreads;
+        const int kk = k < Q ? k : 0;
+        px[i] = rf * surf[3 * kk];
+        py[i] = rf * surf[3 * kk + 1];
+        pz[i] = rf * surf[3 * kk + 2];
+        acc[i] = 0.f;
+    }
+    const float d2 = (float)(kDelta * kDelta);
+    for (int e = off[blockIdx.x]; e < off[blockIdx.x + 1]; ++e) {
+        const int a = idx[e];
+        const int64_t sb = rng[4 * a], se = rng[4 * a + 1];
+        for (int64_t j0 = sb; j0 < se; j0 += kSurfThreads) {
+            const int64_t j = j0 + threadIdx.x;
+            if (j < se) {
+                sp[threadIdx.x] = make_float4((sxf[j] - chx) + (sxf[3 * ns + j] - clx),
+                                              (sxf[ns + j] - chy) + (sxf[4 * ns + j] - cly),
+                                              (sxf[2 * ns + j] - chz) + (sxf[5 * ns + j] - clz), qs[j]);
+                if (DIPOLE) sd[threadIdx.x] = make_float4(qs[ns + j], qs[2 * ns + j], 0.f, 0.f);
+            }
+            __syncthreads();
+            const int cnt = (int)((se - j0) < (int64_t)kSurfThreads ? (se - j0) : (int64_t)kSurfThreads);
+#pragma unroll 2
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 y = sp[jj];
+                float4 dq = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (DIPOLE) dq = sd[jj];
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const float dx = px[i] - y.x, dy = py[i] - y.y, dz = pz[i] - y.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float inv = rsqrtf(r2);
+                    float v;
+                    if (DIPOLE) v = (y.w * dx + dq.x * dy + dq.y * dz) * (inv * inv * inv);
+                    else v = y.w * inv;
+                    acc[i] += (r2 >= d2) ? v : 0.f;
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int k = threadIdx.x + i * kSurfThreads;
+        if (k < Q) outbuf[(size_t)b * Qp + k] += acc[i];
+    }
+}
+
+// Sources -> check surfaces of a CSR list of boxes (S2U: leaves and themselves; X list:
+// boxes and their X sources), FP32 through k_surf_f, FP64 through k_src2surf.
+template <typename Real>
+int launch_surf(const Plan& P, const Tree& T, bool dl, int nbox, const int* boxes, const int* off, const int* idx,
+                double radius, const Real* q, const Real* surf, Real* out, cudaStream_t s) {
+    if (nbox <= 0) return KIFMM_OK;
+    if constexpr (std::is_same<Real, float>::value) {
+        const int per = (P.Q + kSurfThreads - 1) / kSurfThreads;
+        switch (per * 2 + (dl ? 1 : 0)) {
+#define KF_SURF(PER)                                                                                             \
+    case 2 * PER:                                                                                                \
+        k_surf_f<false, PER><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, radius, T.lvl.p, T.ctr.p, T.root_h, \
+                                                           T.rng.p, P.sxf.p, T.ns, q, surf, P.Q, P.Qp, out);    \
+        break;                                                                                                   \
+    case 2 * PER + 1:                                                                                            \
+        k_surf_f<true, PER><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, radius, T.lvl.p, T.ctr.p, T.root_h,  \
+                                                          T.rng.p, P.sxf.p, T.ns, q, surf, P.Q, P.Qp, out);     \
+        break;
+            KF_SURF(1) KF_SURF(2) KF_SURF(3) KF_SURF(4) KF_SURF(5) KF_SURF(6) KF_SURF(7) KF_SURF(8)
+#undef KF_SURF
+            default:
+                set_error("check surface of %d points exceeds the FP32 surface kernel", P.Q);
+                return KIFMM_ERR_UNSUPPORTED;
+        }
+    } else {
+        if (dl)
+            k_src2surf<Real, true><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, radius, T.lvl.p, T.ctr.p, T.root_h,
+                                                                 T.rng.p, T.sxyz.p, T.ns, q, surf, P.Q, P.Qp, out);
+        else
+            k_src2surf<Real, false><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, radius, T.lvl.p, T.ctr.p,
+                                                                  T.root_h, T.rng.p, T.sxyz.p, T.ns, q, surf, P.Q,
+                                                                  P.Qp, out);
+    }
+    KF_CHECK_LAUNCH();
+    return KIFMM_OK;
+}
+
 // ---------------------------------------------------------------- grouped pair GEMM (U2U, M2L, L2L)
 // Every tile shares one operator: out[pout[j]] += Op . in[pin[j]] for its pairs.
 // CUDA-core SGEMM/DGEMM blocking: 64 rows x 64 pairs per pass, 4x4 per thread.
@@ -945,15 +1049,8 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_TRY(mark(1));
     // S2U
     if (P.n_s2u) {
-        if (dl)
-            k_src2surf<Real, true><<<P.n_s2u, kSurfThreads, 0, s>>>(
-                P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, kUpCheck, T.lvl.p, T.ctr.p, T.root_h, T.rng.p, T.sxyz.p,
-                T.ns, B.q, B.surf, P.Q, P.Qp, B.u);
-        else
-            k_src2surf<Real, false><<<P.n_s2u, kSurfThreads, 0, s>>>(
-                P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, kUpCheck, T.lvl.p, T.ctr.p, T.root_h, T.rng.p, T.sxyz.p,
-                T.ns, B.q, B.surf, P.Q, P.Qp, B.u);
-        KF_CHECK_LAUNCH();
+        KF_TRY(launch_surf<Real>(P, T, dl, P.n_s2u, P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, kUpCheck, B.q, B.surf,
+                                 B.u, s));
         ++launches;
     }
     KF_TRY(mark(2));
@@ -965,15 +1062,8 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_TRY(mark(3));
     // X list, then V list
     if (P.n_p2l) {
-        if (dl)
-            k_src2surf<Real, true><<<P.n_p2l, kSurfThreads, 0, s>>>(
-                P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, kDnCheck, T.lvl.p, T.ctr.p, T.root_h, T.rng.p, T.sxyz.p,
-                T.ns, B.q, B.surf, P.Q, P.Qp, B.d);
-        else
-            k_src2surf<Real, false><<<P.n_p2l, kSurfThreads, 0, s>>>(
-                P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, kDnCheck, T.lvl.p, T.ctr.p, T.root_h, T.rng.p, T.sxyz.p,
-                T.ns, B.q, B.surf, P.Q, P.Qp, B.d);
-        KF_CHECK_LAUNCH();
+        KF_TRY(launch_surf<Real>(P, T, dl, P.n_p2l, P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, kDnCheck, B.q, B.surf,
+                                 B.d, s));
         ++launches;
     }
     KF_TRY(mark(4));
