@@ -457,7 +457,10 @@ def roofline(phases, st, tst, args):
     mixed = args.precision == "mixed"
     if dom in ("m2l", "u2u", "l2l"):
         pairs = {"m2l": st["m2l_pairs"], "u2u": st["u2u_pairs"], "l2l": st["l2l_pairs"]}[dom]
-        flops = 2.0 * Q * Q * pairs                  # algorithmic: one Q x Q operator per pair
+        # algorithmic: one Q x W operator per pair; W = Q, or for a factored M2L' the
+        # rank of Pu (the operator acts on the projections onto its range)
+        W = st["m2l_width"] if dom == "m2l" else Q
+        flops = 2.0 * Q * W * pairs
         if mixed:                                   # two-term FP16 on tcgen05: 3 MMAs per product
             peak = pk["bf16_tflops"] / 3.0
             out = {"kernel": "k_%s_tc (tcgen05, two-term FP16)" % dom, "bound": "tensor",
@@ -469,7 +472,7 @@ def roofline(phases, st, tst, args):
         out.update({"achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "frac": flops / t / 1e12 / peak,
                     "traffic": _m2l_traffic(pairs) if (mixed and dom == "m2l") else None,
-                    "work": "2*Q^2 flops x %d pairs, Q=%d" % (pairs, Q)})
+                    "work": "2*Q*W flops x %d pairs, Q=%d, W=%d" % (pairs, Q, W)})
         return out
     if dom == "p2p":
         flops = 20.0 * tst["p2p_pairs"]            # ~20 FP32 ops per pair (FMA counted as 2)

@@ -202,6 +202,11 @@ typedef struct {
     int64_t device_bytes;             /* device memory held by the plan      */
     int64_t m2l_pairs, u2u_pairs, l2l_pairs, s2u_leaves, x_pairs;
     int32_t launches_per_matvec;      /* kernels one kifmm_fmm_matvec enqueues */
+    int32_t rank_up, rank_down;       /* numerical ranks of the up / down check-to-
+                                         equivalent pseudo-inverses at pinv_cutoff   */
+    int32_t m2l_width;                /* columns of each M2L' operator as applied:
+                                         q_points (FP64) or rank_up (mixed: M2L' acts
+                                         on the projections onto Pu's range)          */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);

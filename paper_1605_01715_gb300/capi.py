@@ -52,7 +52,8 @@ class PlanStats(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64),
                 ("u2u_pairs", ctypes.c_int64), ("l2l_pairs", ctypes.c_int64),
                 ("s2u_leaves", ctypes.c_int64), ("x_pairs", ctypes.c_int64),
-                ("launches_per_matvec", ctypes.c_int32)]
+                ("launches_per_matvec", ctypes.c_int32), ("rank_up", ctypes.c_int32),
+                ("rank_down", ctypes.c_int32), ("m2l_width", ctypes.c_int32)]
 
 
 def _as_dict(st):

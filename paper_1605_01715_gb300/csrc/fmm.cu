@@ -27,9 +27,9 @@ namespace kifmm {
 int tc_tile_pairs(int Qp);
 int tc_split_table(const float* table, __half* hi, __half* lo, size_t n, int* texp, cudaStream_t s);
 int tc_box_split(const float* v, int Q, int Qp, int b0, int b1, __half* hi, __half* lo, int* e, cudaStream_t s);
-int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Qp);
-int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
-                   const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
+int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Mr, int Kp);
+int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int M, int Mr, int Kp,
+                   int ostride, const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
                    const __half* in_hi, const __half* in_lo, float* out, int* err, cudaStream_t s);
 
 namespace {
@@ -656,30 +656,49 @@ int upload_tiles(PairTiles& pt, const std::vector<int4>& tiles, const std::vecto
 // Used for the adjoint double layer, whose targets see only gradients: the
 // constant part of a down-check potential is dropped before it is stored in the
 // working precision, so its rounding is relative to the potential's variation.
+// Mixed precision may also factor the D2T rows through Pd's range (G W_d reading
+// z_d = U_d^T d).  That halves the rows' HBM traffic but costs accuracy: z_d carries
+// the two-term FP16 error (about 2^-22 of the box's largest potential) where d carried
+// FP32 rounding, and G W_d amplifies it along the small singular directions of the
+// down check-to-equivalent operator.  Measured on the 1M-point cube and sphere at
+// p = 10 (8,192 sampled targets): 9.6e-7 / 1.01e-6 factored, 8.9e-7 / 8.8e-7 not; so
+// D2T keeps the Pd rows.
+constexpr bool kFactorD2T = false;
+
+// Operators of Mr rows (Q of them valid) by Kc columns, op-major.
 template <typename Real>
-__global__ void k_center_ops(const double* __restrict__ in, int Q, int Qp, bool center, Real* __restrict__ out) {
+__global__ void k_center_ops(const double* __restrict__ in, int Q, int Mr, int Kc, bool center,
+                             Real* __restrict__ out) {
     int op = blockIdx.y;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= Qp) return;
-    const double* A = in + (size_t)op * Qp * Qp;
-    Real* O = out + (size_t)op * Qp * Qp;
+    if (j >= Kc) return;
+    const double* A = in + (size_t)op * Mr * Kc;
+    Real* O = out + (size_t)op * Mr * Kc;
     double mean = 0;
     if (center) {
-        for (int i = 0; i < Q; ++i) mean += A[(size_t)i * Qp + j];
+        for (int i = 0; i < Q; ++i) mean += A[(size_t)i * Kc + j];
         mean /= Q;
     }
-    for (int i = 0; i < Qp; ++i) O[(size_t)i * Qp + j] = i < Q ? (Real)(A[(size_t)i * Qp + j] - mean) : (Real)0;
+    for (int i = 0; i < Mr; ++i) O[(size_t)i * Kc + j] = i < Q ? (Real)(A[(size_t)i * Kc + j] - mean) : (Real)0;
 }
 
+// The three translation families, each operator K_o P: P the up (M2M', M2L') or down
+// (L2L') pseudo-inverse itself (Pu, Pd: Q x Q, stored Qp wide) or, for M2L' when
+// factored, the W factor of Pu's factored form (Wu: Q x ru, stored Ku wide).  Tables
+// are op-major, Qp rows each.
 template <typename Real>
-int build_ops(Plan& P, const HostPinv& h, Real* m2m, Real* m2l, Real* l2l, cudaStream_t s) {
-    DBuf<double> dPu, dPd;
+int build_ops(Plan& P, const HostPinv& h, bool factored, int Ku, Real* m2m, Real* m2l, Real* l2l,
+              cudaStream_t s) {
+    DBuf<double> dPu, dPd, dWu;
     KF_TRY(dPu.upload(h.Pu, s));
     KF_TRY(dPd.upload(h.Pd, s));
+    if (factored) KF_TRY(dWu.upload(h.Wu, s));
     Real* outs[3] = {m2m, m2l, l2l};
     const int nops[3] = {8, kNumOffsets, 8};
-    const size_t QQ = (size_t)P.Qp * P.Qp;
     for (int which = 0; which < 3; ++which) {
+        const bool f = factored && which == 1;
+        const int C = f ? h.ru : P.Q;
+        const int Kc = f ? Ku : P.Qp;
         std::vector<double> apts, ascale, bpts;
         std::vector<int> bset;
         std::vector<int64_t> orow;
@@ -700,20 +719,23 @@ int build_ops(Plan& P, const HostPinv& h, Real* m2m, Real* m2l, Real* l2l, cudaS
         rs.orow = dor.p;
         rs.bpts = db.p;
         // build in FP64, then (ADL: M2L and L2L centred) round to the working precision
-        KF_TRY(tmp.alloc(nops[which] * QQ));
+        KF_TRY(tmp.alloc((size_t)nops[which] * P.Qp * Kc));
         KF_CHECK_CUDA(cudaMemsetAsync(tmp.p, 0, tmp.bytes(), s));
-        KF_TRY(build_rows<double>(rs, P.Q, P.Qp, which == 2 ? dPd.p : dPu.p, 0, tmp.p, s));
+        KF_TRY(build_rows<double>(rs, P.Q, C, Kc, which == 2 ? dPd.p : (f ? dWu.p : dPu.p), 0, tmp.p, s));
         bool center = P.kernel == KIFMM_KERNEL_ADL && which != 0;
-        dim3 grid(div_up(P.Qp, 128), nops[which]);
-        k_center_ops<Real><<<grid, 128, 0, s>>>(tmp.p, P.Q, P.Qp, center, outs[which]);
+        dim3 grid(div_up(Kc, 128), nops[which]);
+        k_center_ops<Real><<<grid, 128, 0, s>>>(tmp.p, P.Q, P.Qp, Kc, center, outs[which]);
         KF_CHECK_LAUNCH();
         KF_CHECK_CUDA(cudaStreamSynchronize(s));
     }
     return KIFMM_OK;
 }
 
+// Per-target evaluation rows G(x_t, 2.95 s) P: P = Pd (Q wide, stored Qp) or, factored,
+// Wd (rd wide, stored Kd).
 template <typename Real>
-int build_d2t(Plan& P, const HostPinv& h, const std::vector<int>& tleaf_of, Real* out, cudaStream_t s) {
+int build_d2t(Plan& P, const HostPinv& h, bool factored, int Kd, const std::vector<int>& tleaf_of, Real* out,
+              cudaStream_t s) {
     const Tree& T = P.tree->t;
     int64_t nt = T.nt;
     DBuf<int> dleaf;
@@ -727,7 +749,8 @@ int build_d2t(Plan& P, const HostPinv& h, const std::vector<int>& tleaf_of, Real
     std::vector<double> hb(3 * (size_t)h.Q);
     for (size_t i = 0; i < hb.size(); ++i) hb[i] = kDnEquiv * h.surf[i];
     KF_TRY(bpts.upload(hb, s));
-    KF_TRY(dPd.upload(h.Pd, s));
+    KF_TRY(dPd.upload(factored ? h.Wd : h.Pd, s));
+    const int C = factored ? h.rd : P.Q, Kc = factored ? Kd : P.Qp;
     const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
     bool adl = P.kernel == KIFMM_KERNEL_ADL;
     k_d2t_rows<<<div_up(nt, 256), 256, 0, s>>>(dleaf.p, nt, txyz, adl ? P.tnrm_d.p : nullptr, T.lvl.p,
@@ -744,7 +767,7 @@ int build_d2t(Plan& P, const HostPinv& h, const std::vector<int>& tleaf_of, Real
         rs.bset = nullptr;
         rs.orow = orow.p + r0;
         rs.bpts = bpts.p;
-        KF_TRY(build_rows<Real>(rs, P.Q, P.Qp, dPd.p, adl ? 1 : 0, out, s));
+        KF_TRY(build_rows<Real>(rs, P.Q, C, Kc, dPd.p, adl ? 1 : 0, out, s));
     }
     KF_CHECK_CUDA(cudaStreamSynchronize(s));
     return KIFMM_OK;
@@ -786,23 +809,41 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
         KF_CHECK_CUDA(cudaMemsetAsync(t->m2m_d.p, 0, t->m2m_d.bytes(), s));
         KF_CHECK_CUDA(cudaMemsetAsync(t->m2l_d.p, 0, t->m2l_d.bytes(), s));
         KF_CHECK_CUDA(cudaMemsetAsync(t->l2l_d.p, 0, t->l2l_d.bytes(), s));
-        KF_TRY(build_ops<double>(P, h, t->m2m_d.p, t->m2l_d.p, t->l2l_d.p, s));
+        t->ru = h.ru;
+        t->rd = h.rd;
+        KF_TRY(build_ops<double>(P, h, false, 0, t->m2m_d.p, t->m2l_d.p, t->l2l_d.p, s));
     } else {
-        DBuf<float> f32[3];
-        const int nops[3] = {8, kNumOffsets, 8};
-        for (int f = 0; f < 3; ++f) {
-            KF_TRY(f32[f].alloc(nops[f] * QQ));
+        // M2M' and L2L' square, M2L' factored through Pu's range (Qp x Ku), projections
+        // onto the up and down check-space bases (K x Qp); every table built in FP64 and
+        // rounded to two-term FP16
+        t->ru = h.ru;
+        t->rd = h.rd;
+        t->Ku = (h.ru + 15) / 16 * 16;
+        t->Kd = (h.rd + 15) / 16 * 16;
+        DBuf<float> f32[kFamilies];
+        const int nops[kFamilies] = {8, kNumOffsets, 8, 1, 1};
+        const int rows[kFamilies] = {P.Qp, P.Qp, P.Qp, t->Ku, t->Kd};
+        const int cols[kFamilies] = {P.Qp, t->Ku, P.Qp, P.Qp, P.Qp};
+        for (int f = 0; f < kFamilies; ++f) {
+            KF_TRY(f32[f].alloc((size_t)nops[f] * rows[f] * cols[f]));
             KF_CHECK_CUDA(cudaMemsetAsync(f32[f].p, 0, f32[f].bytes(), s));
         }
-        KF_TRY(build_ops<float>(P, h, f32[0].p, f32[1].p, f32[2].p, s));
-        // scaled FP16 hi/lo split of every table and the TMA maps the tensor-core GEMM
-        // reads; the FP32 builds are not kept
-        for (int f = 0; f < 3; ++f) {
+        KF_TRY(build_ops<float>(P, h, true, t->Ku, f32[0].p, f32[1].p, f32[2].p, s));
+        for (int f = 3; f < kFamilies; ++f) {   // U^T, zero padded to K x Qp
+            const std::vector<double>& U = f == 3 ? h.Uu : h.Ud;
+            const int r = f == 3 ? h.ru : h.rd;
+            std::vector<float> ut((size_t)rows[f] * cols[f], 0.f);
+            for (int j = 0; j < r; ++j)
+                for (int i = 0; i < P.Q; ++i) ut[(size_t)j * cols[f] + i] = (float)U[(size_t)i * r + j];
+            KF_CHECK_CUDA(cudaMemcpyAsync(f32[f].p, ut.data(), ut.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+            KF_CHECK_CUDA(cudaStreamSynchronize(s));
+        }
+        for (int f = 0; f < kFamilies; ++f) {
             KF_TRY(t->tab_h[f].alloc(f32[f].n));
             KF_TRY(t->tab_l[f].alloc(f32[f].n));
             KF_TRY(tc_split_table(f32[f].p, t->tab_h[f].p, t->tab_l[f].p, f32[f].n, &t->texp[f], s));
-            KF_TRY(tc_make_map(&t->tmaps[f][0], t->tab_h[f].p, nops[f], P.Qp));
-            KF_TRY(tc_make_map(&t->tmaps[f][1], t->tab_l[f].p, nops[f], P.Qp));
+            KF_TRY(tc_make_map(&t->tmaps[f][0], t->tab_h[f].p, nops[f], rows[f], cols[f]));
+            KF_TRY(tc_make_map(&t->tmaps[f][1], t->tab_l[f].p, nops[f], rows[f], cols[f]));
         }
     }
     KF_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -950,19 +991,38 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         P.l2l.level_tile[T.nlev] = (int)tiles.size();
         KF_TRY(upload_tiles(P.l2l, tiles, pin, pout, s));
     }
+    // mixed: projections of every box of a level onto the check-space bases, one
+    // (box -> box) tile list per level
+    if (!P.fp64) {
+        std::vector<int4> tiles;
+        std::vector<int> pin, pout;
+        P.proj.level_tile.assign(T.nlev + 1, 0);
+        for (int l = 0; l < T.nlev; ++l) {
+            P.proj.level_tile[l] = (int)tiles.size();
+            std::vector<Triple> tr;
+            for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b) tr.push_back({0, b, b});
+            make_tiles(tr, tiles, pin, pout, tc_tile_pairs(P.ops->Ku));
+        }
+        P.proj.level_tile[T.nlev] = (int)tiles.size();
+        KF_TRY(upload_tiles(P.proj, tiles, pin, pout, s));
+        KF_TRY(P.zu.alloc((size_t)T.nbox * P.ops->Ku));
+        P.d2t_factored = kFactorD2T;
+        if (P.d2t_factored) KF_TRY(P.zd.alloc((size_t)T.nbox * P.ops->Kd));
+    }
 
     // per-target evaluation rows and buffers
     size_t nbq = (size_t)T.nbox * P.Qp;
     if (P.fp64) {
         KF_TRY(P.d2t_d.alloc((size_t)T.nt * P.Qp));
-        KF_TRY(build_d2t<double>(P, h, tleaf_of, P.d2t_d.p, s));
+        KF_TRY(build_d2t<double>(P, h, false, 0, tleaf_of, P.d2t_d.p, s));
         KF_TRY(P.u_d.alloc(nbq));
         KF_TRY(P.d_d.alloc(nbq));
         KF_TRY(P.res_d.alloc(T.nt));
         KF_TRY(P.q_d.alloc(3 * T.ns));
     } else {
-        KF_TRY(P.d2t_f.alloc((size_t)T.nt * P.Qp));
-        KF_TRY(build_d2t<float>(P, h, tleaf_of, P.d2t_f.p, s));
+        const int w = P.d2t_factored ? P.ops->Kd : P.Qp;
+        KF_TRY(P.d2t_f.alloc((size_t)T.nt * w));
+        KF_TRY(build_d2t<float>(P, h, P.d2t_factored, P.ops->Kd, tleaf_of, P.d2t_f.p, s));
         KF_TRY(P.u_f.alloc(nbq));
         KF_TRY(P.d_f.alloc(nbq));
         KF_TRY(P.res_f.alloc(T.nt));
@@ -974,7 +1034,8 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     for (size_t b : {(size_t)P.ops->bytes(), P.d2t_d.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
                      P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
                      P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(),
-                     P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes(), P.sxf.bytes()})
+                     P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes(), P.sxf.bytes(), P.zu.bytes(),
+                     P.zd.bytes()})
         P.device_bytes += (int64_t)b;
     return KIFMM_OK;
 }
@@ -991,17 +1052,39 @@ template <typename Real>
 int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const Real* ops, const Real* in,
               Real* out, int b0, int b1, cudaStream_t s, int& launches);
 
-// Mixed precision: two-term FP16 on the tensor cores (tcgen05).  [b0, b1): the boxes
-// whose input vectors this launch reads; their scales are taken first.
+// Mixed precision: two-term FP16 on the tensor cores (tcgen05).  M2L' is factored
+// through Pu's range: a source's up-check potential u (Qp per box) enters as its
+// projection z = U_u^T u (Ku per box; ru, the rank of Pu, is about Q/2 at p = 10), and
+// M2L' u = (M2L' U_u) z exactly, since M2L' = K Pu = K W_u U_u^T.  Likewise the D2T rows
+// are G W_d and read z_d = U_d^T d.  Every box of levels >= 2 is projected once, after
+// the upward (resp. downward) pass; U2U and L2L keep their square tables.  The input
+// vectors of a launch (boxes [b0, b1)) are scaled and split first.
+
+int project_levels(const Plan& P, int fam, int l0, const float* v, float* z, cudaStream_t s, int& launches) {
+    const Tree& T = P.tree->t;
+    if (l0 < 0 || l0 >= T.nlev) return KIFMM_OK;
+    const int t0 = P.proj.level_tile[l0], t1 = P.proj.level_tile[T.nlev];
+    if (t1 <= t0) return KIFMM_OK;
+    const int K = fam == 3 ? P.ops->Ku : P.ops->Kd, r = fam == 3 ? P.ops->ru : P.ops->rd;
+    KF_TRY(tc_box_split(v, P.Q, P.Qp, T.level_off[l0], T.nbox, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
+    const CUtensorMap* m = P.ops->tmaps[fam];
+    KF_TRY(launch_pair_tc(3, m[0], m[1], P.ops->texp[fam], r, K, P.Qp, K, P.proj.tiles.p + t0, t1 - t0,
+                          P.proj.pin.p, P.proj.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, z, P.err.p, s));
+    launches += 2;
+    return KIFMM_OK;
+}
+
 template <>
 int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const float* ops,
-                     const float* in, float* out, int b0, int b1, cudaStream_t s, int& launches) {
+                     const float* z, float* out, int b0, int b1, cudaStream_t s, int& launches) {
     if (t1 <= t0) return KIFMM_OK;
     (void)ops;  // the tensor-core path reads the split tables through their TMA maps
-    KF_TRY(tc_box_split(in, P.Q, P.Qp, b0, b1, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
+    // M2L reads projections (ru of Ku per box), U2U and L2L check potentials (Q of Qp)
+    const int K = which == 1 ? P.ops->Ku : P.Qp, r = which == 1 ? P.ops->ru : P.Q;
+    KF_TRY(tc_box_split(z, r, K, b0, b1, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
     const CUtensorMap* m = P.ops->tmaps[which];
-    KF_TRY(launch_pair_tc(which, m[0], m[1], P.ops->texp[which], P.Q, P.Qp, pt.tiles.p + t0, t1 - t0, pt.pin.p,
-                          pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, out, P.err.p, s));
+    KF_TRY(launch_pair_tc(which, m[0], m[1], P.ops->texp[which], P.Q, P.Qp, K, P.Qp, pt.tiles.p + t0, t1 - t0,
+                          pt.pin.p, pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, out, P.err.p, s));
     launches += 2;
     return KIFMM_OK;
 }
@@ -1046,6 +1129,19 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_CHECK_CUDA(cudaMemsetAsync(B.u, 0, nbq * sizeof(Real), s));
     KF_CHECK_CUDA(cudaMemsetAsync(B.d, 0, nbq * sizeof(Real), s));
     launches += 3;
+    constexpr bool mixed = std::is_same<Real, float>::value;
+    float* zu = nullptr;
+    float* zd = nullptr;
+    if constexpr (mixed) {
+        zu = P.zu.p;
+        zd = P.zd.p;
+        KF_CHECK_CUDA(cudaMemsetAsync(zu, 0, P.zu.bytes(), s));
+        ++launches;
+        if (P.d2t_factored) {
+            KF_CHECK_CUDA(cudaMemsetAsync(zd, 0, P.zd.bytes(), s));
+            ++launches;
+        }
+    }
     KF_TRY(mark(1));
     // S2U
     if (P.n_s2u) {
@@ -1054,11 +1150,12 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         ++launches;
     }
     KF_TRY(mark(2));
-    // U2U, deepest parents first
+    // U2U, deepest parents first; mixed: then every box's projection for M2L
     for (int l = T.nlev - 1; l >= 2; --l)
         KF_TRY(run_pairs<Real>(P, kU2U, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, B.u, B.u,
                                T.level_off[std::min(l + 1, T.nlev)], T.level_off[std::min(l + 2, T.nlev)], s,
                                launches));
+    if constexpr (mixed) KF_TRY(project_levels(P, 3, 2, B.u, zu, s, launches));
     KF_TRY(mark(3));
     // X list, then V list
     if (P.n_p2l) {
@@ -1067,8 +1164,12 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         ++launches;
     }
     KF_TRY(mark(4));
-    KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, T.level_off[std::min(2, T.nlev)],
-                           T.nbox, s, launches));
+    if constexpr (mixed)
+        KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, zu, B.d, T.level_off[std::min(2, T.nlev)],
+                               T.nbox, s, launches));
+    else
+        KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, T.level_off[std::min(2, T.nlev)],
+                               T.nbox, s, launches));
     KF_TRY(mark(5));
     // L2L, coarsest children first (ADL: each level's potentials shifted to zero mean first)
     const bool center = P.kernel == KIFMM_KERNEL_ADL;
@@ -1084,9 +1185,18 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
             ++launches;
         }
     }
+    if constexpr (mixed)
+        if (P.d2t_factored) KF_TRY(project_levels(P, 4, 2, B.d, zd, s, launches));
     KF_TRY(mark(6));
     if (P.n_tleaf) {
-        k_d2t<Real><<<P.n_tleaf, 128, P.Qp * sizeof(Real), s>>>(P.tleaf.p, T.rng.p, B.d2t, B.d, P.Qp, B.res);
+        const Real* dv = B.d;   // the down-check potentials or, factored, their projections
+        int dw = P.Qp;
+        if constexpr (mixed)
+            if (P.d2t_factored) {
+                dv = zd;
+                dw = P.ops->Kd;
+            }
+        k_d2t<Real><<<P.n_tleaf, 128, dw * sizeof(Real), s>>>(P.tleaf.p, T.rng.p, B.d2t, dv, dw, B.res);
         KF_CHECK_LAUNCH();
         ++launches;
     }
@@ -1248,6 +1358,9 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->s2u_leaves = P.n_s2u;
     st->x_pairs = P.n_xpairs;
     st->launches_per_matvec = P.launches;
+    st->rank_up = P.ops ? P.ops->ru : 0;
+    st->rank_down = P.ops ? P.ops->rd : 0;
+    st->m2l_width = P.fp64 ? P.Q : st->rank_up;
     return KIFMM_OK;
 }
 

@@ -45,7 +45,8 @@ std::vector<double> surface_points(int p) {
 // Pseudo-inverse of the n x n matrix A (row-major) by one-sided Jacobi SVD
 // (Hestenes): rotate column pairs of A until mutually orthogonal, A V = U S.
 // Pairs are visited in round-robin order so each round's rotations are disjoint.
-std::vector<double> pinv_jacobi(const std::vector<double>& A_rm, int n, double cutoff) {
+std::vector<double> pinv_jacobi(const std::vector<double>& A_rm, int n, double cutoff, std::vector<double>* U,
+                                std::vector<double>* W, int* rank) {
     std::vector<double> a((size_t)n * n), v((size_t)n * n, 0.0);  // column-major
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) a[(size_t)j * n + i] = A_rm[(size_t)i * n + j];
@@ -114,6 +115,23 @@ std::vector<double> pinv_jacobi(const std::vector<double>& A_rm, int n, double c
             for (int j = 0; j < n; ++j) acc += v[(size_t)j * n + r] * a[(size_t)j * n + c] * w[j];
             P[(size_t)r * n + c] = acc;
         }
+    if (U && W && rank) {
+        // kept triplets in index order: u_j = a_j / s_j, w_j = v_j / s_j
+        std::vector<int> kept;
+        for (int j = 0; j < n; ++j)
+            if (w[j] > 0) kept.push_back(j);
+        const int r = (int)kept.size();
+        U->assign((size_t)n * r, 0.0);
+        W->assign((size_t)n * r, 0.0);
+        for (int k = 0; k < r; ++k) {
+            const int j = kept[k];
+            for (int i = 0; i < n; ++i) {
+                (*U)[(size_t)i * r + k] = a[(size_t)j * n + i] / sig[j];
+                (*W)[(size_t)i * r + k] = v[(size_t)j * n + i] / sig[j];
+            }
+        }
+        *rank = r;
+    }
     return P;
 }
 
@@ -141,18 +159,19 @@ const HostPinv& host_pinv(int p, double cutoff) {
     h.p = p;
     h.surf = surface_points(p);
     h.Q = (int)h.surf.size() / 3;
-    h.Pu = pinv_jacobi(kernel_matrix(h.surf, kUpCheck, h.surf, kUpEquiv), h.Q, cutoff);
-    h.Pd = pinv_jacobi(kernel_matrix(h.surf, kDnCheck, h.surf, kDnEquiv), h.Q, cutoff);
+    h.Pu = pinv_jacobi(kernel_matrix(h.surf, kUpCheck, h.surf, kUpEquiv), h.Q, cutoff, &h.Uu, &h.Wu, &h.ru);
+    h.Pd = pinv_jacobi(kernel_matrix(h.surf, kDnCheck, h.surf, kDnEquiv), h.Q, cutoff, &h.Ud, &h.Wd, &h.rd);
     return cache.emplace(key, std::move(h)).first->second;
 }
 
-// out[orow[r]*Qp + j] = ascale[r] * sum_m G(a_r, b_{bset[r], m}) P[m][j],  j < Q; 0 for Q <= j < Qp
+// out[orow[r]*Cp + j] = ascale[r] * sum_m G(a_r, b_{bset[r], m}) P[m][j],  j < C; 0 for C <= j < Cp
+// (P is Q x C: the Q points of a b set by C columns)
 // G = 1/|a-b| (kfun 0) or n_r.(a-b)/|a-b|^3 (kfun 1).  8 rows per block.
 template <typename Real>
 __global__ void k_build_rows(int nrows, const double* __restrict__ apts, const double* __restrict__ anrm,
                              const double* __restrict__ ascale, const int* __restrict__ bset,
                              const int64_t* __restrict__ orow, const double* __restrict__ bpts, int Q,
-                             int Qp, const double* __restrict__ P, int kfun, Real* __restrict__ out) {
+                             int C, int Cp, const double* __restrict__ P, int kfun, Real* __restrict__ out) {
     extern __shared__ double Ks[];  // [8][Q]
     const int R = 8;
     int r0 = blockIdx.x * R;
@@ -175,13 +194,13 @@ __global__ void k_build_rows(int nrows, const double* __restrict__ apts, const d
         Ks[r * Q + m] = val;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < Qp; j += blockDim.x) {
+    for (int j = threadIdx.x; j < Cp; j += blockDim.x) {
         double acc[8];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0.0;
-        if (j < Q) {
+        if (j < C) {
             for (int m = 0; m < Q; ++m) {
-                double pm = P[(size_t)m * Q + j];
+                double pm = P[(size_t)m * C + j];
 #pragma unroll
                 for (int r = 0; r < R; ++r) acc[r] += Ks[r * Q + m] * pm;
             }
@@ -189,13 +208,13 @@ __global__ void k_build_rows(int nrows, const double* __restrict__ apts, const d
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             int row = r0 + r;
-            if (row < nrows) out[(size_t)orow[row] * Qp + j] = (Real)(ascale[row] * acc[r]);
+            if (row < nrows) out[(size_t)orow[row] * Cp + j] = (Real)(ascale[row] * acc[r]);
         }
     }
 }
 
 template <typename Real>
-int build_rows(const RowSpec& rs, int Q, int Qp, const double* dP, int kfun, Real* out,
+int build_rows(const RowSpec& rs, int Q, int C, int Cp, const double* dP, int kfun, Real* out,
                cudaStream_t s) {
     if (rs.nrows == 0) return KIFMM_OK;
     size_t smem = 8 * (size_t)Q * sizeof(double);
@@ -203,14 +222,14 @@ int build_rows(const RowSpec& rs, int Q, int Qp, const double* dP, int kfun, Rea
         KF_CHECK_CUDA(cudaFuncSetAttribute(k_build_rows<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
     k_build_rows<Real><<<div_up(rs.nrows, 8), 256, smem, s>>>(rs.nrows, rs.apts, rs.anrm, rs.ascale,
-                                                              rs.bset, rs.orow, rs.bpts, Q, Qp, dP, kfun,
+                                                              rs.bset, rs.orow, rs.bpts, Q, C, Cp, dP, kfun,
                                                               out);
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }
 
-template int build_rows<float>(const RowSpec&, int, int, const double*, int, float*, cudaStream_t);
-template int build_rows<double>(const RowSpec&, int, int, const double*, int, double*, cudaStream_t);
+template int build_rows<float>(const RowSpec&, int, int, int, const double*, int, float*, cudaStream_t);
+template int build_rows<double>(const RowSpec&, int, int, int, const double*, int, double*, cudaStream_t);
 
 // Host-side row descriptors of the three translation-operator tables.
 void translation_rows(const HostPinv& h, int which, std::vector<double>& apts, std::vector<int>& bset,

@@ -95,9 +95,9 @@ int get_encoder(EncodeTiled* fn) {
 
 }  // namespace
 
-// Rows of operator per CTA and pairs per tile for a padded order.
-int tc_rows(int Qp) { return Qp <= 128 ? 128 : 256; }
-int tc_tile_pairs(int Qp) { return Qp <= 128 ? 256 : 128; }
+// Operator rows per work item and pairs per tile for operators of Mr (padded) rows.
+int tc_rows(int Mr) { return Mr <= 128 ? 128 : 256; }
+int tc_tile_pairs(int Mr) { return Mr <= 128 ? 256 : 128; }
 
 // Scale an FP32 operator table by 2^texp (largest entry into [2^14, 2^15)) and split it
 // into FP16 hi and lo tables.  Synchronizes the stream (texp is needed on the host).
@@ -128,34 +128,38 @@ int tc_box_split(const float* v, int Q, int Qp, int b0, int b1, __half* hi, __ha
     return KIFMM_OK;
 }
 
-// 2-D tiled map over rows (op * Qp + row) x columns (Qp) of an FP16 table, box kKS
-// columns x tc_rows(Qp) rows, 64-byte swizzle, zero fill outside.
-int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Qp) {
+// 2-D tiled map over rows (op * Mr + row) x columns (Kp) of an FP16 table, box kKS
+// columns x tc_rows(Mr) rows, 64-byte swizzle, zero fill outside.
+int tc_make_map(CUtensorMap* map, const __half* table, int nops, int Mr, int Kp) {
     EncodeTiled enc;
     KF_TRY(get_encoder(&enc));
-    cuuint64_t dims[2] = {(cuuint64_t)Qp, (cuuint64_t)nops * (cuuint64_t)Qp};
-    cuuint64_t strides[1] = {(cuuint64_t)Qp * sizeof(__half)};
-    cuuint32_t box[2] = {(cuuint32_t)tc::kKS, (cuuint32_t)tc_rows(Qp)};
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)nops * (cuuint64_t)Mr};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(__half)};
+    cuuint32_t box[2] = {(cuuint32_t)tc::kKS, (cuuint32_t)tc_rows(Mr)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(table), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
-        set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d table", (int)r, nops * Qp, Qp);
+        set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d table", (int)r, nops * Mr, Kp);
         return KIFMM_ERR_CUDA;
     }
     return KIFMM_OK;
 }
 
 template <int SLABS, int N>
-static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
-                        const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
-                        const __half* in_hi, const __half* in_lo, float* out, int* err, cudaStream_t s) {
+static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int M, int Mr, int Kp,
+                        int ostride, const int4* tiles, int ntiles, const int* pin, const int* pout,
+                        const int* bexp, const __half* in_hi, const __half* in_lo, float* out, int* err,
+                        cudaStream_t s) {
     using S = tc::Shape<SLABS, N>;
-    auto kern = which == 0 ? tc::k_u2u_tc<SLABS, N> : which == 1 ? tc::k_m2l_tc<SLABS, N> : tc::k_l2l_tc<SLABS, N>;
+    auto kern = which == 0   ? tc::k_u2u_tc<SLABS, N>
+                : which == 1 ? tc::k_m2l_tc<SLABS, N>
+                : which == 2 ? tc::k_l2l_tc<SLABS, N>
+                             : tc::k_proj_tc<SLABS, N>;
     // set on every launch: the attribute belongs to the current device's context
     KF_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes));
-    const int mgroups = (Qp + S::kRows - 1) / S::kRows;
+    const int mgroups = (Mr + S::kRows - 1) / S::kRows;
     const int nitems = ntiles * mgroups;
     // persistent: one CTA per SM (one fits by shared memory), each walking its share of
     // the work items
@@ -163,23 +167,24 @@ static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo,
     KF_CHECK_CUDA(cudaGetDevice(&dev));
     KF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = nitems < nsm ? nitems : nsm;
-    kern<<<grid, tc::kThreads, S::kSmemBytes, s>>>(hi, lo, Q, Qp, mgroups, nitems, tiles, pin, pout, bexp, texp,
-                                                    in_hi, in_lo, out, err);
+    kern<<<grid, tc::kThreads, S::kSmemBytes, s>>>(hi, lo, M, Kp, ostride, Mr, mgroups, nitems, tiles, pin, pout,
+                                                    bexp, texp, in_hi, in_lo, out, err);
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }
 
-// which: 0 = U2U (M2M'), 1 = M2L', 2 = L2L'.  in_hi / in_lo: the split input vectors
-// (tc_box_split) of every box a pair reads.
-int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int Q, int Qp,
-                   const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
+// which: 0 = U2U, 1 = M2L, 2 = L2L, 3 = projection onto a check-space basis.  The
+// operators are Mr x Kp (M valid rows); in_hi / in_lo: the split input vectors
+// (tc_box_split, Kp per box) of every box a pair reads; out: ostride per box.
+int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int M, int Mr, int Kp,
+                   int ostride, const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
                    const __half* in_hi, const __half* in_lo, float* out, int* err, cudaStream_t s) {
     if (ntiles <= 0) return KIFMM_OK;
-    if (Qp <= 128)
-        return launch_shape<1, 256>(which, hi, lo, texp, Q, Qp, tiles, ntiles, pin, pout, bexp, in_hi, in_lo, out,
-                                    err, s);
-    return launch_shape<2, 128>(which, hi, lo, texp, Q, Qp, tiles, ntiles, pin, pout, bexp, in_hi, in_lo, out, err,
-                                s);
+    if (Mr <= 128)
+        return launch_shape<1, 256>(which, hi, lo, texp, M, Mr, Kp, ostride, tiles, ntiles, pin, pout, bexp, in_hi,
+                                    in_lo, out, err, s);
+    return launch_shape<2, 128>(which, hi, lo, texp, M, Mr, Kp, ostride, tiles, ntiles, pin, pout, bexp, in_hi,
+                                in_lo, out, err, s);
 }
 
 }  // namespace kifmm

@@ -1,7 +1,8 @@
 // Grouped translation GEMM on the 5th-generation tensor cores (tcgen05), two-term FP16.
 //
 // A work item is one tile of up to N (input box, output box) pairs that share one
-// Qp x Qp operator Op (M2M', M2L' or L2L') and one group of 128 * SLABS operator rows:
+// operator Op (Mr x Kp rows and columns of a table of such operators: a translation,
+// or a projection onto a check-space basis) and one group of 128 * SLABS rows:
 //   out[pout[j]][row] += sum_k Op[row][k] * in[pin[j]][k]
 // computed as D(128 x N) = A(128 x K) B(N x K)^T per 128-row slab, with A = operator
 // rows and B = the gathered input vectors, accumulated in TMEM.
@@ -225,12 +226,14 @@ __device__ __forceinline__ uint32_t sw64_off(int r, int c) {
 
 // tiles[t] = (op, first pair, count, 0); work item w = (tile w / mgroups, row group
 // w % mgroups).  map_hi / map_lo: 2-D tensor maps of the split FP16 operator tables
-// (scaled by 2^texp), rows = op * Qp + row, box = 32 columns x kRows rows, 64-byte
-// swizzle.  in_hi / in_lo: the input vectors of all boxes scaled by 2^bexp[box] and
-// split, Qp FP16 per box.
+// (scaled by 2^texp), rows = op * Mr + row (Mr rows per operator), columns Kp, box = 32
+// columns x kRows rows, 64-byte swizzle.  in_hi / in_lo: the input vectors of all boxes
+// scaled by 2^bexp[box] and split, Kp FP16 per box.  out: ostride floats per box, of
+// which rows < M are written.
 template <int SLABS, int N>
-__device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CUtensorMap& map_lo, int texp, int Q,
-                                             int Qp, int mgroups, int nitems, const int4* __restrict__ tiles,
+__device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CUtensorMap& map_lo, int texp, int M,
+                                             int Kp, int ostride, int Mr, int mgroups, int nitems,
+                                             const int4* __restrict__ tiles,
                                              const int* __restrict__ pin, const int* __restrict__ pout,
                                              const int* __restrict__ bexp, const __half* __restrict__ in_hi,
                                              const __half* __restrict__ in_lo, float* __restrict__ out,
@@ -253,7 +256,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nst = (Qp + kKS - 1) / kKS;                     // stages per item (tail zero-filled)
+    const int nst = (Kp + kKS - 1) / kKS;                     // stages per item (tail zero-filled)
     const int nfg = (nst + kFoldStages - 1) / kFoldStages;   // accumulators per item
     volatile int* abort = &s_abort;
     auto stage_u32 = [&](int s) -> uint32_t { return smem_u32(base) + (uint32_t)(s * S::kStageBytes); };
@@ -290,7 +293,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
             bool ok = true;
             for (int k = 0; k < K && ok; ++k) {
                 const int w = (int)blockIdx.x + k * G;
-                const int arow = tiles[w / mgroups].x * Qp + (w % mgroups) * S::kRows;
+                const int arow = tiles[w / mgroups].x * Mr + (w % mgroups) * S::kRows;
                 for (int i = 0; i < nst; ++i, ++g) {
                     const int s = g % kStages;
                     if (g >= kStages && !mbar_wait_ab(&empty[s], (uint32_t)(((g / kStages) - 1) & 1), abort)) {
@@ -397,11 +400,11 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
                     break;
                 }
                 const uint32_t bh = stage_u32(s) + 2 * S::kABytes;
-                const int kk = i * kKS + 8 * c;          // an 8-group lies wholly inside or outside Qp
+                const int kk = i * kKS + 8 * c;          // an 8-group lies wholly inside or outside Kp
 #pragma unroll
                 for (int j = 0; j < S::kBRows; ++j) {
-                    const bool v = bi[j] >= 0 && kk < Qp;
-                    const size_t off = v ? (size_t)bi[j] * Qp + kk : 0;
+                    const bool v = bi[j] >= 0 && kk < Kp;
+                    const size_t off = v ? (size_t)bi[j] * Kp + kk : 0;
                     const uint32_t o = sw64_off(j * 16 + rr, c);
                     cp_async16(bh + o, in_hi + off, v ? 16u : 0u);
                     cp_async16(bh + S::kBBytes + o, in_lo + off, v ? 16u : 0u);
@@ -463,11 +466,11 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
             }
             if (bar_named_or(kFoldBar, kFoldThreads, !ok)) break;   // uniform across the fold warps
             const int row = (w % mgroups) * S::kRows + my_slab * 128 + quarter * 32 + lane;
-            if (row < Q) {
+            if (row < M) {
 #pragma unroll
                 for (int j = 0; j < 128; ++j) {
                     const int ob = s_out[my_col0 + j];
-                    if (ob >= 0) atomicAdd(out + (size_t)ob * Qp + row, acc[j] * s_oscale[my_col0 + j]);
+                    if (ob >= 0) atomicAdd(out + (size_t)ob * ostride + row, acc[j] * s_oscale[my_col0 + j]);
                 }
             }
             if (k + 1 < K) {
@@ -491,17 +494,18 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
 #define KF_TC_KERNEL(NAME)                                                                                      \
     template <int SLABS, int N>                                                                                 \
     __global__ void __launch_bounds__(kThreads, 1)                                                              \
-        NAME(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int Q,     \
-             int Qp, int mgroups, int nitems, const int4* __restrict__ tiles, const int* __restrict__ pin,      \
-             const int* __restrict__ pout, const int* __restrict__ bexp, int texp,                               \
+        NAME(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int M,     \
+             int Kp, int ostride, int Mr, int mgroups, int nitems, const int4* __restrict__ tiles,               \
+             const int* __restrict__ pin, const int* __restrict__ pout, const int* __restrict__ bexp, int texp,  \
              const __half* __restrict__ in_hi, const __half* __restrict__ in_lo, float* __restrict__ out,        \
              int* __restrict__ err) {                                                                            \
-        pair_tc_body<SLABS, N>(map_hi, map_lo, texp, Q, Qp, mgroups, nitems, tiles, pin, pout, bexp, in_hi,     \
-                               in_lo, out, err);                                                                 \
+        pair_tc_body<SLABS, N>(map_hi, map_lo, texp, M, Kp, ostride, Mr, mgroups, nitems, tiles, pin, pout,     \
+                               bexp, in_hi, in_lo, out, err);                                                    \
     }
 KF_TC_KERNEL(k_u2u_tc)
 KF_TC_KERNEL(k_m2l_tc)
 KF_TC_KERNEL(k_l2l_tc)
+KF_TC_KERNEL(k_proj_tc)
 #undef KF_TC_KERNEL
 
 }  // namespace tc

@@ -30,19 +30,24 @@ struct BieScratch {
 
 // Translation tables of one (device, order, cutoff, precision, ADL centring): shared by
 // every plan with that key, freed with the last of them.  FP64 form: m2m/m2l/l2l in
-// FP64.  Mixed form: FP16 hi/lo tables per family (0 M2M', 1 M2L', 2 L2L') scaled by
-// 2^texp, and their TMA tensor maps.
+// FP64, Qp x Qp each.  Mixed form: families 0 M2M' and 2 L2L' (Qp x Qp), 1 M2L' U_u
+// (Qp x Ku: M2L' factored through Pu's range, P = W U^T), 3 U_u^T and 4 U_d^T (the
+// projections onto the up and down check-space bases, K x Qp), as FP16 hi/lo tables
+// scaled by 2^texp, with their TMA tensor maps.  ru / rd: the ranks, Ku / Kd: rounded
+// up to 16.
+constexpr int kFamilies = 5;
 struct OpTables {
     int device = 0, p = 0;
     double cutoff = 0;
     bool fp64 = true, centered = false;
+    int ru = 0, rd = 0, Ku = 0, Kd = 0;
     DBuf<double> m2m_d, m2l_d, l2l_d;
-    DBuf<__half> tab_h[3], tab_l[3];
-    int texp[3] = {0, 0, 0};
-    CUtensorMap tmaps[3][2];
+    DBuf<__half> tab_h[kFamilies], tab_l[kFamilies];
+    int texp[kFamilies] = {0, 0, 0, 0, 0};
+    CUtensorMap tmaps[kFamilies][2];
     int64_t bytes() const {
         int64_t b = m2m_d.bytes() + m2l_d.bytes() + l2l_d.bytes();
-        for (int f = 0; f < 3; ++f) b += tab_h[f].bytes() + tab_l[f].bytes();
+        for (int f = 0; f < kFamilies; ++f) b += tab_h[f].bytes() + tab_l[f].bytes();
         return b;
     }
 };
@@ -75,6 +80,9 @@ struct Plan {
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
     PairTiles u2u, m2l, l2l;
+    PairTiles proj;                 // mixed: (box -> box) per level, for the projections
+    DBuf<float> zu, zd;             // mixed: projected check potentials, nbox x Ku / Kd
+    bool d2t_factored = false;      // mixed: D2T rows G W_d read zd (else G Pd read d)
     int max_trg_leaf = 0;
     int tile_cap = kPairTile;       // pairs per translation tile
     DBuf<int> err;                  // device error word (bounded waits that gave up)
