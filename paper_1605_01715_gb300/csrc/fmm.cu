@@ -656,14 +656,16 @@ int upload_tiles(PairTiles& pt, const std::vector<int4>& tiles, const std::vecto
 // Used for the adjoint double layer, whose targets see only gradients: the
 // constant part of a down-check potential is dropped before it is stored in the
 // working precision, so its rounding is relative to the potential's variation.
-// Mixed precision may also factor the D2T rows through Pd's range (G W_d reading
-// z_d = U_d^T d).  That halves the rows' HBM traffic but costs accuracy: z_d carries
-// the two-term FP16 error (about 2^-22 of the box's largest potential) where d carried
-// FP32 rounding, and G W_d amplifies it along the small singular directions of the
-// down check-to-equivalent operator.  Measured on the 1M-point cube and sphere at
-// p = 10 (8,192 sampled targets): 9.6e-7 / 1.01e-6 factored, 8.9e-7 / 8.8e-7 not; so
-// D2T keeps the Pd rows.
-constexpr bool kFactorD2T = false;
+// Mixed precision also factors the D2T rows through Pd's range: G W_d reading
+// z_d = U_d^T d, half the rows' HBM traffic.  The rows G W_d amplify an error in z_d
+// along the small singular directions of the down check-to-equivalent operator, so the
+// projection must be as accurate as d itself: with 64-column accumulators on the tensor
+// cores it was not (1M-point cube / sphere at p = 10, 8,192 sampled targets: 9.6e-7 /
+// 1.01e-6 factored vs 8.9e-7 / 8.8e-7 not; the same projection computed exactly gave
+// 8.9e-7 / 8.7e-7, and emulating the split operands alone changed nothing -- the
+// accumulator's truncation was the cause); with 32-column accumulators it is
+// (4.8e-7 / 5.8e-7).
+constexpr bool kFactorD2T = true;
 
 // Operators of Mr rows (Q of them valid) by Kc columns, op-major.
 template <typename Real>
