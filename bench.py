@@ -457,10 +457,12 @@ def roofline(phases, st, tst, args):
     mixed = args.precision == "mixed"
     if dom in ("m2l", "u2u", "l2l"):
         pairs = {"m2l": st["m2l_pairs"], "u2u": st["u2u_pairs"], "l2l": st["l2l_pairs"]}[dom]
-        # algorithmic: one Q x W operator per pair; W = Q, or for a factored M2L' the
-        # rank of Pu (the operator acts on the projections onto its range)
-        W = st["m2l_width"] if dom == "m2l" else Q
-        flops = 2.0 * Q * W * pairs
+        # algorithmic: one R x W operator per pair; R = W = Q in FP64; mixed, every
+        # translation acts between projections onto the pseudo-inverses' ranges (up
+        # basis: rank_up values, down basis: rank_down)
+        ru, rd = (st["rank_up"], st["rank_down"]) if mixed else (Q, Q)
+        R, W = {"m2l": (rd, ru), "u2u": (ru, ru), "l2l": (rd, rd)}[dom]
+        flops = 2.0 * R * W * pairs
         if mixed:                                   # two-term FP16 on tcgen05: 3 MMAs per product
             peak = pk["bf16_tflops"] / 3.0
             out = {"kernel": "k_%s_tc (tcgen05, two-term FP16)" % dom, "bound": "tensor",
@@ -472,7 +474,7 @@ def roofline(phases, st, tst, args):
         out.update({"achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "frac": flops / t / 1e12 / peak,
                     "traffic": _m2l_traffic(pairs) if (mixed and dom == "m2l") else None,
-                    "work": "2*Q*W flops x %d pairs, Q=%d, W=%d" % (pairs, Q, W)})
+                    "work": "2*R*W flops x %d pairs, R=%d, W=%d" % (pairs, R, W)})
         return out
     if dom == "p2p":
         flops = 20.0 * tst["p2p_pairs"]            # ~20 FP32 ops per pair (FMA counted as 2)

@@ -207,6 +207,8 @@ typedef struct {
     int32_t m2l_width;                /* columns of each M2L' operator as applied:
                                          q_points (FP64) or rank_up (mixed: M2L' acts
                                          on the projections onto Pu's range)          */
+    int32_t m2l_rows;                 /* its rows: q_points (FP64) or rank_down (mixed:
+                                         it yields the projection onto Pd's range)    */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);

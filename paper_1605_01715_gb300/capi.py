@@ -53,7 +53,8 @@ class PlanStats(ctypes.Structure):
                 ("u2u_pairs", ctypes.c_int64), ("l2l_pairs", ctypes.c_int64),
                 ("s2u_leaves", ctypes.c_int64), ("x_pairs", ctypes.c_int64),
                 ("launches_per_matvec", ctypes.c_int32), ("rank_up", ctypes.c_int32),
-                ("rank_down", ctypes.c_int32), ("m2l_width", ctypes.c_int32)]
+                ("rank_down", ctypes.c_int32), ("m2l_width", ctypes.c_int32),
+                ("m2l_rows", ctypes.c_int32)]
 
 
 def _as_dict(st):

@@ -656,16 +656,6 @@ int upload_tiles(PairTiles& pt, const std::vector<int4>& tiles, const std::vecto
 // Used for the adjoint double layer, whose targets see only gradients: the
 // constant part of a down-check potential is dropped before it is stored in the
 // working precision, so its rounding is relative to the potential's variation.
-// Mixed precision also factors the D2T rows through Pd's range: G W_d reading
-// z_d = U_d^T d, half the rows' HBM traffic.  The rows G W_d amplify an error in z_d
-// along the small singular directions of the down check-to-equivalent operator, so the
-// projection must be as accurate as d itself: with 64-column accumulators on the tensor
-// cores it was not (1M-point cube / sphere at p = 10, 8,192 sampled targets: 9.6e-7 /
-// 1.01e-6 factored vs 8.9e-7 / 8.8e-7 not; the same projection computed exactly gave
-// 8.9e-7 / 8.7e-7, and emulating the split operands alone changed nothing -- the
-// accumulator's truncation was the cause); with 32-column accumulators it is
-// (4.8e-7 / 5.8e-7).
-constexpr bool kFactorD2T = true;
 
 // Operators of Mr rows (Q of them valid) by Kc columns, op-major.
 template <typename Real>
@@ -684,50 +674,153 @@ __global__ void k_center_ops(const double* __restrict__ in, int Q, int Mr, int K
     for (int i = 0; i < Mr; ++i) O[(size_t)i * Kc + j] = i < Q ? (Real)(A[(size_t)i * Kc + j] - mean) : (Real)0;
 }
 
-// The three translation families, each operator K_o P: P the up (M2M', M2L') or down
-// (L2L') pseudo-inverse itself (Pu, Pd: Q x Q, stored Qp wide) or, for M2L' when
-// factored, the W factor of Pu's factored form (Wu: Q x ru, stored Ku wide).  Tables
-// are op-major, Qp rows each.
-template <typename Real>
-int build_ops(Plan& P, const HostPinv& h, bool factored, int Ku, Real* m2m, Real* m2l, Real* l2l,
-              cudaStream_t s) {
-    DBuf<double> dPu, dPd, dWu;
+// Rows K_o P of one translation family (0 M2M', 1 M2L', 2 L2L') for every operator o,
+// in FP64: P is Q x C (row-major), out is op-major with Qp rows (Q used) of Kc columns.
+int translation_ops(const Plan& P, const HostPinv& h, int which, int C, int Kc, const double* dP, double* out,
+                    cudaStream_t s) {
+    std::vector<double> apts, ascale, bpts;
+    std::vector<int> bset;
+    std::vector<int64_t> orow;
+    translation_rows(h, which, apts, bset, orow, ascale, bpts, P.Qp);
+    DBuf<double> da, dsc, db;
+    DBuf<int> dbs;
+    DBuf<int64_t> dor;
+    KF_TRY(da.upload(apts, s));
+    KF_TRY(dsc.upload(ascale, s));
+    KF_TRY(db.upload(bpts, s));
+    KF_TRY(dbs.upload(bset, s));
+    KF_TRY(dor.upload(orow, s));
+    RowSpec rs;
+    rs.nrows = (int)bset.size();
+    rs.apts = da.p;
+    rs.ascale = dsc.p;
+    rs.bset = dbs.p;
+    rs.orow = dor.p;
+    rs.bpts = db.p;
+    KF_TRY(build_rows<double>(rs, P.Q, C, Kc, dP, 0, out, s));
+    KF_CHECK_CUDA(cudaStreamSynchronize(s));   // the row descriptors are freed on return
+    return KIFMM_OK;
+}
+
+// The three translation families in FP64, each operator K_o P with P the up (M2M',
+// M2L') or down (L2L') pseudo-inverse (Q x Q, stored Qp wide); op-major, Qp x Qp each.
+int build_ops(Plan& P, const HostPinv& h, double* m2m, double* m2l, double* l2l, cudaStream_t s) {
+    DBuf<double> dPu, dPd;
     KF_TRY(dPu.upload(h.Pu, s));
     KF_TRY(dPd.upload(h.Pd, s));
-    if (factored) KF_TRY(dWu.upload(h.Wu, s));
-    Real* outs[3] = {m2m, m2l, l2l};
+    double* outs[3] = {m2m, m2l, l2l};
     const int nops[3] = {8, kNumOffsets, 8};
     for (int which = 0; which < 3; ++which) {
-        const bool f = factored && which == 1;
-        const int C = f ? h.ru : P.Q;
-        const int Kc = f ? Ku : P.Qp;
-        std::vector<double> apts, ascale, bpts;
-        std::vector<int> bset;
-        std::vector<int64_t> orow;
-        translation_rows(h, which, apts, bset, orow, ascale, bpts, P.Qp);
-        DBuf<double> da, dsc, db, tmp;
-        DBuf<int> dbs;
-        DBuf<int64_t> dor;
-        KF_TRY(da.upload(apts, s));
-        KF_TRY(dsc.upload(ascale, s));
-        KF_TRY(db.upload(bpts, s));
-        KF_TRY(dbs.upload(bset, s));
-        KF_TRY(dor.upload(orow, s));
-        RowSpec rs;
-        rs.nrows = (int)bset.size();
-        rs.apts = da.p;
-        rs.ascale = dsc.p;
-        rs.bset = dbs.p;
-        rs.orow = dor.p;
-        rs.bpts = db.p;
-        // build in FP64, then (ADL: M2L and L2L centred) round to the working precision
-        KF_TRY(tmp.alloc((size_t)nops[which] * P.Qp * Kc));
+        DBuf<double> tmp;
+        KF_TRY(tmp.alloc((size_t)nops[which] * P.Qp * P.Qp));
         KF_CHECK_CUDA(cudaMemsetAsync(tmp.p, 0, tmp.bytes(), s));
-        KF_TRY(build_rows<double>(rs, P.Q, C, Kc, which == 2 ? dPd.p : (f ? dWu.p : dPu.p), 0, tmp.p, s));
+        KF_TRY(translation_ops(P, h, which, P.Q, P.Qp, which == 2 ? dPd.p : dPu.p, tmp.p, s));
         bool center = P.kernel == KIFMM_KERNEL_ADL && which != 0;
-        dim3 grid(div_up(Kc, 128), nops[which]);
-        k_center_ops<Real><<<grid, 128, 0, s>>>(tmp.p, P.Q, P.Qp, Kc, center, outs[which]);
+        dim3 grid(div_up(P.Qp, 128), nops[which]);
+        k_center_ops<double><<<grid, 128, 0, s>>>(tmp.p, P.Q, P.Qp, P.Qp, center, outs[which]);
         KF_CHECK_LAUNCH();
+        KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    return KIFMM_OK;
+}
+
+// out[op] (Kr x Kc) = L (Kr x Q, row-major) . A[op] (Q of Mr rows x Kc), set-up only:
+// FP64 products, rounded once.  64 x 64 outputs per block, 4 x 4 per thread.
+__global__ void k_left_mul(const double* __restrict__ L, const double* __restrict__ A, int Q, int Mr, int Kr,
+                           int Kc, float* __restrict__ out) {
+    __shared__ double Ls[16][65];
+    __shared__ double As[16][65];
+    const int op = blockIdx.z, r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const double* Ao = A + (size_t)op * Mr * Kc;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < Q; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int r = e >> 4, k = e & 15;          // L: 16 neighbouring k of one row
+            Ls[k][r] = (r0 + r < Kr && k0 + k < Q) ? L[(size_t)(r0 + r) * Q + k0 + k] : 0.0;
+            const int kk = e >> 6, c = e & 63;          // A: 64 neighbouring columns of one row
+            As[kk][c] = (k0 + kk < Q && c0 + c < Kc) ? Ao[(size_t)(k0 + kk) * Kc + c0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += Ls[k][ty * 4 + i] * As[k][tx * 4 + j];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = r0 + ty * 4 + i, c = c0 + tx * 4 + j;
+            if (r < Kr && c < Kc) out[((size_t)op * Kr + r) * Kc + c] = (float)acc[i][j];
+        }
+}
+
+// Mixed-precision tables.  With P = W U^T (U: Q x r orthonormal, W = P U), every
+// check-space operator K P that is followed by another pseudo-inverse only through
+// its range can act between projections: a box's up-check potential enters as
+// U_u^T u (ru values), its down-check potential is kept as U_d^T d (rd values), and
+//   M2M'' = U_u^T (1/2 K_c W_u)    (Ku x Ku)
+//   M2L'' = U_d^T C K_o W_u        (Kd x Ku)
+//   L2L'' = U_d^T C K_c W_d        (Kd x Kd)
+// with C the row-mean removal for ADL (identity otherwise), plus the projections
+// U_u^T and U_d^T C of the leaves' and X-list boxes' full check potentials.  The
+// products are exact: U^T U = I, so the chain reproduces K P ... K P.  Built in FP64,
+// rounded once to FP32 (then split into two-term FP16 by the caller).
+int build_projected(Plan& P, const HostPinv& h, OpTables* t, DBuf<float>* f32, cudaStream_t s) {
+    const int Q = P.Q, Qp = P.Qp, Ku = t->Ku, Kd = t->Kd;
+    const bool adl = P.kernel == KIFMM_KERNEL_ADL;
+    std::vector<double> Lu((size_t)Ku * Q, 0.0), Ld((size_t)Kd * Q, 0.0);
+    for (int j = 0; j < h.ru; ++j)
+        for (int i = 0; i < Q; ++i) Lu[(size_t)j * Q + i] = h.Uu[(size_t)i * h.ru + j];
+    for (int j = 0; j < h.rd; ++j)
+        for (int i = 0; i < Q; ++i) Ld[(size_t)j * Q + i] = h.Ud[(size_t)i * h.rd + j];
+    DBuf<double> dLu, dLd, dWu, dWd;
+    KF_TRY(dLu.upload(Lu, s));
+    KF_TRY(dLd.upload(Ld, s));
+    KF_TRY(dWu.upload(h.Wu, s));
+    KF_TRY(dWd.upload(h.Wd, s));
+    const int nops[3] = {8, kNumOffsets, 8};
+    for (int which = 0; which < 3; ++which) {
+        const int C = which == 2 ? h.rd : h.ru, Kc = which == 2 ? Kd : Ku, Kr = which == 0 ? Ku : Kd;
+        DBuf<double> tmp, cen;
+        KF_TRY(tmp.alloc((size_t)nops[which] * Qp * Kc));
+        KF_CHECK_CUDA(cudaMemsetAsync(tmp.p, 0, tmp.bytes(), s));
+        KF_TRY(translation_ops(P, h, which, C, Kc, which == 2 ? dWd.p : dWu.p, tmp.p, s));
+        const double* A = tmp.p;
+        if (adl && which != 0) {
+            KF_TRY(cen.alloc(tmp.n));
+            dim3 grid(div_up(Kc, 128), nops[which]);
+            k_center_ops<double><<<grid, 128, 0, s>>>(tmp.p, Q, Qp, Kc, true, cen.p);
+            KF_CHECK_LAUNCH();
+            A = cen.p;
+        }
+        dim3 grid(div_up(Kc, 64), div_up(Kr, 64), nops[which]);
+        k_left_mul<<<grid, 256, 0, s>>>(which == 0 ? dLu.p : dLd.p, A, Q, Qp, Kr, Kc, f32[which].p);
+        KF_CHECK_LAUNCH();
+        KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    // projections U_u^T and U_d^T C, zero padded to K x Qp
+    for (int f = 3; f < kFamilies; ++f) {
+        const std::vector<double>& L = f == 3 ? Lu : Ld;
+        const int K = f == 3 ? Ku : Kd;
+        std::vector<float> ut((size_t)K * Qp, 0.f);
+        for (int j = 0; j < K; ++j) {
+            double mean = 0.0;
+            if (adl && f == 4) {
+                for (int i = 0; i < Q; ++i) mean += L[(size_t)j * Q + i];
+                mean /= Q;
+            }
+            for (int i = 0; i < Q; ++i) ut[(size_t)j * Qp + i] = (float)(L[(size_t)j * Q + i] - mean);
+        }
+        KF_CHECK_CUDA(cudaMemcpyAsync(f32[f].p, ut.data(), ut.size() * sizeof(float), cudaMemcpyHostToDevice, s));
         KF_CHECK_CUDA(cudaStreamSynchronize(s));
     }
     return KIFMM_OK;
@@ -813,33 +906,22 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
         KF_CHECK_CUDA(cudaMemsetAsync(t->l2l_d.p, 0, t->l2l_d.bytes(), s));
         t->ru = h.ru;
         t->rd = h.rd;
-        KF_TRY(build_ops<double>(P, h, false, 0, t->m2m_d.p, t->m2l_d.p, t->l2l_d.p, s));
+        KF_TRY(build_ops(P, h, t->m2m_d.p, t->m2l_d.p, t->l2l_d.p, s));
     } else {
-        // M2M' and L2L' square, M2L' factored through Pu's range (Qp x Ku), projections
-        // onto the up and down check-space bases (K x Qp); every table built in FP64 and
-        // rounded to two-term FP16
+        // translations between projections (see build_projected), two-term FP16
         t->ru = h.ru;
         t->rd = h.rd;
         t->Ku = (h.ru + 15) / 16 * 16;
         t->Kd = (h.rd + 15) / 16 * 16;
         DBuf<float> f32[kFamilies];
         const int nops[kFamilies] = {8, kNumOffsets, 8, 1, 1};
-        const int rows[kFamilies] = {P.Qp, P.Qp, P.Qp, t->Ku, t->Kd};
-        const int cols[kFamilies] = {P.Qp, t->Ku, P.Qp, P.Qp, P.Qp};
+        const int rows[kFamilies] = {t->Ku, t->Kd, t->Kd, t->Ku, t->Kd};
+        const int cols[kFamilies] = {t->Ku, t->Ku, t->Kd, P.Qp, P.Qp};
         for (int f = 0; f < kFamilies; ++f) {
             KF_TRY(f32[f].alloc((size_t)nops[f] * rows[f] * cols[f]));
             KF_CHECK_CUDA(cudaMemsetAsync(f32[f].p, 0, f32[f].bytes(), s));
         }
-        KF_TRY(build_ops<float>(P, h, true, t->Ku, f32[0].p, f32[1].p, f32[2].p, s));
-        for (int f = 3; f < kFamilies; ++f) {   // U^T, zero padded to K x Qp
-            const std::vector<double>& U = f == 3 ? h.Uu : h.Ud;
-            const int r = f == 3 ? h.ru : h.rd;
-            std::vector<float> ut((size_t)rows[f] * cols[f], 0.f);
-            for (int j = 0; j < r; ++j)
-                for (int i = 0; i < P.Q; ++i) ut[(size_t)j * cols[f] + i] = (float)U[(size_t)i * r + j];
-            KF_CHECK_CUDA(cudaMemcpyAsync(f32[f].p, ut.data(), ut.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-            KF_CHECK_CUDA(cudaStreamSynchronize(s));
-        }
+        KF_TRY(build_projected(P, h, t.get(), f32, s));
         for (int f = 0; f < kFamilies; ++f) {
             KF_TRY(t->tab_h[f].alloc(f32[f].n));
             KF_TRY(t->tab_l[f].alloc(f32[f].n));
@@ -860,8 +942,6 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     P.Q = h.Q;
     P.Qp = (h.Q + 15) / 16 * 16;
     P.fp64 = P.prec == KIFMM_PREC_FP64;
-    // mixed: tiles sized for the tensor-core GEMM; FP64: CUDA-core blocks of kPairTile
-    P.tile_cap = P.fp64 ? kPairTile : tc_tile_pairs(P.Qp);
     KF_TRY(P.err.alloc(1));
     KF_CHECK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), s));
 
@@ -889,6 +969,10 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
 
     // operators: shared tables of this key, built once
     KF_TRY(get_tables(P, h, s));
+    // mixed: tiles sized for the tensor-core GEMM of each family's row count; FP64:
+    // CUDA-core blocks of kPairTile
+    const int cap_up = P.fp64 ? kPairTile : tc_tile_pairs(P.ops->Ku);
+    const int cap_dn = P.fp64 ? kPairTile : tc_tile_pairs(P.ops->Kd);
     if (!P.fp64) {
         KF_TRY(P.bexp.alloc(T.nbox));
         KF_TRY(P.vin_h.alloc((size_t)T.nbox * P.Qp));
@@ -954,7 +1038,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                         if (c >= 0 && has_src(T, c)) tr.push_back({o, c, b});
                     }
                 }
-                make_tiles(tr, tiles, pin, pout, P.tile_cap);
+                make_tiles(tr, tiles, pin, pout, cap_up);
             }
         }
         P.u2u.level_tile[T.nlev] = (int)tiles.size();
@@ -973,7 +1057,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                     oz = T.h_coord[3 * a + 2] - T.h_coord[3 * b + 2];
                 tr.push_back({(ox + 3) * 49 + (oy + 3) * 7 + (oz + 3), a, b});
             }
-        make_tiles(tr, tiles, pin, pout, P.tile_cap);
+        make_tiles(tr, tiles, pin, pout, cap_dn);
         KF_TRY(upload_tiles(P.m2l, tiles, pin, pout, s));
     }
     // L2L: per child level >= 3, (parent -> child) grouped by the child's octant
@@ -987,29 +1071,26 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                 std::vector<Triple> tr;
                 for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b)
                     if (has_trg(T, b)) tr.push_back({octant_of(T, b), T.h_parent[b], b});
-                make_tiles(tr, tiles, pin, pout, P.tile_cap);
+                make_tiles(tr, tiles, pin, pout, cap_dn);
             }
         }
         P.l2l.level_tile[T.nlev] = (int)tiles.size();
         KF_TRY(upload_tiles(P.l2l, tiles, pin, pout, s));
     }
-    // mixed: projections of every box of a level onto the check-space bases, one
-    // (box -> box) tile list per level
+    // mixed: projections of the S2U leaves' up-check potentials and of the X-list
+    // boxes' down-check potentials (one (box -> box) tile list each), and the
+    // projected potentials of every box
     if (!P.fp64) {
-        std::vector<int4> tiles;
-        std::vector<int> pin, pout;
-        P.proj.level_tile.assign(T.nlev + 1, 0);
-        for (int l = 0; l < T.nlev; ++l) {
-            P.proj.level_tile[l] = (int)tiles.size();
+        for (int up = 1; up >= 0; --up) {
+            std::vector<int4> tiles;
+            std::vector<int> pin, pout;
             std::vector<Triple> tr;
-            for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b) tr.push_back({0, b, b});
-            make_tiles(tr, tiles, pin, pout, tc_tile_pairs(P.ops->Ku));
+            for (int b : up ? s2u_box : p2l_box) tr.push_back({0, b, b});
+            make_tiles(tr, tiles, pin, pout, up ? cap_up : cap_dn);
+            KF_TRY(upload_tiles(up ? P.proj_up : P.proj_x, tiles, pin, pout, s));
         }
-        P.proj.level_tile[T.nlev] = (int)tiles.size();
-        KF_TRY(upload_tiles(P.proj, tiles, pin, pout, s));
         KF_TRY(P.zu.alloc((size_t)T.nbox * P.ops->Ku));
-        P.d2t_factored = kFactorD2T;
-        if (P.d2t_factored) KF_TRY(P.zd.alloc((size_t)T.nbox * P.ops->Kd));
+        KF_TRY(P.zd.alloc((size_t)T.nbox * P.ops->Kd));
     }
 
     // per-target evaluation rows and buffers
@@ -1022,9 +1103,9 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_TRY(P.res_d.alloc(T.nt));
         KF_TRY(P.q_d.alloc(3 * T.ns));
     } else {
-        const int w = P.d2t_factored ? P.ops->Kd : P.Qp;
-        KF_TRY(P.d2t_f.alloc((size_t)T.nt * w));
-        KF_TRY(build_d2t<float>(P, h, P.d2t_factored, P.ops->Kd, tleaf_of, P.d2t_f.p, s));
+        // rows G W_d, reading the projected down-check potentials
+        KF_TRY(P.d2t_f.alloc((size_t)T.nt * P.ops->Kd));
+        KF_TRY(build_d2t<float>(P, h, true, P.ops->Kd, tleaf_of, P.d2t_f.p, s));
         KF_TRY(P.u_f.alloc(nbq));
         KF_TRY(P.d_f.alloc(nbq));
         KF_TRY(P.res_f.alloc(T.nt));
@@ -1054,39 +1135,39 @@ template <typename Real>
 int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const Real* ops, const Real* in,
               Real* out, int b0, int b1, cudaStream_t s, int& launches);
 
-// Mixed precision: two-term FP16 on the tensor cores (tcgen05).  M2L' is factored
-// through Pu's range: a source's up-check potential u (Qp per box) enters as its
-// projection z = U_u^T u (Ku per box; ru, the rank of Pu, is about Q/2 at p = 10), and
-// M2L' u = (M2L' U_u) z exactly, since M2L' = K Pu = K W_u U_u^T.  Likewise the D2T rows
-// are G W_d and read z_d = U_d^T d.  Every box of levels >= 2 is projected once, after
-// the upward (resp. downward) pass; U2U and L2L keep their square tables.  The input
-// vectors of a launch (boxes [b0, b1)) are scaled and split first.
-
-int project_levels(const Plan& P, int fam, int l0, const float* v, float* z, cudaStream_t s, int& launches) {
-    const Tree& T = P.tree->t;
-    if (l0 < 0 || l0 >= T.nlev) return KIFMM_OK;
-    const int t0 = P.proj.level_tile[l0], t1 = P.proj.level_tile[T.nlev];
-    if (t1 <= t0) return KIFMM_OK;
-    const int K = fam == 3 ? P.ops->Ku : P.ops->Kd, r = fam == 3 ? P.ops->ru : P.ops->rd;
-    KF_TRY(tc_box_split(v, P.Q, P.Qp, T.level_off[l0], T.nbox, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
-    const CUtensorMap* m = P.ops->tmaps[fam];
-    KF_TRY(launch_pair_tc(3, m[0], m[1], P.ops->texp[fam], r, K, P.Qp, K, P.proj.tiles.p + t0, t1 - t0,
-                          P.proj.pin.p, P.proj.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, z, P.err.p, s));
-    launches += 2;
-    return KIFMM_OK;
-}
-
+// Mixed precision: two-term FP16 on the tensor cores (tcgen05), every translation
+// between projected check potentials (see build_projected): U2U in the up basis (ru of
+// Ku per box), M2L from the up to the down basis, L2L in the down basis (rd of Kd).
+// The input vectors of a launch (boxes [b0, b1)) are scaled and split first.
 template <>
 int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const float* ops,
                      const float* z, float* out, int b0, int b1, cudaStream_t s, int& launches) {
     if (t1 <= t0) return KIFMM_OK;
     (void)ops;  // the tensor-core path reads the split tables through their TMA maps
-    // M2L reads projections (ru of Ku per box), U2U and L2L check potentials (Q of Qp)
-    const int K = which == 1 ? P.ops->Ku : P.Qp, r = which == 1 ? P.ops->ru : P.Q;
+    const OpTables& o = *P.ops;
+    const bool in_up = which != kL2L, out_up = which == kU2U;
+    const int K = in_up ? o.Ku : o.Kd, r = in_up ? o.ru : o.rd;
+    const int Mr = out_up ? o.Ku : o.Kd, M = out_up ? o.ru : o.rd;
     KF_TRY(tc_box_split(z, r, K, b0, b1, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
-    const CUtensorMap* m = P.ops->tmaps[which];
-    KF_TRY(launch_pair_tc(which, m[0], m[1], P.ops->texp[which], P.Q, P.Qp, K, P.Qp, pt.tiles.p + t0, t1 - t0,
-                          pt.pin.p, pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, out, P.err.p, s));
+    const CUtensorMap* m = o.tmaps[which];
+    KF_TRY(launch_pair_tc(which, m[0], m[1], o.texp[which], M, Mr, K, Mr, pt.tiles.p + t0, t1 - t0, pt.pin.p,
+                          pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, out, P.err.p, s));
+    launches += 2;
+    return KIFMM_OK;
+}
+
+// Mixed: projection of full check potentials v (Q of Qp per box) of the boxes in pt's
+// tiles onto the up (fam 3) or down (fam 4) basis, added into z.
+int project(const Plan& P, int fam, const PairTiles& pt, const float* v, float* z, cudaStream_t s,
+            int& launches) {
+    const Tree& T = P.tree->t;
+    if (pt.ntiles == 0) return KIFMM_OK;
+    const OpTables& o = *P.ops;
+    const int Mr = fam == 3 ? o.Ku : o.Kd, M = fam == 3 ? o.ru : o.rd;
+    KF_TRY(tc_box_split(v, P.Q, P.Qp, 0, T.nbox, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
+    const CUtensorMap* m = o.tmaps[fam];
+    KF_TRY(launch_pair_tc(3, m[0], m[1], o.texp[fam], M, Mr, P.Qp, Mr, pt.tiles.p, pt.ntiles, pt.pin.p,
+                          pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, z, P.err.p, s));
     launches += 2;
     return KIFMM_OK;
 }
@@ -1131,18 +1212,20 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_CHECK_CUDA(cudaMemsetAsync(B.u, 0, nbq * sizeof(Real), s));
     KF_CHECK_CUDA(cudaMemsetAsync(B.d, 0, nbq * sizeof(Real), s));
     launches += 3;
+    // the vectors the translations act on: check potentials (FP64) or, mixed, their
+    // projections (zu, zd); mixed S2U and X write full potentials into B.u / B.d,
+    // which are projected before they are translated
     constexpr bool mixed = std::is_same<Real, float>::value;
-    float* zu = nullptr;
-    float* zd = nullptr;
+    Real* up = B.u;
+    Real* dn = B.d;
+    int dw = P.Qp;
     if constexpr (mixed) {
-        zu = P.zu.p;
-        zd = P.zd.p;
-        KF_CHECK_CUDA(cudaMemsetAsync(zu, 0, P.zu.bytes(), s));
-        ++launches;
-        if (P.d2t_factored) {
-            KF_CHECK_CUDA(cudaMemsetAsync(zd, 0, P.zd.bytes(), s));
-            ++launches;
-        }
+        up = P.zu.p;
+        dn = P.zd.p;
+        dw = P.ops->Kd;
+        KF_CHECK_CUDA(cudaMemsetAsync(up, 0, P.zu.bytes(), s));
+        KF_CHECK_CUDA(cudaMemsetAsync(dn, 0, P.zd.bytes(), s));
+        launches += 2;
     }
     KF_TRY(mark(1));
     // S2U
@@ -1152,34 +1235,31 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         ++launches;
     }
     KF_TRY(mark(2));
-    // U2U, deepest parents first; mixed: then every box's projection for M2L
+    // mixed: the leaves' projections; U2U, deepest parents first
+    if constexpr (mixed) KF_TRY(project(P, 3, P.proj_up, B.u, up, s, launches));
     for (int l = T.nlev - 1; l >= 2; --l)
-        KF_TRY(run_pairs<Real>(P, kU2U, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, B.u, B.u,
+        KF_TRY(run_pairs<Real>(P, kU2U, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, up, up,
                                T.level_off[std::min(l + 1, T.nlev)], T.level_off[std::min(l + 2, T.nlev)], s,
                                launches));
-    if constexpr (mixed) KF_TRY(project_levels(P, 3, 2, B.u, zu, s, launches));
     KF_TRY(mark(3));
-    // X list, then V list
+    // X list (mixed: then the X boxes' projections), then V list
     if (P.n_p2l) {
         KF_TRY(launch_surf<Real>(P, T, dl, P.n_p2l, P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, kDnCheck, B.q, B.surf,
                                  B.d, s));
         ++launches;
+        if constexpr (mixed) KF_TRY(project(P, 4, P.proj_x, B.d, dn, s, launches));
     }
     KF_TRY(mark(4));
-    if constexpr (mixed)
-        KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, zu, B.d, T.level_off[std::min(2, T.nlev)],
-                               T.nbox, s, launches));
-    else
-        KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, B.u, B.d, T.level_off[std::min(2, T.nlev)],
-                               T.nbox, s, launches));
+    KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, up, dn, T.level_off[std::min(2, T.nlev)],
+                           T.nbox, s, launches));
     KF_TRY(mark(5));
-    // L2L, coarsest children first (ADL: each level's potentials shifted to zero mean first)
-    const bool center = P.kernel == KIFMM_KERNEL_ADL;
+    // L2L, coarsest children first (ADL in FP64: each level's potentials shifted to zero
+    // mean first; the mixed tables carry that centring)
+    const bool center = !mixed && P.kernel == KIFMM_KERNEL_ADL;
     for (int l = 2; l < T.nlev; ++l) {
         if (l >= 3)
-            KF_TRY(run_pairs<Real>(P, kL2L, P.l2l, P.l2l.level_tile[l], P.l2l.level_tile[l + 1], B.l2l, B.d, B.d,
-                                   T.level_off[l - 1], T.level_off[l], s,
-                                   launches));
+            KF_TRY(run_pairs<Real>(P, kL2L, P.l2l, P.l2l.level_tile[l], P.l2l.level_tile[l + 1], B.l2l, dn, dn,
+                                   T.level_off[l - 1], T.level_off[l], s, launches));
         int nl = T.level_off[l + 1] - T.level_off[l];
         if (center && nl > 0) {
             k_center<Real><<<nl, 128, 0, s>>>(T.level_off[l], P.Q, P.Qp, B.d);
@@ -1187,18 +1267,9 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
             ++launches;
         }
     }
-    if constexpr (mixed)
-        if (P.d2t_factored) KF_TRY(project_levels(P, 4, 2, B.d, zd, s, launches));
     KF_TRY(mark(6));
     if (P.n_tleaf) {
-        const Real* dv = B.d;   // the down-check potentials or, factored, their projections
-        int dw = P.Qp;
-        if constexpr (mixed)
-            if (P.d2t_factored) {
-                dv = zd;
-                dw = P.ops->Kd;
-            }
-        k_d2t<Real><<<P.n_tleaf, 128, dw * sizeof(Real), s>>>(P.tleaf.p, T.rng.p, B.d2t, dv, dw, B.res);
+        k_d2t<Real><<<P.n_tleaf, 128, dw * sizeof(Real), s>>>(P.tleaf.p, T.rng.p, B.d2t, dn, dw, B.res);
         KF_CHECK_LAUNCH();
         ++launches;
     }
@@ -1363,6 +1434,7 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->rank_up = P.ops ? P.ops->ru : 0;
     st->rank_down = P.ops ? P.ops->rd : 0;
     st->m2l_width = P.fp64 ? P.Q : st->rank_up;
+    st->m2l_rows = P.fp64 ? P.Q : st->rank_down;
     return KIFMM_OK;
 }
 

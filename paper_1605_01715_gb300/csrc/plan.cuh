@@ -30,11 +30,12 @@ struct BieScratch {
 
 // Translation tables of one (device, order, cutoff, precision, ADL centring): shared by
 // every plan with that key, freed with the last of them.  FP64 form: m2m/m2l/l2l in
-// FP64, Qp x Qp each.  Mixed form: families 0 M2M' and 2 L2L' (Qp x Qp), 1 M2L' U_u
-// (Qp x Ku: M2L' factored through Pu's range, P = W U^T), 3 U_u^T and 4 U_d^T (the
-// projections onto the up and down check-space bases, K x Qp), as FP16 hi/lo tables
-// scaled by 2^texp, with their TMA tensor maps.  ru / rd: the ranks, Ku / Kd: rounded
-// up to 16.
+// FP64, Qp x Qp each.  Mixed form: every translation acts between projections onto
+// the ranges of the pseudo-inverses (P = W U^T, U orthonormal): families 0 M2M''
+// = U_u^T M2M' W_u (Ku x Ku), 1 M2L'' = U_d^T M2L' W_u (Kd x Ku), 2 L2L'' = U_d^T
+// L2L' W_d (Kd x Kd), and the projections 3 U_u^T and 4 U_d^T (K x Qp), as FP16 hi/lo
+// tables scaled by 2^texp, with their TMA tensor maps.  ru / rd: the ranks, Ku / Kd:
+// rounded up to 16.
 constexpr int kFamilies = 5;
 struct OpTables {
     int device = 0, p = 0;
@@ -80,9 +81,9 @@ struct Plan {
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
     PairTiles u2u, m2l, l2l;
-    PairTiles proj;                 // mixed: (box -> box) per level, for the projections
+    PairTiles proj_up, proj_x;      // mixed: (box -> box) projections of the S2U leaves'
+                                    // up-check and the X-list boxes' down-check potentials
     DBuf<float> zu, zd;             // mixed: projected check potentials, nbox x Ku / Kd
-    bool d2t_factored = false;      // mixed: D2T rows G W_d read zd (else G Pd read d)
     int max_trg_leaf = 0;
     int tile_cap = kPairTile;       // pairs per translation tile
     DBuf<int> err;                  // device error word (bounded waits that gave up)

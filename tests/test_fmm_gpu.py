@@ -107,8 +107,9 @@ def test_mixed_orders(p, tol):
 
 
 def test_factored_m2l_widths():
-    """The mixed form applies M2L' to projections onto Pu's range (width = its rank,
-    below Q and the same for every plan at one order); FP64 applies the Q x Q form."""
+    """The mixed form applies M2L' between projections (from Pu's range, width = its
+    rank, to Pd's range, rows = its rank; both below Q and the same for every plan at
+    one order); FP64 applies the Q x Q form."""
     from paper_1605_01715_gb300 import Plan, Tree
     m, h, (xyz, w, nrm), sig, refs = case("sphere")
     tree = Tree(xyz, max_leaf=40)
@@ -117,8 +118,8 @@ def test_factored_m2l_widths():
         mx = Plan(tree, kernel="dl", p=p, precision="mixed", src_nrm=nrm, pinv_cutoff=1e-8).stats()
         fp = Plan(tree, kernel="dl", p=p, precision="fp64", src_nrm=nrm, pinv_cutoff=1e-8).stats()
         assert 0 < mx["rank_up"] < Q and 0 < mx["rank_down"] < Q
-        assert mx["m2l_width"] == mx["rank_up"]
-        assert fp["m2l_width"] == Q
+        assert (mx["m2l_width"], mx["m2l_rows"]) == (mx["rank_up"], mx["rank_down"])
+        assert (fp["m2l_width"], fp["m2l_rows"]) == (Q, Q)
         assert (fp["rank_up"], fp["rank_down"]) == (mx["rank_up"], mx["rank_down"])
 
 
