@@ -130,71 +130,126 @@ k_src2surf(const int* __restrict__ boxes, const int* __restrict__ off, const int
     }
 }
 
-// FP32 form: each thread owns exactly PER = ceil(Q / kSurfThreads) surface points (no
-// per-point branch); staged sources are float4 -- (x, y, z, q), and (q n_j) over two
-// float4 for dipoles -- built from FP32 hi/lo coordinates relative to the box centre,
-// so one broadcast load feeds PER evaluations.
-template <bool DIPOLE, int PER>
+// FP32 form.  Each thread owns 2 NP surface points (points threadIdx.x + i kSurfThreads)
+// as NP packed pairs: every step is one FP32x2 instruction for two points (the same
+// round-to-nearest operations as the scalar form).  Staged sources are float4 --
+// (x, y, z, q), and (q n_j) over two float4 for dipoles -- built from FP32 hi/lo
+// coordinates relative to the box centre, so one broadcast load feeds 2 NP
+// evaluations.  Box centres (hi/lo), half-widths and check radii come as FP32 from a
+// per-box table (bcf: 3 float4 per box).  The tolerance-radius test is dropped for a
+// source box whose cube is provably farther than 2 delta from the check surface in
+// the max-norm (outside the surface's cube, or inside it).
+template <bool NEAR, bool DIPOLE, int NP>
+__device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const float4* __restrict__ sd, int cnt,
+                                           const float2* px, const float2* py, const float2* pz, float2* acc) {
+    const float d2 = (float)(kDelta * kDelta);
+#pragma unroll 2
+    for (int jj = 0; jj < cnt; ++jj) {
+        const float4 y = sp[jj];
+        const float2 nx = make_float2(-y.x, -y.x), ny = make_float2(-y.y, -y.y), nz = make_float2(-y.z, -y.z);
+        float2 qa = make_float2(y.w, y.w), qb, qc;
+        if (DIPOLE) {
+            const float4 dq = sd[jj];
+            qb = make_float2(dq.x, dq.x);
+            qc = make_float2(dq.y, dq.y);
+        }
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            const float2 dx = __fadd2_rn(px[m], nx), dy = __fadd2_rn(py[m], ny), dz = __fadd2_rn(pz[m], nz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            float2 v;
+            if (DIPOLE) {
+                const float2 num = __ffma2_rn(qc, dz, __ffma2_rn(qb, dy, __fmul2_rn(qa, dx)));
+                v = __fmul2_rn(num, __fmul2_rn(__fmul2_rn(inv, inv), inv));
+            } else {
+                v = __fmul2_rn(qa, inv);
+            }
+            if (NEAR) {
+                v.x = r2.x >= d2 ? v.x : 0.f;
+                v.y = r2.y >= d2 ? v.y : 0.f;
+            }
+            acc[m] = __fadd2_rn(acc[m], v);
+        }
+    }
+}
+
+template <bool DIPOLE, int NP>
 __global__ void __launch_bounds__(kSurfThreads)
-k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx, double radius,
-         const int* __restrict__ lvl, const double* __restrict__ ctr, double root_h,
-         const int64_t* __restrict__ rng, const float* __restrict__ sxf, int64_t ns, const float* __restrict__ qs,
-         const float* __restrict__ surf, int Q, int Qp, float* __restrict__ outbuf) {
+k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx, int down,
+         const float4* __restrict__ bcf, const int64_t* __restrict__ rng, const float* __restrict__ sxf, int64_t ns,
+         const float* __restrict__ qs, const float* __restrict__ surf, int Q, int Qp, float* __restrict__ outbuf) {
     __shared__ float4 sp[kSurfThreads];
     __shared__ float4 sd[DIPOLE ? kSurfThreads : 1];
     const int b = boxes[blockIdx.x];
-    const double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
-    const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
-    const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
-    const float rf = (float)(radius * ldexp(root_h, -lvl[b]));
-    float px[PER], py[PER], pz[PER], acc[PER];
+    const float4 bh = bcf[3 * b], bl = bcf[3 * b + 1], br = bcf[3 * b + 2];
+    const float rf = down ? br.y : br.x;
+    float2 px[NP], py[NP], pz[NP], acc[NP];
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int k = threadIdx.x + i * kSurfThreads;
-        const int kk = k < Q ? k : 0;
-        px[i] = rf * surf[3 * kk];
-        py[i] = rf * surf[3 * kk + 1];
-        pz[i] = rf * surf[3 * kk + 2];
-        acc[i] = 0.f;
+    for (int m = 0; m < NP; ++m) {
+        float c[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = threadIdx.x + (2 * m + h) * kSurfThreads;
+            const int kk = k < Q ? k : 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) c[h][d] = rf * surf[3 * kk + d];
+        }
+        px[m] = make_float2(c[0][0], c[1][0]);
+        py[m] = make_float2(c[0][1], c[1][1]);
+        pz[m] = make_float2(c[0][2], c[1][2]);
+        acc[m] = make_float2(0.f, 0.f);
     }
-    const float d2 = (float)(kDelta * kDelta);
+    const float margin = (float)(2.0 * kDelta);
     for (int e = off[blockIdx.x]; e < off[blockIdx.x + 1]; ++e) {
         const int a = idx[e];
         const int64_t sb = rng[4 * a], se = rng[4 * a + 1];
+        // max-norm separation between the source cube and the check surface
+        const float4 ah = bcf[3 * a], al = bcf[3 * a + 1];
+        const float dm = fmaxf(fabsf((ah.x - bh.x) + (al.x - bl.x)),
+                               fmaxf(fabsf((ah.y - bh.y) + (al.y - bl.y)), fabsf((ah.z - bh.z) + (al.z - bl.z))));
+        const bool near = fmaxf(dm - ah.w - rf, rf - dm - ah.w) <= margin;
         for (int64_t j0 = sb; j0 < se; j0 += kSurfThreads) {
             const int64_t j = j0 + threadIdx.x;
             if (j < se) {
-                sp[threadIdx.x] = make_float4((sxf[j] - chx) + (sxf[3 * ns + j] - clx),
-                                              (sxf[ns + j] - chy) + (sxf[4 * ns + j] - cly),
-                                              (sxf[2 * ns + j] - chz) + (sxf[5 * ns + j] - clz), qs[j]);
+                sp[threadIdx.x] = make_float4((sxf[j] - bh.x) + (sxf[3 * ns + j] - bl.x),
+                                              (sxf[ns + j] - bh.y) + (sxf[4 * ns + j] - bl.y),
+                                              (sxf[2 * ns + j] - bh.z) + (sxf[5 * ns + j] - bl.z), qs[j]);
                 if (DIPOLE) sd[threadIdx.x] = make_float4(qs[ns + j], qs[2 * ns + j], 0.f, 0.f);
             }
             __syncthreads();
             const int cnt = (int)((se - j0) < (int64_t)kSurfThreads ? (se - j0) : (int64_t)kSurfThreads);
-#pragma unroll 2
-            for (int jj = 0; jj < cnt; ++jj) {
-                const float4 y = sp[jj];
-                float4 dq = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (DIPOLE) dq = sd[jj];
-#pragma unroll
-                for (int i = 0; i < PER; ++i) {
-                    const float dx = px[i] - y.x, dy = py[i] - y.y, dz = pz[i] - y.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float inv = rsqrtf(r2);
-                    float v;
-                    if (DIPOLE) v = (y.w * dx + dq.x * dy + dq.y * dz) * (inv * inv * inv);
-                    else v = y.w * inv;
-                    acc[i] += (r2 >= d2) ? v : 0.f;
-                }
-            }
+            if (near)
+                surf_pairs<true, DIPOLE, NP>(sp, sd, cnt, px, py, pz, acc);
+            else
+                surf_pairs<false, DIPOLE, NP>(sp, sd, cnt, px, py, pz, acc);
             __syncthreads();
         }
     }
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int k = threadIdx.x + i * kSurfThreads;
-        if (k < Q) outbuf[(size_t)b * Qp + k] += acc[i];
+    for (int m = 0; m < NP; ++m) {
+        const int k0 = threadIdx.x + 2 * m * kSurfThreads, k1 = k0 + kSurfThreads;
+        if (k0 < Q) outbuf[(size_t)b * Qp + k0] += acc[m].x;
+        if (k1 < Q) outbuf[(size_t)b * Qp + k1] += acc[m].y;
     }
+}
+
+// Per-box FP32 table of the surface kernel: {centre hi, half-width}, {centre lo, 0},
+// {up-check radius, down-check radius, 0, 0}, each rounded once from FP64.
+__global__ void k_box_f(const double* __restrict__ ctr, const int* __restrict__ lvl, double root_h, int nbox,
+                        float4* __restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const double h = ldexp(root_h, -lvl[b]);
+    float hi[3], lo[3];
+    for (int d = 0; d < 3; ++d) {
+        const double c = ctr[3 * b + d];
+        hi[d] = (float)c;
+        lo[d] = (float)(c - (double)hi[d]);
+    }
+    out[3 * b] = make_float4(hi[0], hi[1], hi[2], (float)h);
+    out[3 * b + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    out[3 * b + 2] = make_float4((float)(kUpCheck * h), (float)(kDnCheck * h), 0.f, 0.f);
 }
 
 // Sources -> check surfaces of a CSR list of boxes (S2U: leaves and themselves; X list:
@@ -204,18 +259,19 @@ int launch_surf(const Plan& P, const Tree& T, bool dl, int nbox, const int* boxe
                 double radius, const Real* q, const Real* surf, Real* out, cudaStream_t s) {
     if (nbox <= 0) return KIFMM_OK;
     if constexpr (std::is_same<Real, float>::value) {
-        const int per = (P.Q + kSurfThreads - 1) / kSurfThreads;
-        switch (per * 2 + (dl ? 1 : 0)) {
-#define KF_SURF(PER)                                                                                             \
-    case 2 * PER:                                                                                                \
-        k_surf_f<false, PER><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, radius, T.lvl.p, T.ctr.p, T.root_h, \
-                                                           T.rng.p, P.sxf.p, T.ns, q, surf, P.Q, P.Qp, out);    \
+        const int np = (P.Q + 2 * kSurfThreads - 1) / (2 * kSurfThreads);
+        const int down = radius == kDnCheck ? 1 : 0;
+        switch (np * 2 + (dl ? 1 : 0)) {
+#define KF_SURF(NP)                                                                                              \
+    case 2 * NP:                                                                                                 \
+        k_surf_f<false, NP><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, \
+                                                          q, surf, P.Q, P.Qp, out);                             \
         break;                                                                                                   \
-    case 2 * PER + 1:                                                                                            \
-        k_surf_f<true, PER><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, radius, T.lvl.p, T.ctr.p, T.root_h,  \
-                                                          T.rng.p, P.sxf.p, T.ns, q, surf, P.Q, P.Qp, out);     \
+    case 2 * NP + 1:                                                                                             \
+        k_surf_f<true, NP><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns,  \
+                                                         q, surf, P.Q, P.Qp, out);                              \
         break;
-            KF_SURF(1) KF_SURF(2) KF_SURF(3) KF_SURF(4) KF_SURF(5) KF_SURF(6) KF_SURF(7) KF_SURF(8)
+            KF_SURF(1) KF_SURF(2) KF_SURF(3) KF_SURF(4)
 #undef KF_SURF
             default:
                 set_error("check surface of %d points exceeds the FP32 surface kernel", P.Q);
@@ -438,7 +494,9 @@ __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ of
 // one shared-memory broadcast load feeds T pair evaluations.  Source positions come as
 // FP32 hi/lo pairs (split once per plan) and the offset from the leaf centre is formed
 // from them in FP32, to within 2 ulp of that offset, with no FP64 arithmetic per pair or
-// per staged source.
+// per staged source.  A lane's targets are packed in pairs (the last pair of an odd
+// count repeats a target and drops it), so each step is one FP32x2 instruction for two
+// pair evaluations, with the scalar form's round-to-nearest operations.
 constexpr int kP2PWarps = 8;
 
 template <int KIND, int T>
@@ -450,20 +508,33 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const int* __
                                          const float* __restrict__ res, const int64_t* __restrict__ tperm,
                                          double* __restrict__ out, int64_t t0, int64_t te, float4* st) {
     const int g = lane >> 3, r = lane & 7;
-    float tx[T], ty[T], tz[T], acc[T], nx[T], ny[T], nz[T];
+    constexpr int TP = (T + 1) / 2;
+    float2 tx[TP], ty[TP], tz[TP], acc[TP], nx[TP], ny[TP], nz[TP];
 #pragma unroll
-    for (int i = 0; i < T; ++i) {
-        int64_t t = t0 + 8 * i + r;
-        t = t < te ? t : t0;                      // padding slots evaluate a real target, unused
-        tx[i] = (float)(txyz[t] - cx);
-        ty[i] = (float)(txyz[nt + t] - cy);
-        tz[i] = (float)(txyz[2 * nt + t] - cz);
-        if (KIND == 2) {
-            nx[i] = tnrm[t];
-            ny[i] = tnrm[nt + t];
-            nz[i] = tnrm[2 * nt + t];
+    for (int m = 0; m < TP; ++m) {
+        float c[2][6];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int64_t t = t0 + 8 * (2 * m + h) + r;
+            t = t < te ? t : t0;                  // padding slots evaluate a real target, unused
+            c[h][0] = (float)(txyz[t] - cx);
+            c[h][1] = (float)(txyz[nt + t] - cy);
+            c[h][2] = (float)(txyz[2 * nt + t] - cz);
+            if (KIND == 2) {
+                c[h][3] = tnrm[t];
+                c[h][4] = tnrm[nt + t];
+                c[h][5] = tnrm[2 * nt + t];
+            }
         }
-        acc[i] = 0.f;
+        tx[m] = make_float2(c[0][0], c[1][0]);
+        ty[m] = make_float2(c[0][1], c[1][1]);
+        tz[m] = make_float2(c[0][2], c[1][2]);
+        if (KIND == 2) {
+            nx[m] = make_float2(c[0][3], c[1][3]);
+            ny[m] = make_float2(c[0][4], c[1][4]);
+            nz[m] = make_float2(c[0][5], c[1][5]);
+        }
+        acc[m] = make_float2(0.f, 0.f);
     }
     // the leaf centre as FP32 hi + lo; a source's offset from it is (yh - ch) + (yl - cl)
     const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
@@ -516,23 +587,36 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const int* __
             const float4 sp = st[jj];
             float4 sd = make_float4(0.f, 0.f, 0.f, 0.f);
             if (KIND == 1) sd = st[32 + jj];
+            const float2 mx = make_float2(-sp.x, -sp.x), my = make_float2(-sp.y, -sp.y),
+                         mz = make_float2(-sp.z, -sp.z), qa = make_float2(sp.w, sp.w);
 #pragma unroll
-            for (int i = 0; i < T; ++i) {
-                const float dx = tx[i] - sp.x, dy = ty[i] - sp.y, dz = tz[i] - sp.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                const float inv = rsqrtf(r2);
-                float v;
-                if (KIND == 0) v = sp.w * inv;
-                else if (KIND == 1) v = (sp.w * dx + sd.x * dy + sd.y * dz) * (inv * inv * inv);
-                else v = sp.w * (nx[i] * dx + ny[i] * dy + nz[i] * dz) * (inv * inv * inv);
-                acc[i] += (r2 >= d2) ? v : 0.f;
+            for (int m = 0; m < TP; ++m) {
+                const float2 dx = __fadd2_rn(tx[m], mx), dy = __fadd2_rn(ty[m], my), dz = __fadd2_rn(tz[m], mz);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                float2 v;
+                if (KIND == 0) {
+                    v = __fmul2_rn(qa, inv);
+                } else {
+                    const float2 i3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+                    float2 num;
+                    if (KIND == 1)
+                        num = __ffma2_rn(make_float2(sd.y, sd.y), dz,
+                                         __ffma2_rn(make_float2(sd.x, sd.x), dy, __fmul2_rn(qa, dx)));
+                    else
+                        num = __fmul2_rn(qa, __ffma2_rn(nz[m], dz, __ffma2_rn(ny[m], dy, __fmul2_rn(nx[m], dx))));
+                    v = __fmul2_rn(num, i3);
+                }
+                v.x = r2.x >= d2 ? v.x : 0.f;
+                v.y = r2.y >= d2 ? v.y : 0.f;
+                acc[m] = __fadd2_rn(acc[m], v);
             }
         }
         __syncwarp();
     }
 #pragma unroll
     for (int i = 0; i < T; ++i) {
-        float v = acc[i];
+        float v = (i & 1) ? acc[i >> 1].y : acc[i >> 1].x;
         v += __shfl_xor_sync(0xffffffffu, v, 8);
         v += __shfl_xor_sync(0xffffffffu, v, 16);
         const int64_t t = t0 + 8 * i + r;
@@ -980,6 +1064,9 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_TRY(P.sxf.alloc(6 * (size_t)T.ns));
         k_split_xyz<<<div_up(T.ns, 256), 256, 0, s>>>(T.sxyz.p, T.ns, P.sxf.p);
         KF_CHECK_LAUNCH();
+        KF_TRY(P.bcf.alloc(3 * (size_t)T.nbox));
+        k_box_f<<<div_up(T.nbox, 256), 256, 0, s>>>(T.ctr.p, T.lvl.p, T.root_h, T.nbox, P.bcf.p);
+        KF_CHECK_LAUNCH();
     }
 
     // work lists (host bookkeeping over the tree's lists)
@@ -1117,7 +1204,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     for (size_t b : {(size_t)P.ops->bytes(), P.d2t_d.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
                      P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
                      P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(),
-                     P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes(), P.sxf.bytes(), P.zu.bytes(),
+                     P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes(), P.sxf.bytes(), P.bcf.bytes(), P.zu.bytes(),
                      P.zd.bytes()})
         P.device_bytes += (int64_t)b;
     return KIFMM_OK;

@@ -72,6 +72,7 @@ struct Plan {
 
     DBuf<double> snrm, tnrm_d;      // sorted normals (DL: sources; ADL: targets)
     DBuf<float> sxf;                // mixed: sorted source coordinates as FP32 hi/lo pairs, 6 x ns SoA
+    DBuf<float4> bcf;               // mixed: per box {centre hi, h}, {centre lo, 0}, {r_upcheck, r_dncheck}
     DBuf<float> tnrm_f;
 
     // work lists
