@@ -63,6 +63,7 @@ __global__ void k_gather_q(const double* __restrict__ q, const int64_t* __restri
 // shared memory relative to the box centre.  DIPOLE: n_j.(x - y)/|x - y|^3 q_j, else q_j/|x - y|.
 constexpr int kSurfThreads = 128;
 constexpr int kSurfPer = 8;  // Q <= 1024
+constexpr int kSurfThreadsF = 128;  // FP32 form: threads per box (2 NP points each)
 
 template <typename Real, bool DIPOLE>
 __global__ void __launch_bounds__(kSurfThreads)
@@ -130,7 +131,7 @@ k_src2surf(const int* __restrict__ boxes, const int* __restrict__ off, const int
     }
 }
 
-// FP32 form.  Each thread owns 2 NP surface points (points threadIdx.x + i kSurfThreads)
+// FP32 form.  Each thread owns 2 NP surface points (points threadIdx.x + i kSurfThreadsF)
 // as NP packed pairs: every step is one FP32x2 instruction for two points (the same
 // round-to-nearest operations as the scalar form).  Staged sources are float4 --
 // (x, y, z, q), and (q n_j) over two float4 for dipoles -- built from FP32 hi/lo
@@ -175,12 +176,12 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
 }
 
 template <bool DIPOLE, int NP>
-__global__ void __launch_bounds__(kSurfThreads)
+__global__ void __launch_bounds__(kSurfThreadsF)
 k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx, int down,
          const float4* __restrict__ bcf, const int64_t* __restrict__ rng, const float* __restrict__ sxf, int64_t ns,
          const float* __restrict__ qs, const float* __restrict__ surf, int Q, int Qp, float* __restrict__ outbuf) {
-    __shared__ float4 sp[kSurfThreads];
-    __shared__ float4 sd[DIPOLE ? kSurfThreads : 1];
+    __shared__ float4 sp[kSurfThreadsF];
+    __shared__ float4 sd[DIPOLE ? kSurfThreadsF : 1];
     const int b = boxes[blockIdx.x];
     const float4 bh = bcf[3 * b], bl = bcf[3 * b + 1], br = bcf[3 * b + 2];
     const float rf = down ? br.y : br.x;
@@ -190,7 +191,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
         float c[2][3];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int k = threadIdx.x + (2 * m + h) * kSurfThreads;
+            const int k = threadIdx.x + (2 * m + h) * kSurfThreadsF;
             const int kk = k < Q ? k : 0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) c[h][d] = rf * surf[3 * kk + d];
@@ -209,7 +210,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
         const float dm = fmaxf(fabsf((ah.x - bh.x) + (al.x - bl.x)),
                                fmaxf(fabsf((ah.y - bh.y) + (al.y - bl.y)), fabsf((ah.z - bh.z) + (al.z - bl.z))));
         const bool near = fmaxf(dm - ah.w - rf, rf - dm - ah.w) <= margin;
-        for (int64_t j0 = sb; j0 < se; j0 += kSurfThreads) {
+        for (int64_t j0 = sb; j0 < se; j0 += kSurfThreadsF) {
             const int64_t j = j0 + threadIdx.x;
             if (j < se) {
                 sp[threadIdx.x] = make_float4((sxf[j] - bh.x) + (sxf[3 * ns + j] - bl.x),
@@ -218,7 +219,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
                 if (DIPOLE) sd[threadIdx.x] = make_float4(qs[ns + j], qs[2 * ns + j], 0.f, 0.f);
             }
             __syncthreads();
-            const int cnt = (int)((se - j0) < (int64_t)kSurfThreads ? (se - j0) : (int64_t)kSurfThreads);
+            const int cnt = (int)((se - j0) < (int64_t)kSurfThreadsF ? (se - j0) : (int64_t)kSurfThreadsF);
             if (near)
                 surf_pairs<true, DIPOLE, NP>(sp, sd, cnt, px, py, pz, acc);
             else
@@ -228,7 +229,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
     }
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
-        const int k0 = threadIdx.x + 2 * m * kSurfThreads, k1 = k0 + kSurfThreads;
+        const int k0 = threadIdx.x + 2 * m * kSurfThreadsF, k1 = k0 + kSurfThreadsF;
         if (k0 < Q) outbuf[(size_t)b * Qp + k0] += acc[m].x;
         if (k1 < Q) outbuf[(size_t)b * Qp + k1] += acc[m].y;
     }
@@ -259,16 +260,16 @@ int launch_surf(const Plan& P, const Tree& T, bool dl, int nbox, const int* boxe
                 double radius, const Real* q, const Real* surf, Real* out, cudaStream_t s) {
     if (nbox <= 0) return KIFMM_OK;
     if constexpr (std::is_same<Real, float>::value) {
-        const int np = (P.Q + 2 * kSurfThreads - 1) / (2 * kSurfThreads);
+        const int np = (P.Q + 2 * kSurfThreadsF - 1) / (2 * kSurfThreadsF);
         const int down = radius == kDnCheck ? 1 : 0;
         switch (np * 2 + (dl ? 1 : 0)) {
 #define KF_SURF(NP)                                                                                              \
     case 2 * NP:                                                                                                 \
-        k_surf_f<false, NP><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, \
+        k_surf_f<false, NP><<<nbox, kSurfThreadsF, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, \
                                                           q, surf, P.Q, P.Qp, out);                             \
         break;                                                                                                   \
     case 2 * NP + 1:                                                                                             \
-        k_surf_f<true, NP><<<nbox, kSurfThreads, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns,  \
+        k_surf_f<true, NP><<<nbox, kSurfThreadsF, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns,  \
                                                          q, surf, P.Q, P.Qp, out);                              \
         break;
             KF_SURF(1) KF_SURF(2) KF_SURF(3) KF_SURF(4)
