@@ -499,6 +499,11 @@ __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ of
 // count repeats a target and drops it), so each step is one FP32x2 instruction for two
 // pair evaluations, with the scalar form's round-to-nearest operations.
 constexpr int kP2PWarps = 8;
+// Larger target leaves go to the block kernel (a thread per target, sources staged once
+// per leaf): at leaf 128 on the 64-sphere pack it takes 2.56 ms against 4.04 ms for two
+// 64-target passes of this kernel, and 3.70 ms for a packed variant with two targets
+// per thread and half the threads.
+constexpr int kP2PWarpMaxLeaf = 64;
 
 template <int KIND, int T>
 __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const int* __restrict__ idx,
@@ -1369,7 +1374,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         // a block per leaf, whose staged sources serve all of the leaf's targets at once
         bool done = false;
         if constexpr (std::is_same<Real, float>::value) {
-          if (P.max_trg_leaf <= 64) {
+          if (P.max_trg_leaf <= kP2PWarpMaxLeaf) {
             const unsigned grid = (unsigned)((P.n_tleaf + kP2PWarps - 1) / kP2PWarps);
 #define KF_P2PW(KIND)                                                                                     \
     k_p2p_warp<KIND><<<grid, 32 * kP2PWarps, 0, s>>>(P.tleaf.p, P.n_tleaf, P.p2p_off.p, P.p2p_idx.p, T.rng.p, \
