@@ -175,11 +175,17 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
     }
 }
 
+//
+// A block holds the whole check potential of its box, so it also writes the box's input
+// for the tensor-core projection that follows: the potential scaled by the power of two
+// that puts its largest entry into [2^14, 2^15) (exponent in bexp[b]) and split into
+// FP16 hi and lo terms (Qp per box, zero past Q) -- the box split done in the producer.
 template <bool DIPOLE, int NP>
 __global__ void __launch_bounds__(kSurfThreadsF)
 k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx, int down,
          const float4* __restrict__ bcf, const int64_t* __restrict__ rng, const float* __restrict__ sxf, int64_t ns,
-         const float* __restrict__ qs, const float* __restrict__ surf, int Q, int Qp, float* __restrict__ outbuf) {
+         const float* __restrict__ qs, const float* __restrict__ surf, int Q, int Qp, __half* __restrict__ vin_h,
+         __half* __restrict__ vin_l, int* __restrict__ bexp) {
     __shared__ float4 sp[kSurfThreadsF];
     __shared__ float4 sd[DIPOLE ? kSurfThreadsF : 1];
     const int b = boxes[blockIdx.x];
@@ -227,11 +233,44 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
             __syncthreads();
         }
     }
+    // the box's largest |potential| (points past Q hold partial sums of a repeated point)
+    __shared__ float s_red[kSurfThreadsF / 32];
+    float mx = 0.f;
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         const int k0 = threadIdx.x + 2 * m * kSurfThreadsF, k1 = k0 + kSurfThreadsF;
-        if (k0 < Q) outbuf[(size_t)b * Qp + k0] += acc[m].x;
-        if (k1 < Q) outbuf[(size_t)b * Qp + k1] += acc[m].y;
+        if (k0 < Q) mx = fmaxf(mx, fabsf(acc[m].x));
+        if (k1 < Q) mx = fmaxf(mx, fabsf(acc[m].y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = s_red[0];
+#pragma unroll
+    for (int w = 1; w < kSurfThreadsF / 32; ++w) mx = fmaxf(mx, s_red[w]);
+    int ex = mx > 0.f ? 14 - ilogbf(mx) : 0;
+    ex = max(-100, min(100, ex));
+    if (threadIdx.x == 0) bexp[b] = ex;
+    const float sc = __int_as_float((127 + ex) << 23);
+    __half* hb = vin_h + (size_t)b * Qp;
+    __half* lb = vin_l + (size_t)b * Qp;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = threadIdx.x + (2 * m + h) * kSurfThreadsF;
+            if (k < Qp) {
+                const float x = k < Q ? (h ? acc[m].y : acc[m].x) * sc : 0.f;
+                const __half hh = __float2half_rn(x);
+                hb[k] = hh;
+                lb[k] = __float2half_rn(x - __half2float(hh));
+            }
+        }
+    }
+    for (int k = threadIdx.x + 2 * NP * kSurfThreadsF; k < Qp; k += kSurfThreadsF) {
+        hb[k] = __float2half_rn(0.f);
+        lb[k] = __float2half_rn(0.f);
     }
 }
 
@@ -254,23 +293,26 @@ __global__ void k_box_f(const double* __restrict__ ctr, const int* __restrict__ 
 }
 
 // Sources -> check surfaces of a CSR list of boxes (S2U: leaves and themselves; X list:
-// boxes and their X sources), FP32 through k_surf_f, FP64 through k_src2surf.
+// boxes and their X sources).  FP32 through k_surf_f, which writes the split input of
+// the projection that follows (out unused); FP64 through k_src2surf, adding into out.
 template <typename Real>
 int launch_surf(const Plan& P, const Tree& T, bool dl, int nbox, const int* boxes, const int* off, const int* idx,
                 double radius, const Real* q, const Real* surf, Real* out, cudaStream_t s) {
     if (nbox <= 0) return KIFMM_OK;
     if constexpr (std::is_same<Real, float>::value) {
+        (void)out;
+        (void)surf;
         const int np = (P.Q + 2 * kSurfThreadsF - 1) / (2 * kSurfThreadsF);
         const int down = radius == kDnCheck ? 1 : 0;
         switch (np * 2 + (dl ? 1 : 0)) {
 #define KF_SURF(NP)                                                                                              \
     case 2 * NP:                                                                                                 \
         k_surf_f<false, NP><<<nbox, kSurfThreadsF, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, \
-                                                          q, surf, P.Q, P.Qp, out);                             \
+                                                          q, surf, P.Q, P.Qp, P.vin_h.p, P.vin_l.p, P.bexp.p);  \
         break;                                                                                                   \
     case 2 * NP + 1:                                                                                             \
         k_surf_f<true, NP><<<nbox, kSurfThreadsF, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns,  \
-                                                         q, surf, P.Q, P.Qp, out);                              \
+                                                         q, surf, P.Q, P.Qp, P.vin_h.p, P.vin_l.p, P.bexp.p);   \
         break;
             KF_SURF(1) KF_SURF(2) KF_SURF(3) KF_SURF(4)
 #undef KF_SURF
@@ -1199,8 +1241,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         // rows G W_d, reading the projected down-check potentials
         KF_TRY(P.d2t_f.alloc((size_t)T.nt * P.ops->Kd));
         KF_TRY(build_d2t<float>(P, h, true, P.ops->Kd, tleaf_of, P.d2t_f.p, s));
-        KF_TRY(P.u_f.alloc(nbq));
-        KF_TRY(P.d_f.alloc(nbq));
+        // (no FP32 check potentials: S2U and X write the projections' split inputs)
         KF_TRY(P.res_f.alloc(T.nt));
         KF_TRY(P.q_f.alloc(3 * T.ns));
     }
@@ -1249,15 +1290,13 @@ int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int 
     return KIFMM_OK;
 }
 
-// Mixed: projection of full check potentials v (Q of Qp per box) of the boxes in pt's
-// tiles onto the up (fam 3) or down (fam 4) basis, added into z.
-int project(const Plan& P, int fam, const PairTiles& pt, const float* v, float* z, cudaStream_t s,
-            int& launches) {
-    const Tree& T = P.tree->t;
+// Mixed: projection of the full check potentials of the boxes in pt's tiles onto the up
+// (fam 3) or down (fam 4) basis, added into z.  Their split inputs (vin_h/vin_l, Qp per
+// box, exponents in bexp) were written by the surface kernel that computed them.
+int project(const Plan& P, int fam, const PairTiles& pt, float* z, cudaStream_t s, int& launches) {
     if (pt.ntiles == 0) return KIFMM_OK;
     const OpTables& o = *P.ops;
     const int Mr = fam == 3 ? o.Ku : o.Kd, M = fam == 3 ? o.ru : o.rd;
-    KF_TRY(tc_box_split(v, P.Q, P.Qp, 0, T.nbox, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
     const CUtensorMap* m = o.tmaps[fam];
     KF_TRY(launch_pair_tc(3, m[0], m[1], o.texp[fam], M, Mr, P.Qp, Mr, pt.tiles.p, pt.ntiles, pt.pin.p,
                           pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, z, P.err.p, s));
@@ -1302,12 +1341,16 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_TRY(mark(0));
     k_gather_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, T.sperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q);
     KF_CHECK_LAUNCH();
-    KF_CHECK_CUDA(cudaMemsetAsync(B.u, 0, nbq * sizeof(Real), s));
-    KF_CHECK_CUDA(cudaMemsetAsync(B.d, 0, nbq * sizeof(Real), s));
-    launches += 3;
+    ++launches;
+    constexpr bool mixed_form = std::is_same<Real, float>::value;
+    if constexpr (!mixed_form) {
+        KF_CHECK_CUDA(cudaMemsetAsync(B.u, 0, nbq * sizeof(Real), s));
+        KF_CHECK_CUDA(cudaMemsetAsync(B.d, 0, nbq * sizeof(Real), s));
+        launches += 2;
+    }
     // the vectors the translations act on: check potentials (FP64) or, mixed, their
-    // projections (zu, zd); mixed S2U and X write full potentials into B.u / B.d,
-    // which are projected before they are translated
+    // projections (zu, zd); mixed S2U and X write their full potentials as the split
+    // input of a projection, which adds them into zu / zd
     constexpr bool mixed = std::is_same<Real, float>::value;
     Real* up = B.u;
     Real* dn = B.d;
@@ -1329,7 +1372,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     }
     KF_TRY(mark(2));
     // mixed: the leaves' projections; U2U, deepest parents first
-    if constexpr (mixed) KF_TRY(project(P, 3, P.proj_up, B.u, up, s, launches));
+    if constexpr (mixed) KF_TRY(project(P, 3, P.proj_up, up, s, launches));
     for (int l = T.nlev - 1; l >= 2; --l)
         KF_TRY(run_pairs<Real>(P, kU2U, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, up, up,
                                T.level_off[std::min(l + 1, T.nlev)], T.level_off[std::min(l + 2, T.nlev)], s,
@@ -1340,7 +1383,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         KF_TRY(launch_surf<Real>(P, T, dl, P.n_p2l, P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, kDnCheck, B.q, B.surf,
                                  B.d, s));
         ++launches;
-        if constexpr (mixed) KF_TRY(project(P, 4, P.proj_x, B.d, dn, s, launches));
+        if constexpr (mixed) KF_TRY(project(P, 4, P.proj_x, dn, s, launches));
     }
     KF_TRY(mark(4));
     KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, up, dn, T.level_off[std::min(2, T.nlev)],
