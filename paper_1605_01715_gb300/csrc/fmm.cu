@@ -540,7 +540,14 @@ __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ of
 // per staged source.  A lane's targets are packed in pairs (the last pair of an odd
 // count repeats a target and drops it), so each step is one FP32x2 instruction for two
 // pair evaluations, with the scalar form's round-to-nearest operations.
+// Work is split into units of at most kP2PUnitSrc sources of one leaf (its U- and
+// W-list source ranges, cut where needed) and the units run heaviest first: on
+// adaptive geometries a few leaves next to dense regions carry W lists of tens of
+// thousands of sources, and one warp per leaf left them running alone at the end.  A
+// leaf with several units adds into its outputs with FP64 atomics (the output is
+// zeroed first); the first unit also adds the far field.
 constexpr int kP2PWarps = 8;
+constexpr int kP2PUnitSrc = 2048;
 // Larger target leaves go to the block kernel (a thread per target, sources staged once
 // per leaf): at leaf 128 on the 64-sphere pack it takes 2.56 ms against 4.04 ms for two
 // 64-target passes of this kernel, and 3.70 ms for a packed variant with two targets
@@ -548,8 +555,8 @@ constexpr int kP2PWarps = 8;
 constexpr int kP2PWarpMaxLeaf = 64;
 
 template <int KIND, int T>
-__device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const int* __restrict__ idx,
-                                         const int64_t* __restrict__ rng, double cx, double cy, double cz,
+__device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlong2* __restrict__ ranges,
+                                         int flags, double cx, double cy, double cz,
                                          const float* __restrict__ sxf, int64_t ns,
                                          const double* __restrict__ txyz, int64_t nt,
                                          const float* __restrict__ qs, const float* __restrict__ tnrm,
@@ -593,9 +600,8 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const int* __
     int e = e0;
     int64_t j0 = 0, se = 0;
     if (e < e1) {
-        const int a = idx[e];
-        j0 = rng[4 * a];
-        se = rng[4 * a + 1];
+        j0 = ranges[e].x;
+        se = ranges[e].y;
     }
     float ph[3], pl[3], pq[3];
     auto fetch = [&](int64_t jb, int64_t je) {
@@ -625,9 +631,8 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const int* __
         // advance to the next chunk and prefetch it
         j0 += 32;
         while (j0 >= se && ++e < e1) {
-            const int a = idx[e];
-            j0 = rng[4 * a];
-            se = rng[4 * a + 1];
+            j0 = ranges[e].x;
+            se = ranges[e].y;
         }
         __syncwarp();
 #pragma unroll 1
@@ -668,25 +673,30 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const int* __
         v += __shfl_xor_sync(0xffffffffu, v, 8);
         v += __shfl_xor_sync(0xffffffffu, v, 16);
         const int64_t t = t0 + 8 * i + r;
-        if (g == 0 && t < te) out[tperm[t]] = (double)(v + res[t]);
+        if (g == 0 && t < te) {
+            if (!(flags & 2)) out[tperm[t]] = (double)(v + res[t]);                        // the leaf's only unit
+            else atomicAdd(out + tperm[t], (double)((flags & 1) ? v + res[t] : v));       // one of several
+        }
     }
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(32 * kP2PWarps)
-k_p2p_warp(const int* __restrict__ leaves, int nleaves, const int* __restrict__ off, const int* __restrict__ idx,
-           const int64_t* __restrict__ rng, const double* __restrict__ ctr, const float* __restrict__ sxf,
+k_p2p_warp(const int* __restrict__ leaves, int nunits, const int4* __restrict__ units,
+           const longlong2* __restrict__ ranges, const int64_t* __restrict__ rng, const double* __restrict__ ctr,
+           const float* __restrict__ sxf,
            int64_t ns, const double* __restrict__ txyz, int64_t nt, const float* __restrict__ qs,
            const float* __restrict__ tnrm, const float* __restrict__ res, const int64_t* __restrict__ tperm,
            double* __restrict__ out) {
     __shared__ float4 stage[kP2PWarps][KIND == 1 ? 64 : 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int li = blockIdx.x * kP2PWarps + warp;
-    if (li >= nleaves) return;                    // whole warp; no block-wide barrier below
-    const int b = leaves[li];
+    const int ui = blockIdx.x * kP2PWarps + warp;
+    if (ui >= nunits) return;                     // whole warp; no block-wide barrier below
+    const int4 u = units[ui];                     // (leaf, first range, end range, flags)
+    const int b = leaves[u.x];
     const double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
     const int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
-    const int e0 = off[li], e1 = off[li + 1];
+    const int e0 = u.y, e1 = u.z;
     float4* st = stage[warp];
     for (int64_t t0 = tb; t0 < te; t0 += 64) {
         const int n = (int)(te - t0 < 64 ? te - t0 : 64);
@@ -694,7 +704,7 @@ k_p2p_warp(const int* __restrict__ leaves, int nleaves, const int* __restrict__ 
         switch ((n + 7) >> 3) {
 #define KF_PASS(TT)                                                                                  \
     case TT:                                                                                         \
-        p2p_pass<KIND, TT>(lane, e0, e1, idx, rng, cx, cy, cz, sxf, ns, txyz, nt, qs, tnrm, res, tperm, \
+        p2p_pass<KIND, TT>(lane, e0, e1, ranges, u.w, cx, cy, cz, sxf, ns, txyz, nt, qs, tnrm, res, tperm, \
                            out, t0, tend, st);                                                       \
         break;
             KF_PASS(1) KF_PASS(2) KF_PASS(3) KF_PASS(4) KF_PASS(5) KF_PASS(6) KF_PASS(7) KF_PASS(8)
@@ -1156,6 +1166,48 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     KF_TRY(P.tleaf.upload(tleaf, s));
     KF_TRY(P.p2p_off.upload(p2p_off, s));
     KF_TRY(P.p2p_idx.upload(p2p_idx, s));
+    // mixed: near-field work units of at most kP2PUnitSrc sources, heaviest first
+    if (!P.fp64) {
+        struct Unit {
+            int4 u;
+            int64_t work;
+        };
+        std::vector<Unit> units;
+        std::vector<longlong2> ranges;
+        for (size_t li = 0; li < tleaf.size(); ++li) {
+            const int b = tleaf[li];
+            const int64_t ntg = T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2];
+            const size_t u0 = units.size();
+            int r0 = (int)ranges.size();
+            int64_t cnt = 0;
+            for (int k = p2p_off[li]; k < p2p_off[li + 1]; ++k) {
+                const int a = p2p_idx[k];
+                int64_t j0 = T.h_rng[4 * a], j1 = T.h_rng[4 * a + 1];
+                while (j0 < j1) {
+                    const int64_t take = std::min<int64_t>(j1 - j0, kP2PUnitSrc - cnt);
+                    ranges.push_back(make_longlong2(j0, j0 + take));
+                    cnt += take;
+                    j0 += take;
+                    if (cnt == kP2PUnitSrc) {
+                        units.push_back({make_int4((int)li, r0, (int)ranges.size(), 0), ntg * cnt});
+                        r0 = (int)ranges.size();
+                        cnt = 0;
+                    }
+                }
+            }
+            if (cnt > 0 || units.size() == u0)
+                units.push_back({make_int4((int)li, r0, (int)ranges.size(), 0), ntg * cnt});
+            const bool split = units.size() - u0 > 1;
+            P.p2p_multi = P.p2p_multi || split;
+            for (size_t i = u0; i < units.size(); ++i) units[i].u.w = (i == u0 ? 1 : 0) | (split ? 2 : 0);
+        }
+        std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.work > y.work; });
+        std::vector<int4> hu(units.size());
+        for (size_t i = 0; i < units.size(); ++i) hu[i] = units[i].u;
+        KF_TRY(P.p2p_units.upload(hu, s));
+        KF_TRY(P.p2p_ranges.upload(ranges, s));
+        P.n_p2p_units = (int)hu.size();
+    }
 
     // U2U: per parent level, (child -> parent) grouped by the child's octant
     {
@@ -1418,11 +1470,15 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         bool done = false;
         if constexpr (std::is_same<Real, float>::value) {
           if (P.max_trg_leaf <= kP2PWarpMaxLeaf) {
-            const unsigned grid = (unsigned)((P.n_tleaf + kP2PWarps - 1) / kP2PWarps);
-#define KF_P2PW(KIND)                                                                                     \
-    k_p2p_warp<KIND><<<grid, 32 * kP2PWarps, 0, s>>>(P.tleaf.p, P.n_tleaf, P.p2p_off.p, P.p2p_idx.p, T.rng.p, \
-                                                      T.ctr.p, P.sxf.p, T.ns, txyz, T.nt,                   \
-                                                      B.q, B.tnrm, B.res, tperm, out)
+            const unsigned grid = (unsigned)((P.n_p2p_units + kP2PWarps - 1) / kP2PWarps);
+            if (P.p2p_multi) {
+                KF_CHECK_CUDA(cudaMemsetAsync(out, 0, (size_t)T.nt * sizeof(double), s));
+                ++launches;
+            }
+#define KF_P2PW(KIND)                                                                                       \
+    k_p2p_warp<KIND><<<grid, 32 * kP2PWarps, 0, s>>>(P.tleaf.p, P.n_p2p_units, P.p2p_units.p, P.p2p_ranges.p, \
+                                                      T.rng.p, T.ctr.p, P.sxf.p, T.ns, txyz, T.nt, B.q,      \
+                                                      B.tnrm, B.res, tperm, out)
             if (P.kernel == KIFMM_KERNEL_SL) KF_P2PW(0);
             else if (P.kernel == KIFMM_KERNEL_DL) KF_P2PW(1);
             else KF_P2PW(2);

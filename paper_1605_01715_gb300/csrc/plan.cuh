@@ -79,6 +79,11 @@ struct Plan {
     DBuf<int> s2u_box, s2u_off, s2u_idx;  // S2U: leaf boxes, CSR of source boxes (itself)
     DBuf<int> p2l_box, p2l_off, p2l_idx;  // X list: boxes, CSR of source leaves
     DBuf<int> tleaf, p2p_off, p2p_idx;    // target leaves, CSR of U + W source boxes
+    DBuf<int4> p2p_units;                 // mixed: near-field work units (leaf, first range,
+                                          // end range, flags: 1 first of its leaf, 2 leaf split)
+    DBuf<longlong2> p2p_ranges;           // mixed: source index ranges of the units
+    int n_p2p_units = 0;
+    bool p2p_multi = false;               // some leaf spans several units
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
     PairTiles u2u, m2l, l2l;
