@@ -5,11 +5,13 @@
 //           source-to-check step, Sec. III.A.1 Eq. p2m -- the paper's second method)
 //   S2U     leaf up-check potentials from the leaf's sources
 //   U2U     parent up-check += M2M'_oct child up-check, level by level upward
-//   X       down-check potentials from the sources of X-list leaves
+//   X       down-check potentials from the sources of X-list leaves (non-leaf targets;
+//           a target leaf takes its X-list sources directly in P2P)
 //   M2L     down-check += M2L'_offset up-check of each V-list box
 //   L2L     child down-check += L2L'_oct parent down-check, level by level downward
 //   D2T     far-field value at each target = its precomputed row . leaf down-check
-//   P2P     near field over U- and W-list sources, added, scattered to input order
+//   P2P     near field over U-, W- (and for leaves X-) list sources, added, scattered to
+//           input order
 // Near-singular pairs (|r_i - r_j| < 1e-5) contribute nothing (Sec. III.A.1).
 #include <algorithm>
 #include <cmath>
@@ -1137,7 +1139,12 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
             s2u_idx.push_back(b);
             s2u_off.push_back((int)s2u_idx.size());
         }
-        if (has_trg(T, b) && T.h_x_off[b + 1] > T.h_x_off[b]) {
+        // X list: a leaf with fewer targets than check points takes its X sources
+        // directly, with its U and W sources (|A| x n_t kernel evaluations, exact, instead
+        // of |A| x Q onto its down-check surface); other boxes go through the surface
+        const int64_t ntb = T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2];
+        const bool x_direct = T.h_leaf[b] && ntb < P.Q;
+        if (has_trg(T, b) && T.h_x_off[b + 1] > T.h_x_off[b] && !x_direct) {
             p2l_box.push_back(b);
             for (int k = T.h_x_off[b]; k < T.h_x_off[b + 1]; ++k) {
                 p2l_idx.push_back(T.h_x_idx[k]);
@@ -1149,6 +1156,8 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
             tleaf.push_back(b);
             for (int k = T.h_u_off[b]; k < T.h_u_off[b + 1]; ++k) p2p_idx.push_back(T.h_u_idx[k]);
             for (int k = T.h_w_off[b]; k < T.h_w_off[b + 1]; ++k) p2p_idx.push_back(T.h_w_idx[k]);
+            if (x_direct)
+                for (int k = T.h_x_off[b]; k < T.h_x_off[b + 1]; ++k) p2p_idx.push_back(T.h_x_idx[k]);
             p2p_off.push_back((int)p2p_idx.size());
             for (int64_t t = T.h_rng[4 * b + 2]; t < T.h_rng[4 * b + 3]; ++t) tleaf_of[t] = b;
             P.max_trg_leaf = std::max<int>(P.max_trg_leaf, (int)(T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2]));
