@@ -209,6 +209,10 @@ typedef struct {
                                          on the projections onto Pu's range)          */
     int32_t m2l_rows;                 /* its rows: q_points (FP64) or rank_down (mixed:
                                          it yields the projection onto Pd's range)    */
+    int32_t near_units;               /* mixed: near-field work units (pieces of at
+                                         most 2048 sources of one target leaf)        */
+    int32_t near_split_leaves;        /* mixed: target leaves spread over several
+                                         units (their sums meet by FP64 atomics)      */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);

@@ -54,7 +54,8 @@ class PlanStats(ctypes.Structure):
                 ("s2u_leaves", ctypes.c_int64), ("x_pairs", ctypes.c_int64),
                 ("launches_per_matvec", ctypes.c_int32), ("rank_up", ctypes.c_int32),
                 ("rank_down", ctypes.c_int32), ("m2l_width", ctypes.c_int32),
-                ("m2l_rows", ctypes.c_int32)]
+                ("m2l_rows", ctypes.c_int32), ("near_units", ctypes.c_int32),
+                ("near_split_leaves", ctypes.c_int32)]
 
 
 def _as_dict(st):

@@ -1208,6 +1208,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                 units.push_back({make_int4((int)li, r0, (int)ranges.size(), 0), ntg * cnt});
             const bool split = units.size() - u0 > 1;
             P.p2p_multi = P.p2p_multi || split;
+            P.n_p2p_split += split ? 1 : 0;
             for (size_t i = u0; i < units.size(); ++i) units[i].u.w = (i == u0 ? 1 : 0) | (split ? 2 : 0);
         }
         std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.work > y.work; });
@@ -1636,6 +1637,8 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->rank_down = P.ops ? P.ops->rd : 0;
     st->m2l_width = P.fp64 ? P.Q : st->rank_up;
     st->m2l_rows = P.fp64 ? P.Q : st->rank_down;
+    st->near_units = P.n_p2p_units;
+    st->near_split_leaves = P.n_p2p_split;
     return KIFMM_OK;
 }
 

@@ -82,7 +82,7 @@ struct Plan {
     DBuf<int4> p2p_units;                 // mixed: near-field work units (leaf, first range,
                                           // end range, flags: 1 first of its leaf, 2 leaf split)
     DBuf<longlong2> p2p_ranges;           // mixed: source index ranges of the units
-    int n_p2p_units = 0;
+    int n_p2p_units = 0, n_p2p_split = 0;
     bool p2p_multi = false;               // some leaf spans several units
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
