@@ -676,8 +676,10 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
         v += __shfl_xor_sync(0xffffffffu, v, 16);
         const int64_t t = t0 + 8 * i + r;
         if (g == 0 && t < te) {
-            if (!(flags & 2)) out[tperm[t]] = (double)(v + res[t]);                        // the leaf's only unit
-            else atomicAdd(out + tperm[t], (double)((flags & 1) ? v + res[t] : v));       // one of several
+            // res (the far field) is added here, or later by the caller when null
+            const float far = res ? res[t] : 0.f;
+            if (!(flags & 2)) out[tperm[t]] = (double)(v + far);                          // the leaf's only unit
+            else atomicAdd(out + tperm[t], (double)((flags & 1) ? v + far : v));         // one of several
         }
     }
 }
@@ -713,6 +715,13 @@ k_p2p_warp(const int* __restrict__ leaves, int nunits, const int4* __restrict__ 
 #undef KF_PASS
         }
     }
+}
+
+// out[tperm[t]] += res[t]: the far field, after a near field that ran beside it.
+__global__ void k_add_far(const int64_t* __restrict__ tperm, const float* __restrict__ res, int64_t nt,
+                          double* __restrict__ out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < nt) out[tperm[t]] += (double)res[t];
 }
 
 // ---------------------------------------------------------------- set-up kernels
@@ -1288,6 +1297,13 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         }
         KF_TRY(P.zu.alloc((size_t)T.nbox * P.ops->Ku));
         KF_TRY(P.zd.alloc((size_t)T.nbox * P.ops->Kd));
+        int prio_lo = 0, prio_hi = 0;
+        KF_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        KF_CHECK_CUDA(cudaStreamCreateWithPriority(&P.near_stream, cudaStreamNonBlocking, prio_lo));
+        KF_CHECK_CUDA(cudaStreamCreateWithPriority(&P.far_stream, cudaStreamNonBlocking, prio_hi));
+        KF_CHECK_CUDA(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
+        KF_CHECK_CUDA(cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming));
+        KF_CHECK_CUDA(cudaEventCreateWithFlags(&P.ev_far, cudaEventDisableTiming));
     }
 
     // per-target evaluation rows and buffers
@@ -1395,15 +1411,71 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         }
         if (P.slots_used < (int)P.ev_slots.size()) slot = P.ev_slots[P.slots_used++].data();
     }
-    auto mark = [&](int i) -> int {
-        if (slot) KF_CHECK_CUDA(cudaEventRecord(slot[i], s));
+    auto mark = [&](int i, cudaStream_t on = nullptr) -> int {
+        if (slot) KF_CHECK_CUDA(cudaEventRecord(slot[i], on ? on : s));
         return KIFMM_OK;
     };
+    // the near field on stream ns; res: the far field to add, or null (added later)
+    auto near_field = [&](cudaStream_t ns, const Real* res) -> int {
+        const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
+        const int64_t* tperm = T.same ? T.sperm.p : T.tperm.p;
+        // FP32 with leaves of up to 64 targets: a warp per leaf; larger leaves (and FP64):
+        // a block per leaf, whose staged sources serve all of the leaf's targets at once
+        bool done = false;
+        if constexpr (std::is_same<Real, float>::value) {
+          if (P.max_trg_leaf <= kP2PWarpMaxLeaf) {
+            const unsigned grid = (unsigned)((P.n_p2p_units + kP2PWarps - 1) / kP2PWarps);
+            if (P.p2p_multi) {
+                KF_CHECK_CUDA(cudaMemsetAsync(out, 0, (size_t)T.nt * sizeof(double), ns));
+                ++launches;
+            }
+#define KF_P2PW(KIND)                                                                                       \
+    k_p2p_warp<KIND><<<grid, 32 * kP2PWarps, 0, ns>>>(P.tleaf.p, P.n_p2p_units, P.p2p_units.p, P.p2p_ranges.p, \
+                                                      T.rng.p, T.ctr.p, P.sxf.p, T.ns, txyz, T.nt, B.q,      \
+                                                      B.tnrm, res, tperm, out)
+            if (P.kernel == KIFMM_KERNEL_SL) KF_P2PW(0);
+            else if (P.kernel == KIFMM_KERNEL_DL) KF_P2PW(1);
+            else KF_P2PW(2);
+#undef KF_P2PW
+            done = true;
+          }
+        }
+        if (!done) {
+        int threads = std::min(256, std::max(32, (P.max_trg_leaf + 31) / 32 * 32));
+        size_t smem = 6 * threads * sizeof(Real);
+#define KF_P2P(KIND)                                                                                     \
+    k_p2p<Real, KIND><<<P.n_tleaf, threads, smem, ns>>>(P.tleaf.p, P.p2p_off.p, P.p2p_idx.p, T.rng.p,     \
+                                                        T.ctr.p, T.sxyz.p, T.ns, txyz, T.nt, B.q, B.tnrm, \
+                                                        res, tperm, out)
+        if (P.kernel == KIFMM_KERNEL_SL) KF_P2P(0);
+        else if (P.kernel == KIFMM_KERNEL_DL) KF_P2P(1);
+        else KF_P2P(2);
+#undef KF_P2P
+        }
+        KF_CHECK_LAUNCH();
+        ++launches;
+        return KIFMM_OK;
+    };
+    // mixed, warp near field: it runs on its own stream beside the far field (forked
+    // after the gather) and the far field is added once both are done
+    const bool near_overlap = std::is_same<Real, float>::value && P.n_tleaf && P.near_stream &&
+                              P.max_trg_leaf <= kP2PWarpMaxLeaf;
     const bool dl = P.kernel == KIFMM_KERNEL_DL;
     KF_TRY(mark(0));
     k_gather_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, T.sperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q);
     KF_CHECK_LAUNCH();
     ++launches;
+    const cudaStream_t s_in = s;                  // the caller's stream
+    if (near_overlap) {
+        KF_CHECK_CUDA(cudaEventRecord(P.ev_fork, s));
+        KF_CHECK_CUDA(cudaStreamWaitEvent(P.near_stream, P.ev_fork, 0));
+        KF_CHECK_CUDA(cudaStreamWaitEvent(P.far_stream, P.ev_fork, 0));
+        KF_TRY(mark(9, P.near_stream));
+        KF_TRY(near_field(P.near_stream, nullptr));
+        KF_TRY(mark(10, P.near_stream));
+        KF_CHECK_CUDA(cudaEventRecord(P.ev_join, P.near_stream));
+        s = P.far_stream;                         // the far-field phases below
+    }
     constexpr bool mixed_form = std::is_same<Real, float>::value;
     if constexpr (!mixed_form) {
         KF_CHECK_CUDA(cudaMemsetAsync(B.u, 0, nbq * sizeof(Real), s));
@@ -1472,42 +1544,19 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         ++launches;
     }
     KF_TRY(mark(7));
-    if (P.n_tleaf) {
-        const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
-        const int64_t* tperm = T.same ? T.sperm.p : T.tperm.p;
-        // FP32 with leaves of up to 64 targets: a warp per leaf; larger leaves (and FP64):
-        // a block per leaf, whose staged sources serve all of the leaf's targets at once
-        bool done = false;
-        if constexpr (std::is_same<Real, float>::value) {
-          if (P.max_trg_leaf <= kP2PWarpMaxLeaf) {
-            const unsigned grid = (unsigned)((P.n_p2p_units + kP2PWarps - 1) / kP2PWarps);
-            if (P.p2p_multi) {
-                KF_CHECK_CUDA(cudaMemsetAsync(out, 0, (size_t)T.nt * sizeof(double), s));
-                ++launches;
-            }
-#define KF_P2PW(KIND)                                                                                       \
-    k_p2p_warp<KIND><<<grid, 32 * kP2PWarps, 0, s>>>(P.tleaf.p, P.n_p2p_units, P.p2p_units.p, P.p2p_ranges.p, \
-                                                      T.rng.p, T.ctr.p, P.sxf.p, T.ns, txyz, T.nt, B.q,      \
-                                                      B.tnrm, B.res, tperm, out)
-            if (P.kernel == KIFMM_KERNEL_SL) KF_P2PW(0);
-            else if (P.kernel == KIFMM_KERNEL_DL) KF_P2PW(1);
-            else KF_P2PW(2);
-#undef KF_P2PW
-            done = true;
-          }
-        }
-        if (!done) {
-        int threads = std::min(256, std::max(32, (P.max_trg_leaf + 31) / 32 * 32));
-        size_t smem = 6 * threads * sizeof(Real);
-#define KF_P2P(KIND)                                                                                     \
-    k_p2p<Real, KIND><<<P.n_tleaf, threads, smem, s>>>(P.tleaf.p, P.p2p_off.p, P.p2p_idx.p, T.rng.p,     \
-                                                        T.ctr.p, T.sxyz.p, T.ns, txyz, T.nt, B.q, B.tnrm, \
-                                                        B.res, tperm, out)
-        if (P.kernel == KIFMM_KERNEL_SL) KF_P2P(0);
-        else if (P.kernel == KIFMM_KERNEL_DL) KF_P2P(1);
-        else KF_P2P(2);
-#undef KF_P2P
-        }
+    if (!near_overlap) {
+        KF_TRY(mark(9));
+        if (P.n_tleaf) KF_TRY(near_field(s, B.res));
+        KF_TRY(mark(10));
+    }
+    if (near_overlap) {
+        // join both streams on the caller's, then add the far field into the near sums
+        KF_CHECK_CUDA(cudaEventRecord(P.ev_far, s));
+        s = s_in;
+        KF_CHECK_CUDA(cudaStreamWaitEvent(s, P.ev_far, 0));
+        KF_CHECK_CUDA(cudaStreamWaitEvent(s, P.ev_join, 0));
+        k_add_far<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(T.same ? T.sperm.p : T.tperm.p,
+                                                              reinterpret_cast<const float*>(B.res), T.nt, out);
         KF_CHECK_LAUNCH();
         ++launches;
     }
@@ -1603,7 +1652,8 @@ extern "C" int kifmm_fmm_matvec_graph(kifmm_plan plan, const double* q, double* 
             cudaGetLastError();
             return rc;
         }
-        cudaError_t ie = cudaGraphInstantiate(&P.gexec, g, 0);
+        // keep the stream priorities of the overlapped near and far fields
+        cudaError_t ie = cudaGraphInstantiate(&P.gexec, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) {
             P.gexec = nullptr;
@@ -1648,17 +1698,21 @@ extern "C" int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases) {
     Plan& P = plan->P;
     if (phases) {
         // mean over the matvecs recorded since the last read:
-        // {gather, s2u, u2u, x, m2l, l2l, d2t, p2p, total}
-        constexpr int L = kPhaseEvents - 1;
+        // {gather, s2u, u2u, x, m2l, l2l, d2t, p2p, total}.  p2p is the near field's own
+        // time (events 9, 10), which overlaps the far-field phases when it runs on its own
+        // stream; then [7, 8) is the join and the far-field add
+        constexpr int L = 8;
         for (int i = 0; i <= L; ++i) phases[i] = 0;
         for (int k = 0; k < P.slots_used; ++k) {
             const std::vector<cudaEvent_t>& e = P.ev_slots[k];
             KF_CHECK_CUDA(cudaEventSynchronize(e[L]));
             float ms;
-            for (int i = 0; i < L; ++i) {
+            for (int i = 0; i < L - 1; ++i) {
                 KF_CHECK_CUDA(cudaEventElapsedTime(&ms, e[i], e[i + 1]));
                 phases[i] += ms;
             }
+            KF_CHECK_CUDA(cudaEventElapsedTime(&ms, e[9], e[10]));
+            phases[L - 1] += ms;
             KF_CHECK_CUDA(cudaEventElapsedTime(&ms, e[0], e[L]));
             phases[L] += ms;
         }

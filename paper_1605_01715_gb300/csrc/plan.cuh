@@ -20,7 +20,9 @@ struct PairTiles {
 };
 
 constexpr int kPairTile = 64;
-constexpr int kPhaseEvents = 9;     // events per profiled matvec (8 phases + total)
+// events per profiled matvec: 0..8 bound the 8 phases on the matvec's stream (8 = end),
+// 9 and 10 bound the near field (on the near-field stream when it overlaps the far field)
+constexpr int kPhaseEvents = 11;
 
 // Device scratch of the boundary-integral operators and GMRES, kept between calls
 // (the Krylov basis stays resident for the next solve on the same plan).
@@ -111,6 +113,12 @@ struct Plan {
     // was captured for, and the private stream it was captured on
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    // mixed: after the gather the far field runs on a highest-priority stream and the
+    // near field on a lowest-priority one, so the near field's blocks fill the SMs the
+    // far field's many short launches leave idle; both join the caller's stream before
+    // the far-field sum is added
+    cudaStream_t near_stream = nullptr, far_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
     const double* g_q = nullptr;
     double* g_out = nullptr;
 
@@ -120,6 +128,11 @@ struct Plan {
                 if (e) cudaEventDestroy(e);
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (ev_far) cudaEventDestroy(ev_far);
+        if (near_stream) cudaStreamDestroy(near_stream);
+        if (far_stream) cudaStreamDestroy(far_stream);
     }
 };
 
