@@ -213,6 +213,9 @@ typedef struct {
                                          most 2048 sources of one target leaf)        */
     int32_t near_split_leaves;        /* mixed: target leaves spread over several
                                          units (their sums meet by FP64 atomics)      */
+    int32_t near_overlap;             /* 1: the near field runs on its own (lowest-
+                                         priority) stream beside the far field, so its
+                                         profiled phase time spans the overlap         */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);

@@ -55,7 +55,7 @@ class PlanStats(ctypes.Structure):
                 ("launches_per_matvec", ctypes.c_int32), ("rank_up", ctypes.c_int32),
                 ("rank_down", ctypes.c_int32), ("m2l_width", ctypes.c_int32),
                 ("m2l_rows", ctypes.c_int32), ("near_units", ctypes.c_int32),
-                ("near_split_leaves", ctypes.c_int32)]
+                ("near_split_leaves", ctypes.c_int32), ("near_overlap", ctypes.c_int32)]
 
 
 def _as_dict(st):

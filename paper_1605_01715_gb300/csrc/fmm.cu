@@ -1689,6 +1689,7 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->m2l_rows = P.fp64 ? P.Q : st->rank_down;
     st->near_units = P.n_p2p_units;
     st->near_split_leaves = P.n_p2p_split;
+    st->near_overlap = (!P.fp64 && P.near_stream && P.n_tleaf && P.max_trg_leaf <= kP2PWarpMaxLeaf) ? 1 : 0;
     return KIFMM_OK;
 }
 
