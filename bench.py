@@ -291,7 +291,7 @@ def run_kifmm(args):
     tst = tree.stats()
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "n_targets": n, "kernel": wl["kernel"], "p": p,
                        "q_points": st["q_points"], "max_leaf": max_leaf, "precision": args.precision,
@@ -369,7 +369,7 @@ def run_serve(args):
     line = {"metric": "serving throughput (solve requests/s) with p50/p99 latency", "value": top["throughput_req_s"],
             "unit": "requests/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
             "ms_per_step": 1e3 / max(top["throughput_req_s"], 1e-9), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": "serve_stream", "sizes": "log-uniform 2k-500k", "p": args.serve_p,
                        "precision": args.precision, "mem_budget_gb": args.serve_mem_gb,
                        "kinds": "half polarization GMRES(50) tol 1e-6, half demag phi2"},
@@ -457,7 +457,7 @@ def roofline(phases, st, tst, args):
     items = {k: v for k, v in phases.items() if k != "total" and not (k == "p2p" and st.get("near_overlap"))}
     dom = max(items, key=items.get)
     t = items[dom] * 1e-3
-    mixed = args.precision == "mixed"
+    mixed = args.precision != "fp64"
     if dom in ("m2l", "u2u", "l2l"):
         pairs = {"m2l": st["m2l_pairs"], "u2u": st["u2u_pairs"], "l2l": st["l2l_pairs"]}[dom]
         # algorithmic: one R x W operator per pair; R = W = Q in FP64; mixed, every
@@ -500,7 +500,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="kifmm", choices=["kifmm", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_cn", "fp64"],
+                    help="mixed_cn: mixed with the compensated DL/ADL near field")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--max-leaf", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=8192)

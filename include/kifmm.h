@@ -52,6 +52,13 @@ extern "C" {
 
 #define KIFMM_PREC_FP64  0   /* every step in FP64 (the plain form)                        */
 #define KIFMM_PREC_MIXED 1   /* FP32 near field and translations, FP64 set-up and output   */
+#define KIFMM_PREC_MIXED_CN 2 /* as MIXED, with the double- and adjoint-double-layer near
+                                 field compensated: positions as FP32 hi + lo pairs, the
+                                 n.(x - y) products and sums error-free (FMA two-products,
+                                 two-sums).  On curved surfaces the plain FP32 form loses
+                                 digits there to cancellation between close neighbours.
+                                 Target leaves above 64 targets use the plain FP32 block
+                                 kernel.                                                  */
 
 typedef struct kifmm_tree_s* kifmm_tree;
 typedef struct kifmm_plan_s* kifmm_plan;
@@ -166,7 +173,7 @@ int kifmm_tree_destroy(kifmm_tree tree);
  * Eq. p2m, the "second method"); the adjoint target normal at evaluation.
  *   kernel      KIFMM_KERNEL_SL / DL / ADL.
  *   p           2..16.
- *   precision   KIFMM_PREC_FP64 or KIFMM_PREC_MIXED.
+ *   precision   KIFMM_PREC_FP64, KIFMM_PREC_MIXED or KIFMM_PREC_MIXED_CN.
  *   pinv_cutoff > 0 and < 1, or 0 for the default (1e-8 mixed, 1e-9 FP64).
  *   src_nrm     device 3*n_src SoA; required for DL, else ignored (may be NULL).
  *   trg_nrm     device 3*n_trg SoA; required for ADL, else ignored (may be NULL).

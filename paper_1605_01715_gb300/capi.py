@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkifmm.so")
 
 KERNELS = {"sl": 0, "dl": 1, "adl": 2}
-PRECISIONS = {"fp64": 0, "mixed": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_cn": 2}
 LISTS = {"U": 0, "V": 1, "W": 2, "X": 3}
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED",
           -5: "TIMEOUT", -6: "BREAKDOWN", -7: "UNSUPPORTED"}

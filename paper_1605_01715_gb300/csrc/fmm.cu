@@ -45,16 +45,20 @@ template <> struct RT<double> {
 };
 
 // ---------------------------------------------------------------- gather
+// lo: also write the rounding remainders of the dipoles (3 more rows, compensated
+// near field)
 template <typename Real>
 __global__ void k_gather_q(const double* __restrict__ q, const int64_t* __restrict__ perm, int64_t n,
-                           const double* __restrict__ snrm, Real* __restrict__ qs) {
+                           const double* __restrict__ snrm, Real* __restrict__ qs, bool lo) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double v = q[perm[i]];
     if (snrm) {  // dipole strengths q n_j, SoA
-        qs[i] = (Real)(v * snrm[i]);
-        qs[n + i] = (Real)(v * snrm[n + i]);
-        qs[2 * n + i] = (Real)(v * snrm[2 * n + i]);
+        for (int d = 0; d < 3; ++d) {
+            const double pd = v * snrm[d * n + i];
+            qs[d * n + i] = (Real)pd;
+            if (lo) qs[(3 + d) * n + i] = (Real)(pd - (double)(Real)pd);
+        }
     } else {
         qs[i] = (Real)v;
     }
@@ -684,15 +688,187 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
     }
 }
 
-template <int KIND>
+// ---- compensated near field (KIFMM_PREC_MIXED_CN), double and adjoint double layer.
+// On a curved surface n.(x - y) between close neighbours is about |x - y|^2 / (2 R),
+// far below |x - y|: plain FP32 loses the digits to cancellation (positions rounded to
+// 2^-24 of the leaf size, normals or dipoles to 2^-24).  Here every offset from the
+// leaf centre is a pair hi + lo with hi on a grid of 2^(e-19) (e: the leaf half-width's
+// binade), so the difference of two hi parts is exact in FP32; normals and dipoles are
+// hi + lo pairs too; the dot product of the hi parts is formed with error-free
+// transformations (FMA two-products, two-sums) and the cross terms are added in FP32.
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
+
+// a . b (3-vectors, packed pairs) as hi + lo
+__device__ __forceinline__ void dot3_ef(float2 ax, float2 ay, float2 az, float2 bx, float2 by, float2 bz,
+                                        float2& hi, float2& lo) {
+    const float2 p1 = __fmul2_rn(ax, bx), p2 = __fmul2_rn(ay, by), p3 = __fmul2_rn(az, bz);
+    const float2 e1 = __ffma2_rn(ax, bx, f2neg(p1)), e2 = __ffma2_rn(ay, by, f2neg(p2)),
+                 e3 = __ffma2_rn(az, bz, f2neg(p3));
+    const float2 s = __fadd2_rn(p1, p2), z = __fadd2_rn(s, f2neg(p1));
+    const float2 t1 = __fadd2_rn(__fadd2_rn(p1, f2neg(__fadd2_rn(s, f2neg(z)))), __fadd2_rn(p2, f2neg(z)));
+    const float2 u = __fadd2_rn(s, p3), z2 = __fadd2_rn(u, f2neg(s));
+    const float2 t2 = __fadd2_rn(__fadd2_rn(s, f2neg(__fadd2_rn(u, f2neg(z2)))), __fadd2_rn(p3, f2neg(z2)));
+    hi = u;
+    lo = __fadd2_rn(__fadd2_rn(__fadd2_rn(e1, e2), __fadd2_rn(e3, t1)), t2);
+}
+
+// x rounded to the grid of quantum g (|x| < 2^22 g), by the magic-number sum
+__device__ __forceinline__ float grid_round(float x, float magic) { return __fsub_rn(__fadd_rn(x, magic), magic); }
+
+// A source's offset from the leaf centre as hi (on the grid) + lo, from its FP32
+// hi/lo coordinates and the centre's.
+__device__ __forceinline__ void src_offset_ef(float ph, float pl, float ch, float cl, float magic, float& oh,
+                                              float& ol) {
+    const float a = __fsub_rn(ph, ch);                         // two-sum of ph and -ch
+    const float bb = __fsub_rn(a, ph);
+    const float err = __fadd_rn(__fsub_rn(ph, __fsub_rn(a, bb)), __fsub_rn(-ch, bb));
+    const float rest = __fadd_rn(__fsub_rn(pl, cl), err);
+    oh = grid_round(a, magic);
+    ol = __fadd_rn(__fsub_rn(a, oh), rest);
+}
+
+template <int KIND, int T>
+__device__ __forceinline__ void p2p_pass_cn(int lane, int e0, int e1, const longlong2* __restrict__ ranges,
+                                            int flags, double cx, double cy, double cz, float hbox,
+                                            const float* __restrict__ sxf, int64_t ns,
+                                            const double* __restrict__ txyz, int64_t nt,
+                                            const float* __restrict__ qs, const double* __restrict__ tnrm_d,
+                                            const float* __restrict__ res, const int64_t* __restrict__ tperm,
+                                            double* __restrict__ out, int64_t t0, int64_t te, float4* st) {
+    static_assert(KIND == 1 || KIND == 2, "compensated form for the double layers");
+    const int g = lane >> 3, r = lane & 7;
+    constexpr int TP = (T + 1) / 2;
+    const double quantum = ldexp(1.0, ilogbf(hbox) - 19);
+    const float magic = (float)(1.5 * 8388608.0 * quantum);    // 1.5 * 2^23 * quantum
+    float2 thx[TP], thy[TP], thz[TP], tlx[TP], tly[TP], tlz[TP], acc[TP];
+    float2 nhx[TP], nhy[TP], nhz[TP], nlx[TP], nly[TP], nlz[TP];
+#pragma unroll
+    for (int m = 0; m < TP; ++m) {
+        float c[2][12];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int64_t t = t0 + 8 * (2 * m + h) + r;
+            t = t < te ? t : t0;                  // padding slots evaluate a real target, unused
+            const double o[3] = {txyz[t] - cx, txyz[nt + t] - cy, txyz[2 * nt + t] - cz};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double oh = rint(o[d] / quantum) * quantum;
+                c[h][d] = (float)oh;
+                c[h][3 + d] = (float)(o[d] - oh);
+                if (KIND == 2) {
+                    const double nd = tnrm_d[d * nt + t];
+                    c[h][6 + d] = (float)nd;
+                    c[h][9 + d] = (float)(nd - (double)(float)nd);
+                }
+            }
+        }
+        thx[m] = make_float2(c[0][0], c[1][0]);
+        thy[m] = make_float2(c[0][1], c[1][1]);
+        thz[m] = make_float2(c[0][2], c[1][2]);
+        tlx[m] = make_float2(c[0][3], c[1][3]);
+        tly[m] = make_float2(c[0][4], c[1][4]);
+        tlz[m] = make_float2(c[0][5], c[1][5]);
+        if (KIND == 2) {
+            nhx[m] = make_float2(c[0][6], c[1][6]);
+            nhy[m] = make_float2(c[0][7], c[1][7]);
+            nhz[m] = make_float2(c[0][8], c[1][8]);
+            nlx[m] = make_float2(c[0][9], c[1][9]);
+            nly[m] = make_float2(c[0][10], c[1][10]);
+            nlz[m] = make_float2(c[0][11], c[1][11]);
+        }
+        acc[m] = make_float2(0.f, 0.f);
+    }
+    const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
+    const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
+    const float d2 = (float)(kDelta * kDelta);
+    int e = e0;
+    int64_t j0 = 0, se = 0;
+    if (e < e1) {
+        j0 = ranges[e].x;
+        se = ranges[e].y;
+    }
+    while (e < e1) {
+        const int64_t j = j0 + lane;
+        if (j < se) {
+            float oh[3], ol[3];
+            src_offset_ef(sxf[j], sxf[3 * ns + j], chx, clx, magic, oh[0], ol[0]);
+            src_offset_ef(sxf[ns + j], sxf[4 * ns + j], chy, cly, magic, oh[1], ol[1]);
+            src_offset_ef(sxf[2 * ns + j], sxf[5 * ns + j], chz, clz, magic, oh[2], ol[2]);
+            // A: (offset hi, q or dipole hi x), B: (offset lo, dipole hi y), C: (dipole hi z, dipole lo)
+            st[lane] = make_float4(oh[0], oh[1], oh[2], qs[j]);
+            if (KIND == 1) {
+                st[32 + lane] = make_float4(ol[0], ol[1], ol[2], qs[ns + j]);
+                st[64 + lane] = make_float4(qs[2 * ns + j], qs[3 * ns + j], qs[4 * ns + j], qs[5 * ns + j]);
+            } else {
+                st[32 + lane] = make_float4(ol[0], ol[1], ol[2], 0.f);
+            }
+        }
+        const int cnt = (int)(se - j0 < 32 ? se - j0 : 32);
+        j0 += 32;
+        while (j0 >= se && ++e < e1) {
+            j0 = ranges[e].x;
+            se = ranges[e].y;
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int jj = g; jj < cnt; jj += 4) {
+            const float4 sa = st[jj], sb = st[32 + jj];
+            float4 sc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (KIND == 1) sc = st[64 + jj];
+#pragma unroll
+            for (int m = 0; m < TP; ++m) {
+                // d = t - s as hi (exact: both on the grid) + lo
+                const float2 dhx = __fadd2_rn(thx[m], f2b(-sa.x)), dhy = __fadd2_rn(thy[m], f2b(-sa.y)),
+                             dhz = __fadd2_rn(thz[m], f2b(-sa.z));
+                const float2 dlx = __fadd2_rn(tlx[m], f2b(-sb.x)), dly = __fadd2_rn(tly[m], f2b(-sb.y)),
+                             dlz = __fadd2_rn(tlz[m], f2b(-sb.z));
+                const float2 dx = __fadd2_rn(dhx, dlx), dy = __fadd2_rn(dhy, dly), dz = __fadd2_rn(dhz, dlz);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                const float2 i3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+                float2 hi, lo, corr;
+                if (KIND == 1) {                  // (q n_j) . d, dipole hi (sa.w, sb.w, sc.x), lo (sc.y..w)
+                    dot3_ef(f2b(sa.w), f2b(sb.w), f2b(sc.x), dhx, dhy, dhz, hi, lo);
+                    corr = __ffma2_rn(f2b(sa.w), dlx, __ffma2_rn(f2b(sb.w), dly, __fmul2_rn(f2b(sc.x), dlz)));
+                    corr = __ffma2_rn(f2b(sc.y), dhx, __ffma2_rn(f2b(sc.z), dhy, __ffma2_rn(f2b(sc.w), dhz, corr)));
+                } else {                          // n_i . d, normal hi / lo per target
+                    dot3_ef(nhx[m], nhy[m], nhz[m], dhx, dhy, dhz, hi, lo);
+                    corr = __ffma2_rn(nhx[m], dlx, __ffma2_rn(nhy[m], dly, __fmul2_rn(nhz[m], dlz)));
+                    corr = __ffma2_rn(nlx[m], dhx, __ffma2_rn(nly[m], dhy, __ffma2_rn(nlz[m], dhz, corr)));
+                }
+                float2 v = __fadd2_rn(hi, __fadd2_rn(lo, corr));
+                v = KIND == 1 ? __fmul2_rn(v, i3) : __fmul2_rn(__fmul2_rn(f2b(sa.w), v), i3);
+                v.x = r2.x >= d2 ? v.x : 0.f;
+                v.y = r2.y >= d2 ? v.y : 0.f;
+                acc[m] = __fadd2_rn(acc[m], v);
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        float v = (i & 1) ? acc[i >> 1].y : acc[i >> 1].x;
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        const int64_t t = t0 + 8 * i + r;
+        if (g == 0 && t < te) {
+            const float far = res ? res[t] : 0.f;
+            if (!(flags & 2)) out[tperm[t]] = (double)(v + far);
+            else atomicAdd(out + tperm[t], (double)((flags & 1) ? v + far : v));
+        }
+    }
+}
+
+template <int KIND, bool CN>
 __global__ void __launch_bounds__(32 * kP2PWarps)
 k_p2p_warp(const int* __restrict__ leaves, int nunits, const int4* __restrict__ units,
            const longlong2* __restrict__ ranges, const int64_t* __restrict__ rng, const double* __restrict__ ctr,
            const float* __restrict__ sxf,
            int64_t ns, const double* __restrict__ txyz, int64_t nt, const float* __restrict__ qs,
-           const float* __restrict__ tnrm, const float* __restrict__ res, const int64_t* __restrict__ tperm,
-           double* __restrict__ out) {
-    __shared__ float4 stage[kP2PWarps][KIND == 1 ? 64 : 32];
+           const float* __restrict__ tnrm, const double* __restrict__ tnrm_d, const float4* __restrict__ bcf,
+           const float* __restrict__ res, const int64_t* __restrict__ tperm, double* __restrict__ out) {
+    __shared__ float4 stage[kP2PWarps][CN ? (KIND == 1 ? 96 : 64) : (KIND == 1 ? 64 : 32)];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ui = blockIdx.x * kP2PWarps + warp;
     if (ui >= nunits) return;                     // whole warp; no block-wide barrier below
@@ -702,14 +878,22 @@ k_p2p_warp(const int* __restrict__ leaves, int nunits, const int4* __restrict__ 
     const int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
     const int e0 = u.y, e1 = u.z;
     float4* st = stage[warp];
-    for (int64_t t0 = tb; t0 < te; t0 += 64) {
-        const int n = (int)(te - t0 < 64 ? te - t0 : 64);
+    // passes of up to 8 kMaxT targets (the compensated form keeps four per lane)
+    constexpr int kMaxT = CN ? 4 : 8;
+    for (int64_t t0 = tb; t0 < te; t0 += 8 * kMaxT) {
+        const int n = (int)(te - t0 < 8 * kMaxT ? te - t0 : 8 * kMaxT);
         const int64_t tend = t0 + n;
         switch ((n + 7) >> 3) {
-#define KF_PASS(TT)                                                                                  \
-    case TT:                                                                                         \
-        p2p_pass<KIND, TT>(lane, e0, e1, ranges, u.w, cx, cy, cz, sxf, ns, txyz, nt, qs, tnrm, res, tperm, \
-                           out, t0, tend, st);                                                       \
+#define KF_PASS(TT)                                                                                        \
+    case TT:                                                                                               \
+        if constexpr (TT <= kMaxT) {                                                                       \
+            if constexpr (CN)                                                                              \
+                p2p_pass_cn<KIND == 0 ? 1 : KIND, TT>(lane, e0, e1, ranges, u.w, cx, cy, cz, bcf[3 * b].w, sxf, \
+                                                      ns, txyz, nt, qs, tnrm_d, res, tperm, out, t0, tend, st); \
+            else                                                                                           \
+                p2p_pass<KIND, TT>(lane, e0, e1, ranges, u.w, cx, cy, cz, sxf, ns, txyz, nt, qs, tnrm, res,  \
+                                   tperm, out, t0, tend, st);                                              \
+        }                                                                                                  \
         break;
             KF_PASS(1) KF_PASS(2) KF_PASS(3) KF_PASS(4) KF_PASS(5) KF_PASS(6) KF_PASS(7) KF_PASS(8)
 #undef KF_PASS
@@ -1095,6 +1279,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     P.Q = h.Q;
     P.Qp = (h.Q + 15) / 16 * 16;
     P.fp64 = P.prec == KIFMM_PREC_FP64;
+    P.cnear = P.prec == KIFMM_PREC_MIXED_CN && P.kernel != KIFMM_KERNEL_SL;
     KF_TRY(P.err.alloc(1));
     KF_CHECK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), s));
 
@@ -1321,7 +1506,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_TRY(build_d2t<float>(P, h, true, P.ops->Kd, tleaf_of, P.d2t_f.p, s));
         // (no FP32 check potentials: S2U and X write the projections' split inputs)
         KF_TRY(P.res_f.alloc(T.nt));
-        KF_TRY(P.q_f.alloc(3 * T.ns));
+        KF_TRY(P.q_f.alloc((P.cnear ? 6 : 3) * T.ns));
     }
     KF_CHECK_CUDA(cudaStreamSynchronize(s));
 
@@ -1429,13 +1614,18 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
                 KF_CHECK_CUDA(cudaMemsetAsync(out, 0, (size_t)T.nt * sizeof(double), ns));
                 ++launches;
             }
-#define KF_P2PW(KIND)                                                                                       \
-    k_p2p_warp<KIND><<<grid, 32 * kP2PWarps, 0, ns>>>(P.tleaf.p, P.n_p2p_units, P.p2p_units.p, P.p2p_ranges.p, \
-                                                      T.rng.p, T.ctr.p, P.sxf.p, T.ns, txyz, T.nt, B.q,      \
-                                                      B.tnrm, res, tperm, out)
-            if (P.kernel == KIFMM_KERNEL_SL) KF_P2PW(0);
-            else if (P.kernel == KIFMM_KERNEL_DL) KF_P2PW(1);
-            else KF_P2PW(2);
+#define KF_P2PW(KIND, CN)                                                                                    \
+    k_p2p_warp<KIND, CN><<<grid, 32 * kP2PWarps, 0, ns>>>(P.tleaf.p, P.n_p2p_units, P.p2p_units.p,           \
+                                                          P.p2p_ranges.p, T.rng.p, T.ctr.p, P.sxf.p, T.ns, txyz, \
+                                                          T.nt, B.q, B.tnrm, P.tnrm_d.p, P.bcf.p, res, tperm, out)
+            if (P.kernel == KIFMM_KERNEL_SL) KF_P2PW(0, false);
+            else if (P.kernel == KIFMM_KERNEL_DL) {
+                if (P.cnear) KF_P2PW(1, true);
+                else KF_P2PW(1, false);
+            } else {
+                if (P.cnear) KF_P2PW(2, true);
+                else KF_P2PW(2, false);
+            }
 #undef KF_P2PW
             done = true;
           }
@@ -1462,7 +1652,8 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
                               P.max_trg_leaf <= kP2PWarpMaxLeaf;
     const bool dl = P.kernel == KIFMM_KERNEL_DL;
     KF_TRY(mark(0));
-    k_gather_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, T.sperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q);
+    k_gather_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, T.sperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q,
+                                                       P.cnear && dl);
     KF_CHECK_LAUNCH();
     ++launches;
     const cudaStream_t s_in = s;                  // the caller's stream
@@ -1590,7 +1781,8 @@ extern "C" int kifmm_fmm_setup(kifmm_tree tree, int kernel, int p, int precision
     KF_ARG(tree != nullptr, "tree is NULL");
     KF_ARG(kernel >= KIFMM_KERNEL_SL && kernel <= KIFMM_KERNEL_ADL, "unknown kernel");
     KF_ARG(p >= 2 && p <= 16, "p must be in [2, 16]");
-    KF_ARG(precision == KIFMM_PREC_FP64 || precision == KIFMM_PREC_MIXED, "unknown precision");
+    KF_ARG(precision == KIFMM_PREC_FP64 || precision == KIFMM_PREC_MIXED || precision == KIFMM_PREC_MIXED_CN,
+           "unknown precision");
     KF_ARG(pinv_cutoff == 0.0 || (pinv_cutoff > 0.0 && pinv_cutoff < 1.0), "pinv_cutoff must be 0 or in (0,1)");
     KF_ARG(kernel != KIFMM_KERNEL_DL || src_nrm != nullptr, "DL needs src_nrm");
     KF_ARG(kernel != KIFMM_KERNEL_ADL || trg_nrm != nullptr, "ADL needs trg_nrm");

@@ -85,6 +85,7 @@ struct Plan {
                                           // end range, flags: 1 first of its leaf, 2 leaf split)
     DBuf<longlong2> p2p_ranges;           // mixed: source index ranges of the units
     int n_p2p_units = 0, n_p2p_split = 0;
+    bool cnear = false;                   // mixed: compensated DL/ADL near field
     bool p2p_multi = false;               // some leaf spans several units
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
