@@ -553,6 +553,7 @@ __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ of
 // leaf with several units adds into its outputs with FP64 atomics (the output is
 // zeroed first); the first unit also adds the far field.
 constexpr int kP2PWarps = 8;
+constexpr long long kFarRange = 1LL << 62;   // range flag: W/X sources, not adjacent to the leaf
 constexpr int kP2PUnitSrc = 2048;
 // Larger target leaves go to the block kernel (a thread per target, sources staged once
 // per leaf): at leaf 128 on the 64-sphere pack it takes 2.56 ms against 4.04 ms for two
@@ -606,7 +607,7 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
     int e = e0;
     int64_t j0 = 0, se = 0;
     if (e < e1) {
-        j0 = ranges[e].x;
+        j0 = ranges[e].x & ~kFarRange;
         se = ranges[e].y;
     }
     float ph[3], pl[3], pq[3];
@@ -637,7 +638,7 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
         // advance to the next chunk and prefetch it
         j0 += 32;
         while (j0 >= se && ++e < e1) {
-            j0 = ranges[e].x;
+            j0 = ranges[e].x & ~kFarRange;
             se = ranges[e].y;
         }
         __syncwarp();
@@ -696,6 +697,8 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
 // binade), so the difference of two hi parts is exact in FP32; normals and dipoles are
 // hi + lo pairs too; the dot product of the hi parts is formed with error-free
 // transformations (FMA two-products, two-sums) and the cross terms are added in FP32.
+// W- and X-list sources (ranges flagged kFarRange) are not adjacent to the leaf, so
+// there the plain FP32 evaluation (of the same hi + lo offsets) is accurate enough.
 __device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
 
@@ -784,8 +787,10 @@ __device__ __forceinline__ void p2p_pass_cn(int lane, int e0, int e1, const long
     const float d2 = (float)(kDelta * kDelta);
     int e = e0;
     int64_t j0 = 0, se = 0;
+    bool far = false;
     if (e < e1) {
-        j0 = ranges[e].x;
+        j0 = ranges[e].x & ~kFarRange;
+        far = (ranges[e].x & kFarRange) != 0;
         se = ranges[e].y;
     }
     while (e < e1) {
@@ -805,9 +810,11 @@ __device__ __forceinline__ void p2p_pass_cn(int lane, int e0, int e1, const long
             }
         }
         const int cnt = (int)(se - j0 < 32 ? se - j0 : 32);
+        const bool chunk_far = far;               // a chunk lies within one range
         j0 += 32;
         while (j0 >= se && ++e < e1) {
-            j0 = ranges[e].x;
+            j0 = ranges[e].x & ~kFarRange;
+            far = (ranges[e].x & kFarRange) != 0;
             se = ranges[e].y;
         }
         __syncwarp();
@@ -827,6 +834,16 @@ __device__ __forceinline__ void p2p_pass_cn(int lane, int e0, int e1, const long
                 const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
                 const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
                 const float2 i3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+                if (chunk_far) {                  // W/X sources: no cancellation worth the cost
+                    const float2 num = KIND == 1
+                        ? __ffma2_rn(f2b(sc.x), dz, __ffma2_rn(f2b(sb.w), dy, __fmul2_rn(f2b(sa.w), dx)))
+                        : __fmul2_rn(f2b(sa.w), __ffma2_rn(nhz[m], dz, __ffma2_rn(nhy[m], dy, __fmul2_rn(nhx[m], dx))));
+                    float2 v = __fmul2_rn(num, i3);
+                    v.x = r2.x >= d2 ? v.x : 0.f;
+                    v.y = r2.y >= d2 ? v.y : 0.f;
+                    acc[m] = __fadd2_rn(acc[m], v);
+                    continue;
+                }
                 float2 hi, lo, corr;
                 if (KIND == 1) {                  // (q n_j) . d, dipole hi (sa.w, sb.w, sc.x), lo (sc.y..w)
                     dot3_ef(f2b(sa.w), f2b(sb.w), f2b(sc.x), dhx, dhy, dhz, hi, lo);
@@ -1383,12 +1400,14 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
             const size_t u0 = units.size();
             int r0 = (int)ranges.size();
             int64_t cnt = 0;
+            const int n_u = T.h_u_off[b + 1] - T.h_u_off[b];   // the U list comes first
             for (int k = p2p_off[li]; k < p2p_off[li + 1]; ++k) {
                 const int a = p2p_idx[k];
+                const long long far = k - p2p_off[li] >= n_u ? kFarRange : 0;
                 int64_t j0 = T.h_rng[4 * a], j1 = T.h_rng[4 * a + 1];
                 while (j0 < j1) {
                     const int64_t take = std::min<int64_t>(j1 - j0, kP2PUnitSrc - cnt);
-                    ranges.push_back(make_longlong2(j0, j0 + take));
+                    ranges.push_back(make_longlong2(j0 | far, j0 + take));
                     cnt += take;
                     j0 += take;
                     if (cnt == kP2PUnitSrc) {
