@@ -1403,7 +1403,18 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
             const int n_u = T.h_u_off[b + 1] - T.h_u_off[b];   // the U list comes first
             for (int k = p2p_off[li]; k < p2p_off[li + 1]; ++k) {
                 const int a = p2p_idx[k];
-                const long long far = k - p2p_off[li] >= n_u ? kFarRange : 0;
+                // W- and X-list boxes are not adjacent to the leaf; flagged when their
+                // max-norm gap also exceeds twice the tolerance radius
+                long long far = 0;
+                if (k - p2p_off[li] >= n_u) {
+                    const double ha = std::ldexp(T.root_h, -T.h_lvl[a]), hb = std::ldexp(T.root_h, -T.h_lvl[b]);
+                    double dc = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double ca = (2 * T.h_coord[3 * a + d] + 1) * ha, cb = (2 * T.h_coord[3 * b + d] + 1) * hb;
+                        dc = std::max(dc, std::fabs(ca - cb));
+                    }
+                    if (dc - ha - hb > 2.0 * kDelta) far = kFarRange;
+                }
                 int64_t j0 = T.h_rng[4 * a], j1 = T.h_rng[4 * a + 1];
                 while (j0 < j1) {
                     const int64_t take = std::min<int64_t>(j1 - j0, kP2PUnitSrc - cnt);
