@@ -227,9 +227,10 @@ def run_kifmm(args):
     n = m.n
     out = torch.empty(n, dtype=torch.float64, device=device)
     stream = torch.cuda.current_stream()
-    # a batch of instances replays one captured graph per matvec; single instances
-    # launch directly, with the library's phase events inside the timed region
-    use_graph = inst is not None or args.graph
+    # every timed matvec replays the captured graph (kifmm_fmm_matvec_graph: one launch
+    # on the host; the phase breakdown comes from direct launches after the timed region)
+    # unless --no-graph, which launches each matvec's kernels directly
+    use_graph = inst is not None or not args.no_graph
     matvec = plan.matvec_graph if use_graph else plan.matvec
 
     for _ in range(args.warmup):
@@ -515,7 +516,9 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batch workloads: take p / leaf from the workload")
-    ap.add_argument("--graph", action="store_true", help="time captured-graph matvecs (always for batches)")
+    ap.add_argument("--graph", action="store_true", help="(the default) time captured-graph matvecs")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="single instance: launch each matvec's kernels directly (batches always replay a graph)")
     ap.add_argument("--serve", action="store_true", help="serving-stream sweep instead of the matvec bench")
     ap.add_argument("--serve-rates", default="10,100,1000")
     ap.add_argument("--serve-requests", type=int, default=48)
