@@ -457,13 +457,30 @@ k_d2t(const int* __restrict__ leaves, const int64_t* __restrict__ rng, const Rea
     __syncthreads();
     int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int64_t t = tb + warp; t < te; t += blockDim.x / 32) {
-        const Real* row = T + (size_t)t * Qp;
-        Real s = 0;
-        for (int k = lane; k < Qp; k += 32) s += row[k] * ds[k];
+    if constexpr (std::is_same<Real, float>::value) {
+        // FP32 rows (Qp a multiple of 16): 16-byte streaming loads, read once
+        const float4* ds4 = reinterpret_cast<const float4*>(ds);
+        for (int64_t t = tb + warp; t < te; t += blockDim.x / 32) {
+            const float4* row = reinterpret_cast<const float4*>(T + (size_t)t * Qp);
+            float s = 0.f;
+#pragma unroll 2
+            for (int k = lane; k < Qp / 4; k += 32) {
+                const float4 a = __ldcs(row + k), c = ds4[k];
+                s = fmaf(a.x, c.x, fmaf(a.y, c.y, fmaf(a.z, c.z, fmaf(a.w, c.w, s))));
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) res[t] = s;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) res[t] = s;
+        }
+    } else {
+        for (int64_t t = tb + warp; t < te; t += blockDim.x / 32) {
+            const Real* row = T + (size_t)t * Qp;
+            Real s = 0;
+            for (int k = lane; k < Qp; k += 32) s += row[k] * ds[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) res[t] = s;
+        }
     }
 }
 

@@ -147,12 +147,15 @@ def test_factored_m2l_widths():
         assert (fp["rank_up"], fp["rank_down"]) == (mx["rank_up"], mx["rank_down"])
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed_cn"])
 @pytest.mark.parametrize("kernel,tol", [("sl", 1e-6), ("dl", 3e-6), ("adl", 4e-6)])
-def test_near_field_units_split_heavy_leaves(kernel, tol):
+def test_near_field_units_split_heavy_leaves(kernel, tol, prec):
     """A 5,120-point sphere of radius 0.03 beside a unit sphere of the same point count:
     leaves of the large sphere next to the small one take thousands of W- and X-list
     sources, so the FP32 near field splits them over several work units whose sums
-    meet by atomics.  The result still matches the oracle."""
+    meet by atomics.  The result still matches the oracle, also in the compensated form
+    and replayed from a captured graph (the zeroing of the outputs and the units'
+    atomics run inside it)."""
     from paper_1605_01715_gb300 import Plan, Tree
     m = synth.pack_mesh(np.array([[0.0, 0.0, 0.0], [1.04, 0.0, 0.0]]), np.array([1.0, 0.03]), 16)
     h = quadrature_points(m.tri, m.sph)
@@ -160,16 +163,21 @@ def test_near_field_units_split_heavy_leaves(kernel, tol):
     sig = synth.uniform_density(m.n, 23)
     ref = oracle.direct(kernel, h[0], h[0], sig * h[1], src_nrm=h[2] if kernel == "dl" else None,
                         trg_nrm=h[2] if kernel == "adl" else None)
-    plan = Plan(Tree(xyz, max_leaf=32), kernel=kernel, p=10, precision="mixed", src_nrm=nrm, trg_nrm=nrm)
+    plan = Plan(Tree(xyz, max_leaf=32), kernel=kernel, p=10, precision=prec, src_nrm=nrm, trg_nrm=nrm)
     st = plan.stats()
     assert st["near_split_leaves"] > 0 and st["near_units"] > st["near_split_leaves"]
     q = torch.from_numpy(sig).to(DEV) * w
-    out = plan.matvec(q).cpu().numpy()
+    direct = plan.matvec(q)
+    out = direct.cpu().numpy()
+    graph = torch.full_like(direct, float("nan"))
+    plan.matvec_graph(q, graph)
+    torch.cuda.synchronize()
     plan.check()
     err = rel(out, ref)
-    print("heavy-leaf pair %s mixed p=10 rel-L2 %.3e, %d units, %d split leaves"
-          % (kernel, err, st["near_units"], st["near_split_leaves"]))
+    print("heavy-leaf pair %s %s p=10 rel-L2 %.3e, %d units, %d split leaves"
+          % (kernel, prec, err, st["near_units"], st["near_split_leaves"]))
     assert err < tol
+    assert rel(graph.cpu().numpy(), out) < 1e-6
 
 
 @pytest.mark.parametrize("max_leaf", [1, 7, 200])
