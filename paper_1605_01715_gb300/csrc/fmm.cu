@@ -1704,14 +1704,19 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_CHECK_LAUNCH();
     ++launches;
     const cudaStream_t s_in = s;                  // the caller's stream
-    if (near_overlap) {
-        KF_CHECK_CUDA(cudaEventRecord(P.ev_fork, s));
+    // the near field on its stream, enqueued once the far field's first kernel is (so
+    // that kernel's blocks, not the near field's, take the SMs first)
+    auto fork_near = [&]() -> int {
         KF_CHECK_CUDA(cudaStreamWaitEvent(P.near_stream, P.ev_fork, 0));
-        KF_CHECK_CUDA(cudaStreamWaitEvent(P.far_stream, P.ev_fork, 0));
         KF_TRY(mark(9, P.near_stream));
         KF_TRY(near_field(P.near_stream, nullptr));
         KF_TRY(mark(10, P.near_stream));
         KF_CHECK_CUDA(cudaEventRecord(P.ev_join, P.near_stream));
+        return KIFMM_OK;
+    };
+    if (near_overlap) {
+        KF_CHECK_CUDA(cudaEventRecord(P.ev_fork, s));
+        KF_CHECK_CUDA(cudaStreamWaitEvent(P.far_stream, P.ev_fork, 0));
         s = P.far_stream;                         // the far-field phases below
     }
     constexpr bool mixed_form = std::is_same<Real, float>::value;
@@ -1742,6 +1747,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
                                  B.u, s));
         ++launches;
     }
+    if (near_overlap) KF_TRY(fork_near());
     KF_TRY(mark(2));
     // mixed: the leaves' projections; U2U, deepest parents first
     if constexpr (mixed) KF_TRY(project(P, 3, P.proj_up, up, s, launches));
