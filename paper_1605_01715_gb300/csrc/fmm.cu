@@ -314,11 +314,11 @@ int launch_surf(const Plan& P, const Tree& T, bool dl, int nbox, const int* boxe
 #define KF_SURF(NP)                                                                                              \
     case 2 * NP:                                                                                                 \
         k_surf_f<false, NP><<<nbox, kSurfThreadsF, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, \
-                                                          q, surf, P.Q, P.Qp, P.vin_h.p, P.vin_l.p, P.bexp.p);  \
+                                                          q, surf, P.Q, P.Qp, P.sin_h.p, P.sin_l.p, P.sexp.p);  \
         break;                                                                                                   \
     case 2 * NP + 1:                                                                                             \
         k_surf_f<true, NP><<<nbox, kSurfThreadsF, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns,  \
-                                                         q, surf, P.Q, P.Qp, P.vin_h.p, P.vin_l.p, P.bexp.p);   \
+                                                         q, surf, P.Q, P.Qp, P.sin_h.p, P.sin_l.p, P.sexp.p);   \
         break;
             KF_SURF(1) KF_SURF(2) KF_SURF(3) KF_SURF(4)
 #undef KF_SURF
@@ -1346,9 +1346,13 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     const int cap_up = P.fp64 ? kPairTile : tc_tile_pairs(P.ops->Ku);
     const int cap_dn = P.fp64 ? kPairTile : tc_tile_pairs(P.ops->Kd);
     if (!P.fp64) {
+        const int kz = std::max(P.ops->Ku, P.ops->Kd);
         KF_TRY(P.bexp.alloc(T.nbox));
-        KF_TRY(P.vin_h.alloc((size_t)T.nbox * P.Qp));
-        KF_TRY(P.vin_l.alloc((size_t)T.nbox * P.Qp));
+        KF_TRY(P.vin_h.alloc((size_t)T.nbox * kz));
+        KF_TRY(P.vin_l.alloc((size_t)T.nbox * kz));
+        KF_TRY(P.sexp.alloc(T.nbox));
+        KF_TRY(P.sin_h.alloc((size_t)T.nbox * P.Qp));
+        KF_TRY(P.sin_l.alloc((size_t)T.nbox * P.Qp));
         KF_TRY(P.sxf.alloc(6 * (size_t)T.ns));
         k_split_xyz<<<div_up(T.ns, 256), 256, 0, s>>>(T.sxyz.p, T.ns, P.sxf.p);
         KF_CHECK_LAUNCH();
@@ -1561,7 +1565,8 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     for (size_t b : {(size_t)P.ops->bytes(), P.d2t_d.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
                      P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
                      P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(),
-                     P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes(), P.sxf.bytes(), P.bcf.bytes(), P.zu.bytes(),
+                     P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes(), P.sexp.bytes(), P.sin_h.bytes(),
+                     P.sin_l.bytes(), P.sxf.bytes(), P.bcf.bytes(), P.zu.bytes(),
                      P.zd.bytes()})
         P.device_bytes += (int64_t)b;
     return KIFMM_OK;
@@ -1586,30 +1591,34 @@ int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, con
 template <>
 int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const float* ops,
                      const float* z, float* out, int b0, int b1, cudaStream_t s, int& launches) {
-    if (t1 <= t0) return KIFMM_OK;
     (void)ops;  // the tensor-core path reads the split tables through their TMA maps
     const OpTables& o = *P.ops;
     const bool in_up = which != kL2L, out_up = which == kU2U;
     const int K = in_up ? o.Ku : o.Kd, r = in_up ? o.ru : o.rd;
     const int Mr = out_up ? o.Ku : o.Kd, M = out_up ? o.ru : o.rd;
-    KF_TRY(tc_box_split(z, r, K, b0, b1, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
+    // split even without tiles: M2L reads the splits the upward pass leaves behind
+    if (b1 > b0) {
+        KF_TRY(tc_box_split(z, r, K, b0, b1, P.vin_h.p, P.vin_l.p, P.bexp.p, s));
+        ++launches;
+    }
+    if (t1 <= t0) return KIFMM_OK;
     const CUtensorMap* m = o.tmaps[which];
     KF_TRY(launch_pair_tc(which, m[0], m[1], o.texp[which], M, Mr, K, Mr, pt.tiles.p + t0, t1 - t0, pt.pin.p,
                           pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, out, P.err.p, s));
-    launches += 2;
+    ++launches;
     return KIFMM_OK;
 }
 
 // Mixed: projection of the full check potentials of the boxes in pt's tiles onto the up
-// (fam 3) or down (fam 4) basis, added into z.  Their split inputs (vin_h/vin_l, Qp per
-// box, exponents in bexp) were written by the surface kernel that computed them.
+// (fam 3) or down (fam 4) basis, added into z.  Their split inputs (sin_h/sin_l, Qp per
+// box, exponents in sexp) were written by the surface kernel that computed them.
 int project(const Plan& P, int fam, const PairTiles& pt, float* z, cudaStream_t s, int& launches) {
     if (pt.ntiles == 0) return KIFMM_OK;
     const OpTables& o = *P.ops;
     const int Mr = fam == 3 ? o.Ku : o.Kd, M = fam == 3 ? o.ru : o.rd;
     const CUtensorMap* m = o.tmaps[fam];
     KF_TRY(launch_pair_tc(3, m[0], m[1], o.texp[fam], M, Mr, P.Qp, Mr, pt.tiles.p, pt.ntiles, pt.pin.p,
-                          pt.pout.p, P.bexp.p, P.vin_h.p, P.vin_l.p, z, P.err.p, s));
+                          pt.pout.p, P.sexp.p, P.sin_h.p, P.sin_l.p, z, P.err.p, s));
     launches += 2;
     return KIFMM_OK;
 }
@@ -1764,8 +1773,9 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         if constexpr (mixed) KF_TRY(project(P, 4, P.proj_x, dn, s, launches));
     }
     KF_TRY(mark(4));
+    // the upward pass split levels 3 and deeper (mixed); level 2 is split here
     KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, up, dn, T.level_off[std::min(2, T.nlev)],
-                           T.nbox, s, launches));
+                           T.level_off[std::min(3, T.nlev)], s, launches));
     KF_TRY(mark(5));
     // L2L, coarsest children first (ADL in FP64: each level's potentials shifted to zero
     // mean first; the mixed tables carry that centring)

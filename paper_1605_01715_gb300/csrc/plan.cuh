@@ -63,12 +63,15 @@ struct Plan {
 
     // translation tables (shared, see OpTables), each Qp x Qp row-major; D2T rows in
     // the working precision; mixed: bexp the per-box input scales and vin_h/vin_l the
-    // scaled, split input vectors of a translation (nbox x Qp each)
+    // scaled, split projected vectors a translation reads (nbox x max(Ku, Kd) each), and
+    // sexp, sin_h/sin_l the same for the full check potentials the surface kernels
+    // write for the projections (nbox x Qp each).  Kept apart, so the splits of the
+    // upward pass survive the X list's surface pass and serve M2L as well.
     std::shared_ptr<OpTables> ops;
     DBuf<double> d2t_d;
     DBuf<float> d2t_f;
-    DBuf<int> bexp;
-    DBuf<__half> vin_h, vin_l;
+    DBuf<int> bexp, sexp;
+    DBuf<__half> vin_h, vin_l, sin_h, sin_l;
     DBuf<double> surf_d;            // Q x 3 unit surface
     DBuf<float> surf_f;
 
