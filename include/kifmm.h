@@ -223,9 +223,33 @@ typedef struct {
     int32_t near_overlap;             /* 1: the near field runs on its own (lowest-
                                          priority) stream beside the far field, so its
                                          profiled phase time spans the overlap         */
+    int32_t s2u_points;               /* up-check points S2U evaluates: q_points (FP64)
+                                         or the skeleton of kifmm_up_skeleton (mixed)  */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);
+
+/*
+ * Skeleton of the upward check surface of order p (host only: no device work).  The
+ * paper's S2U (Sec. III.A.2, the source-to-up-check step of the upward pass) evaluates
+ * the sources' potential at all Q = 6(p-1)^2 + 2 check points; the mixed form evaluates
+ * it at k of them and interpolates the rest, an interpolative decomposition that is
+ * not in the paper.  The k points are the first k pivots of a column-pivoted
+ * Householder QR of K(e_j, c_i) (rows: the Q upward equivalent points at 1.05
+ * half-widths, columns: the Q check points at 2.95), in FP64.  Then the potential of
+ * any source inside the box satisfies u(c_i) = sum_m E[i][m] u(c_idx[m]) up to that
+ * QR's truncation.
+ *   p      expansion order, 2..16.
+ *   k      skeleton size, 1..Q.
+ *   idx    host, k int32 or NULL: check-point indices of the skeleton.  Points are
+ *          numbered as kifmm's unit surface: the boundary points of the p x p x p grid
+ *          on [-1, 1]^3, x outermost, then y, then z.
+ *   E      host, Q x k doubles (row-major) or NULL: the interpolation matrix.
+ *   k_tol  host, 1 int32 or NULL: pivots with |R_ii| > 1e-9 |R_00| (how many a
+ *          mixed plan starts from before rounding up to its surface kernel's shape).
+ * Errors: INVALID_ARG (p or k out of range).
+ */
+int kifmm_up_skeleton(int p, int k, int32_t* idx, double* E, int32_t* k_tol);
 
 /*
  * Per-phase device times (milliseconds).  While enabled, every matvec records CUDA

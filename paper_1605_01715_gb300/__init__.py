@@ -14,6 +14,7 @@ from .capi import (  # noqa: F401
     exported_symbols,
     kifmm_polarization_rhs,
     kifmm_quadrature_points,
+    kifmm_up_skeleton,
     kifmm_version,
     lib,
 )

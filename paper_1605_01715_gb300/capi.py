@@ -55,7 +55,8 @@ class PlanStats(ctypes.Structure):
                 ("launches_per_matvec", ctypes.c_int32), ("rank_up", ctypes.c_int32),
                 ("rank_down", ctypes.c_int32), ("m2l_width", ctypes.c_int32),
                 ("m2l_rows", ctypes.c_int32), ("near_units", ctypes.c_int32),
-                ("near_split_leaves", ctypes.c_int32), ("near_overlap", ctypes.c_int32)]
+                ("near_split_leaves", ctypes.c_int32), ("near_overlap", ctypes.c_int32),
+                ("s2u_points", ctypes.c_int32)]
 
 
 def _as_dict(st):
@@ -83,6 +84,7 @@ _SIGS = {
     "kifmm_fmm_matvec": ([_P, _P, _P, _P], ctypes.c_int),
     "kifmm_fmm_matvec_graph": ([_P, _P, _P, _P], ctypes.c_int),
     "kifmm_plan_get_stats": ([_P, ctypes.POINTER(PlanStats)], ctypes.c_int),
+    "kifmm_up_skeleton": ([ctypes.c_int, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "kifmm_plan_profile": ([_P, ctypes.c_int, _P], ctypes.c_int),
     "kifmm_plan_check": ([_P], ctypes.c_int),
     "kifmm_plan_destroy": ([_P], ctypes.c_int),
@@ -324,6 +326,21 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def kifmm_up_skeleton(p, k):
+    """Skeleton of the upward check surface of order p (host only, no GPU): returns
+    (idx, E, k_tol) -- k check-point indices (int32), the Q x k interpolation matrix
+    (float64) with u(c_i) = sum_m E[i, m] u(c_idx[m]), and the pivot count above 1e-9
+    (include/kifmm.h, kifmm_up_skeleton)."""
+    import numpy as np
+    Q = 6 * (p - 1) ** 2 + 2
+    idx = np.zeros(max(k, 0), dtype=np.int32)
+    E = np.zeros((Q, max(k, 0)), dtype=np.float64)
+    kt = ctypes.c_int32(0)
+    _check(lib().kifmm_up_skeleton(int(p), int(k), idx.ctypes.data_as(_P), E.ctypes.data_as(_P),
+                                   ctypes.byref(kt)))
+    return idx, E, kt.value
 
 
 def kifmm_polarization_rhs(nrm, eps_in, eps_out, e0, out=None, stream=None):

@@ -69,7 +69,7 @@ __global__ void k_gather_q(const double* __restrict__ q, const int64_t* __restri
 // shared memory relative to the box centre.  DIPOLE: n_j.(x - y)/|x - y|^3 q_j, else q_j/|x - y|.
 constexpr int kSurfThreads = 128;
 constexpr int kSurfPer = 8;  // Q <= 1024
-constexpr int kSurfThreadsF = 128;  // FP32 form: threads per box (2 NP points each)
+constexpr double kSkelTol = 1e-9;   // pivots of the S2U skeleton: |R_ii| above this x |R_00|
 
 template <typename Real, bool DIPOLE>
 __global__ void __launch_bounds__(kSurfThreads)
@@ -137,7 +137,7 @@ k_src2surf(const int* __restrict__ boxes, const int* __restrict__ off, const int
     }
 }
 
-// FP32 form.  Each thread owns 2 NP surface points (points threadIdx.x + i kSurfThreadsF)
+// FP32 form.  Each of NT threads owns 2 NP surface points (points threadIdx.x + i NT)
 // as NP packed pairs: every step is one FP32x2 instruction for two points (the same
 // round-to-nearest operations as the scalar form).  Staged sources are float4 --
 // (x, y, z, q), and (q n_j) over two float4 for dipoles -- built from FP32 hi/lo
@@ -186,14 +186,14 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
 // for the tensor-core projection that follows: the potential scaled by the power of two
 // that puts its largest entry into [2^14, 2^15) (exponent in bexp[b]) and split into
 // FP16 hi and lo terms (Qp per box, zero past Q) -- the box split done in the producer.
-template <bool DIPOLE, int NP>
-__global__ void __launch_bounds__(kSurfThreadsF)
+template <bool DIPOLE, int NP, int NT>
+__global__ void __launch_bounds__(NT)
 k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx, int down,
          const float4* __restrict__ bcf, const int64_t* __restrict__ rng, const float* __restrict__ sxf, int64_t ns,
          const float* __restrict__ qs, const float* __restrict__ surf, int Q, int Qp, __half* __restrict__ vin_h,
          __half* __restrict__ vin_l, int* __restrict__ bexp) {
-    __shared__ float4 sp[kSurfThreadsF];
-    __shared__ float4 sd[DIPOLE ? kSurfThreadsF : 1];
+    __shared__ float4 sp[NT];
+    __shared__ float4 sd[DIPOLE ? NT : 1];
     const int b = boxes[blockIdx.x];
     const float4 bh = bcf[3 * b], bl = bcf[3 * b + 1], br = bcf[3 * b + 2];
     const float rf = down ? br.y : br.x;
@@ -203,7 +203,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
         float c[2][3];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int k = threadIdx.x + (2 * m + h) * kSurfThreadsF;
+            const int k = threadIdx.x + (2 * m + h) * NT;
             const int kk = k < Q ? k : 0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) c[h][d] = rf * surf[3 * kk + d];
@@ -222,7 +222,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
         const float dm = fmaxf(fabsf((ah.x - bh.x) + (al.x - bl.x)),
                                fmaxf(fabsf((ah.y - bh.y) + (al.y - bl.y)), fabsf((ah.z - bh.z) + (al.z - bl.z))));
         const bool near = fmaxf(dm - ah.w - rf, rf - dm - ah.w) <= margin;
-        for (int64_t j0 = sb; j0 < se; j0 += kSurfThreadsF) {
+        for (int64_t j0 = sb; j0 < se; j0 += NT) {
             const int64_t j = j0 + threadIdx.x;
             if (j < se) {
                 sp[threadIdx.x] = make_float4((sxf[j] - bh.x) + (sxf[3 * ns + j] - bl.x),
@@ -231,7 +231,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
                 if (DIPOLE) sd[threadIdx.x] = make_float4(qs[ns + j], qs[2 * ns + j], 0.f, 0.f);
             }
             __syncthreads();
-            const int cnt = (int)((se - j0) < (int64_t)kSurfThreadsF ? (se - j0) : (int64_t)kSurfThreadsF);
+            const int cnt = (int)((se - j0) < (int64_t)NT ? (se - j0) : (int64_t)NT);
             if (near)
                 surf_pairs<true, DIPOLE, NP>(sp, sd, cnt, px, py, pz, acc);
             else
@@ -240,11 +240,11 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
         }
     }
     // the box's largest |potential| (points past Q hold partial sums of a repeated point)
-    __shared__ float s_red[kSurfThreadsF / 32];
+    __shared__ float s_red[NT / 32];
     float mx = 0.f;
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
-        const int k0 = threadIdx.x + 2 * m * kSurfThreadsF, k1 = k0 + kSurfThreadsF;
+        const int k0 = threadIdx.x + 2 * m * NT, k1 = k0 + NT;
         if (k0 < Q) mx = fmaxf(mx, fabsf(acc[m].x));
         if (k1 < Q) mx = fmaxf(mx, fabsf(acc[m].y));
     }
@@ -254,7 +254,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
     __syncthreads();
     mx = s_red[0];
 #pragma unroll
-    for (int w = 1; w < kSurfThreadsF / 32; ++w) mx = fmaxf(mx, s_red[w]);
+    for (int w = 1; w < NT / 32; ++w) mx = fmaxf(mx, s_red[w]);
     int ex = mx > 0.f ? 14 - ilogbf(mx) : 0;
     ex = max(-100, min(100, ex));
     if (threadIdx.x == 0) bexp[b] = ex;
@@ -265,7 +265,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
     for (int m = 0; m < NP; ++m) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int k = threadIdx.x + (2 * m + h) * kSurfThreadsF;
+            const int k = threadIdx.x + (2 * m + h) * NT;
             if (k < Qp) {
                 const float x = k < Q ? (h ? acc[m].y : acc[m].x) * sc : 0.f;
                 const __half hh = __float2half_rn(x);
@@ -274,11 +274,20 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
             }
         }
     }
-    for (int k = threadIdx.x + 2 * NP * kSurfThreadsF; k < Qp; k += kSurfThreadsF) {
+    for (int k = threadIdx.x + 2 * NP * NT; k < Qp; k += NT) {
         hb[k] = __float2half_rn(0.f);
         lb[k] = __float2half_rn(0.f);
     }
 }
+
+// Point slots of the FP32 surface kernel's shapes (NT threads x 2 NP points): the
+// smallest that holds n points.  The X list keeps the 128-thread shapes.
+int surf_slots(int n) {
+    for (int v : {256, 384, 512, 576, 768, 1024})
+        if (n <= v) return v;
+    return 0;
+}
+int surf_slots_full(int n) { return n <= 1024 ? (n + 255) / 256 * 256 : 0; }
 
 // Per-box FP32 table of the surface kernel: {centre hi, half-width}, {centre lo, 0},
 // {up-check radius, down-check radius, 0, 0}, each rounded once from FP64.
@@ -308,22 +317,26 @@ int launch_surf(const Plan& P, const Tree& T, bool dl, int nbox, const int* boxe
     if constexpr (std::is_same<Real, float>::value) {
         (void)out;
         (void)surf;
-        const int np = (P.Q + 2 * kSurfThreadsF - 1) / (2 * kSurfThreadsF);
+        // S2U evaluates the skeleton of the up-check surface (ks points, rows of ks);
+        // the X list the whole down-check surface (Q points, rows of Qp)
         const int down = radius == kDnCheck ? 1 : 0;
-        switch (np * 2 + (dl ? 1 : 0)) {
-#define KF_SURF(NP)                                                                                              \
-    case 2 * NP:                                                                                                 \
-        k_surf_f<false, NP><<<nbox, kSurfThreadsF, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, \
-                                                          q, surf, P.Q, P.Qp, P.sin_h.p, P.sin_l.p, P.sexp.p);  \
+        const int npts = down ? P.Q : P.ops->ks, stride = down ? P.Qp : P.ops->ks;
+        const float* sf = down ? P.surf_f.p : P.ops->surf_up.p;
+        const int slots = down ? surf_slots_full(P.Q) : surf_slots(npts);
+        switch (slots * 2 + (dl ? 1 : 0)) {
+#define KF_SURF(NP, NT)                                                                                          \
+    case 2 * (2 * NP * NT):                                                                                      \
+        k_surf_f<false, NP, NT><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, q, sf,   \
+                                                    npts, stride, P.sin_h.p, P.sin_l.p, P.sexp.p);               \
         break;                                                                                                   \
-    case 2 * NP + 1:                                                                                             \
-        k_surf_f<true, NP><<<nbox, kSurfThreadsF, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns,  \
-                                                         q, surf, P.Q, P.Qp, P.sin_h.p, P.sin_l.p, P.sexp.p);   \
+    case 2 * (2 * NP * NT) + 1:                                                                                  \
+        k_surf_f<true, NP, NT><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, q, sf,    \
+                                                   npts, stride, P.sin_h.p, P.sin_l.p, P.sexp.p);                \
         break;
-            KF_SURF(1) KF_SURF(2) KF_SURF(3) KF_SURF(4)
+            KF_SURF(1, 128) KF_SURF(2, 96) KF_SURF(2, 128) KF_SURF(3, 96) KF_SURF(3, 128) KF_SURF(4, 128)
 #undef KF_SURF
             default:
-                set_error("check surface of %d points exceeds the FP32 surface kernel", P.Q);
+                set_error("check surface of %d points exceeds the FP32 surface kernel", npts);
                 return KIFMM_ERR_UNSUPPORTED;
         }
     } else {
@@ -1145,7 +1158,8 @@ __global__ void k_left_mul(const double* __restrict__ L, const double* __restric
 // U_u^T and U_d^T C of the leaves' and X-list boxes' full check potentials.  The
 // products are exact: U^T U = I, so the chain reproduces K P ... K P.  Built in FP64,
 // rounded once to FP32 (then split into two-term FP16 by the caller).
-int build_projected(Plan& P, const HostPinv& h, OpTables* t, DBuf<float>* f32, cudaStream_t s) {
+int build_projected(Plan& P, const HostPinv& h, OpTables* t, const std::vector<double>& Eup, DBuf<float>* f32,
+                    cudaStream_t s) {
     const int Q = P.Q, Qp = P.Qp, Ku = t->Ku, Kd = t->Kd;
     const bool adl = P.kernel == KIFMM_KERNEL_ADL;
     std::vector<double> Lu((size_t)Ku * Q, 0.0), Ld((size_t)Kd * Q, 0.0);
@@ -1178,18 +1192,27 @@ int build_projected(Plan& P, const HostPinv& h, OpTables* t, DBuf<float>* f32, c
         KF_CHECK_LAUNCH();
         KF_CHECK_CUDA(cudaStreamSynchronize(s));
     }
-    // projections U_u^T and U_d^T C, zero padded to K x Qp
+    // projections U_u^T E (from the ks skeleton potentials; E interpolates the whole
+    // up-check surface) and U_d^T C, zero padded to K x ks and K x Qp
     for (int f = 3; f < kFamilies; ++f) {
         const std::vector<double>& L = f == 3 ? Lu : Ld;
-        const int K = f == 3 ? Ku : Kd;
-        std::vector<float> ut((size_t)K * Qp, 0.f);
+        const int K = f == 3 ? Ku : Kd, W = f == 3 ? t->ks : Qp;
+        std::vector<float> ut((size_t)K * W, 0.f);
         for (int j = 0; j < K; ++j) {
+            if (f == 3) {
+                for (int m = 0; m < t->ks; ++m) {
+                    double acc = 0.0;
+                    for (int i = 0; i < Q; ++i) acc += L[(size_t)j * Q + i] * Eup[(size_t)i * t->ks + m];
+                    ut[(size_t)j * W + m] = (float)acc;
+                }
+                continue;
+            }
             double mean = 0.0;
-            if (adl && f == 4) {
+            if (adl) {
                 for (int i = 0; i < Q; ++i) mean += L[(size_t)j * Q + i];
                 mean /= Q;
             }
-            for (int i = 0; i < Q; ++i) ut[(size_t)j * Qp + i] = (float)(L[(size_t)j * Q + i] - mean);
+            for (int i = 0; i < Q; ++i) ut[(size_t)j * W + i] = (float)(L[(size_t)j * Q + i] - mean);
         }
         KF_CHECK_CUDA(cudaMemcpyAsync(f32[f].p, ut.data(), ut.size() * sizeof(float), cudaMemcpyHostToDevice, s));
         KF_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -1284,15 +1307,38 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
         t->rd = h.rd;
         t->Ku = (h.ru + 15) / 16 * 16;
         t->Kd = (h.rd + 15) / 16 * 16;
+        // S2U on a skeleton of the up-check surface: the pivots above kSkelTol, rounded
+        // up to the surface kernel's next shape (all Q points once that shape holds them)
+        std::vector<int> sk;
+        std::vector<double> Eup;
+        {
+            const UpPivots& f = host_up_pivots(P.p);
+            const int kt = up_pivot_count(f, kSkelTol);
+            const int slots = surf_slots(std::min(kt, h.Q));
+            if (slots == 0 || slots >= h.Q) {
+                t->ks = h.Q;
+                sk.resize(h.Q);
+                for (int i = 0; i < h.Q; ++i) sk[i] = i;
+                Eup.assign((size_t)h.Q * h.Q, 0.0);
+                for (int i = 0; i < h.Q; ++i) Eup[(size_t)i * h.Q + i] = 1.0;
+            } else {
+                t->ks = slots;
+                up_skeleton(f, slots, sk, Eup);
+            }
+            std::vector<float> su(3 * (size_t)t->ks);
+            for (int m = 0; m < t->ks; ++m)
+                for (int d = 0; d < 3; ++d) su[3 * m + d] = (float)h.surf[3 * (size_t)sk[m] + d];
+            KF_TRY(t->surf_up.upload(su, s));
+        }
         DBuf<float> f32[kFamilies];
         const int nops[kFamilies] = {8, kNumOffsets, 8, 1, 1};
         const int rows[kFamilies] = {t->Ku, t->Kd, t->Kd, t->Ku, t->Kd};
-        const int cols[kFamilies] = {t->Ku, t->Ku, t->Kd, P.Qp, P.Qp};
+        const int cols[kFamilies] = {t->Ku, t->Ku, t->Kd, t->ks, P.Qp};
         for (int f = 0; f < kFamilies; ++f) {
             KF_TRY(f32[f].alloc((size_t)nops[f] * rows[f] * cols[f]));
             KF_CHECK_CUDA(cudaMemsetAsync(f32[f].p, 0, f32[f].bytes(), s));
         }
-        KF_TRY(build_projected(P, h, t.get(), f32, s));
+        KF_TRY(build_projected(P, h, t.get(), Eup, f32, s));
         for (int f = 0; f < kFamilies; ++f) {
             KF_TRY(t->tab_h[f].alloc(f32[f].n));
             KF_TRY(t->tab_l[f].alloc(f32[f].n));
@@ -1615,9 +1661,9 @@ int run_pairs<float>(const Plan& P, int which, const PairTiles& pt, int t0, int 
 int project(const Plan& P, int fam, const PairTiles& pt, float* z, cudaStream_t s, int& launches) {
     if (pt.ntiles == 0) return KIFMM_OK;
     const OpTables& o = *P.ops;
-    const int Mr = fam == 3 ? o.Ku : o.Kd, M = fam == 3 ? o.ru : o.rd;
+    const int Mr = fam == 3 ? o.Ku : o.Kd, M = fam == 3 ? o.ru : o.rd, Kp = fam == 3 ? o.ks : P.Qp;
     const CUtensorMap* m = o.tmaps[fam];
-    KF_TRY(launch_pair_tc(3, m[0], m[1], o.texp[fam], M, Mr, P.Qp, Mr, pt.tiles.p, pt.ntiles, pt.pin.p,
+    KF_TRY(launch_pair_tc(3, m[0], m[1], o.texp[fam], M, Mr, Kp, Mr, pt.tiles.p, pt.ntiles, pt.pin.p,
                           pt.pout.p, P.sexp.p, P.sin_h.p, P.sin_l.p, z, P.err.p, s));
     launches += 2;
     return KIFMM_OK;
@@ -1945,6 +1991,25 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->near_units = P.n_p2p_units;
     st->near_split_leaves = P.n_p2p_split;
     st->near_overlap = (!P.fp64 && P.near_stream && P.n_tleaf && P.max_trg_leaf <= kP2PWarpMaxLeaf) ? 1 : 0;
+    st->s2u_points = (P.fp64 || !P.ops) ? P.Q : P.ops->ks;
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_up_skeleton(int p, int k, int32_t* idx, double* E, int32_t* k_tol) {
+    clear_error();
+    KF_ARG(p >= 2 && p <= 16, "p must be in [2, 16]");
+    const int Q = 6 * (p - 1) * (p - 1) + 2;
+    KF_ARG(k >= 1 && k <= Q, "k must be in [1, Q]");
+    const UpPivots& f = host_up_pivots(p);
+    if (k_tol) *k_tol = up_pivot_count(f, kSkelTol);
+    if (idx || E) {
+        std::vector<int> sk;
+        std::vector<double> e;
+        up_skeleton(f, k, sk, e);
+        if (idx)
+            for (int m = 0; m < k; ++m) idx[m] = sk[m];
+        if (E) std::copy(e.begin(), e.end(), E);
+    }
     return KIFMM_OK;
 }
 

@@ -164,6 +164,94 @@ const HostPinv& host_pinv(int p, double cutoff) {
     return cache.emplace(key, std::move(h)).first->second;
 }
 
+const UpPivots& host_up_pivots(int p) {
+    static std::mutex mu;
+    static std::map<int, UpPivots> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(p);
+    if (it != cache.end()) return it->second;
+    const std::vector<double> s = surface_points(p);
+    const int n = (int)s.size() / 3;
+    // a: column j = row j of K(check, equivalent), i.e. column j of A (column-major)
+    std::vector<double> a = kernel_matrix(s, kUpCheck, s, kUpEquiv);
+    UpPivots f;
+    f.n = n;
+    f.perm.resize(n);
+    for (int j = 0; j < n; ++j) f.perm[j] = j;
+    std::vector<double> v(n);
+    for (int i = 0; i < n; ++i) {
+        // the trailing column of largest norm (norms recomputed, not downdated)
+        int best = i;
+        double bn = -1.0;
+        for (int j = i; j < n; ++j) {
+            const double* c = &a[(size_t)j * n];
+            double t = 0.0;
+            for (int r = i; r < n; ++r) t += c[r] * c[r];
+            if (t > bn) {
+                bn = t;
+                best = j;
+            }
+        }
+        if (best != i) {
+            std::swap_ranges(a.begin() + (size_t)i * n, a.begin() + (size_t)(i + 1) * n, a.begin() + (size_t)best * n);
+            std::swap(f.perm[i], f.perm[best]);
+        }
+        // Householder reflection taking column i's trailing part to alpha e_i
+        double* c = &a[(size_t)i * n];
+        const double nx = std::sqrt(bn > 0 ? bn : 0.0);
+        if (nx == 0.0) continue;
+        const double alpha = c[i] > 0 ? -nx : nx;
+        double vn = 0.0;
+        for (int r = i; r < n; ++r) {
+            v[r] = c[r] - (r == i ? alpha : 0.0);
+            vn += v[r] * v[r];
+        }
+        c[i] = alpha;
+        for (int r = i + 1; r < n; ++r) c[r] = 0.0;
+        if (vn == 0.0) continue;
+#pragma omp parallel for schedule(static)
+        for (int j = i + 1; j < n; ++j) {
+            double* cj = &a[(size_t)j * n];
+            double t = 0.0;
+            for (int r = i; r < n; ++r) t += v[r] * cj[r];
+            t = 2.0 * t / vn;
+            for (int r = i; r < n; ++r) cj[r] -= t * v[r];
+        }
+    }
+    f.R.assign((size_t)n * n, 0.0);
+    for (int c = 0; c < n; ++c)
+        for (int r = 0; r <= c; ++r) f.R[(size_t)r * n + c] = a[(size_t)c * n + r];
+    return cache.emplace(p, std::move(f)).first->second;
+}
+
+int up_pivot_count(const UpPivots& f, double tol) {
+    if (f.n == 0) return 0;
+    const double r0 = std::fabs(f.R[0]);
+    int k = 0;
+    for (int i = 0; i < f.n; ++i)
+        if (std::fabs(f.R[(size_t)i * f.n + i]) > tol * r0) ++k;
+    return k;
+}
+
+void up_skeleton(const UpPivots& f, int k, std::vector<int>& idx, std::vector<double>& E) {
+    const int n = f.n;
+    k = std::max(0, std::min(k, n));
+    idx.assign(f.perm.begin(), f.perm.begin() + k);
+    E.assign((size_t)n * k, 0.0);
+    for (int m = 0; m < k; ++m) E[(size_t)f.perm[m] * k + m] = 1.0;
+    // column j of T = R11^-1 R12 by back substitution, one per non-skeleton point
+#pragma omp parallel for schedule(static)
+    for (int j = k; j < n; ++j) {
+        std::vector<double> t(k);
+        for (int m = k - 1; m >= 0; --m) {
+            double acc = f.R[(size_t)m * n + j];
+            for (int l = m + 1; l < k; ++l) acc -= f.R[(size_t)m * n + l] * t[l];
+            t[m] = acc / f.R[(size_t)m * n + m];
+        }
+        for (int m = 0; m < k; ++m) E[(size_t)f.perm[j] * k + m] = t[m];
+    }
+}
+
 // out[orow[r]*Cp + j] = ascale[r] * sum_m G(a_r, b_{bset[r], m}) P[m][j],  j < C; 0 for C <= j < Cp
 // (P is Q x C: the Q points of a b set by C columns)
 // G = 1/|a-b| (kfun 0) or n_r.(a-b)/|a-b|^3 (kfun 1).  8 rows per block.

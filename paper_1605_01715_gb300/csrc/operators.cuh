@@ -31,6 +31,26 @@ std::vector<double> pinv_jacobi(const std::vector<double>& A_rm, int n, double c
                                 int* rank = nullptr);
 const HostPinv& host_pinv(int p, double cutoff);
 
+// Column-pivoted Householder QR of A = K(2.95 s_i, 1.05 s_j)^T, the transposed map from
+// the upward equivalent surface to the upward check surface (both Q points of the unit
+// box), in FP64: A[:, perm] = Q R.  Its pivots order the check points so that the first
+// k of them interpolate the rest (up_skeleton).  Cached per order.
+struct UpPivots {
+    int n = 0;
+    std::vector<int> perm;          // check point of each pivot position
+    std::vector<double> R;          // n x n upper triangle, row-major
+};
+const UpPivots& host_up_pivots(int p);
+// Pivots with |R_ii| > tol |R_00|.
+int up_pivot_count(const UpPivots& f, double tol);
+// Skeleton of the upward check surface (an interpolative decomposition; the method
+// itself evaluates all Q points): idx = the first k pivots and E (Q x k, row-major)
+// with E[idx[m]][m] = 1 and, for every other point, the row T = R11^-1 R12 gives.  The
+// potential u of any upward equivalent density, and so of any source inside the box,
+// then satisfies u(c_i) = sum_m E[i][m] u(c_idx[m]) up to the QR's truncation after k
+// pivots.  k = n gives the identity.
+void up_skeleton(const UpPivots& f, int k, std::vector<int>& idx, std::vector<double>& E);
+
 // Device row descriptors for build_rows (all device pointers); a table row is
 // ascale * G(a, B) P with P an (Q x C) matrix, stored C of Cp wide (zero padding).
 struct RowSpec {

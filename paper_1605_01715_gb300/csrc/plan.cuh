@@ -44,12 +44,14 @@ struct OpTables {
     double cutoff = 0;
     bool fp64 = true, centered = false;
     int ru = 0, rd = 0, Ku = 0, Kd = 0;
+    int ks = 0;                     // mixed: S2U points (skeleton of the up-check surface)
+    DBuf<float> surf_up;            // mixed: those points on the unit surface, ks x 3
     DBuf<double> m2m_d, m2l_d, l2l_d;
     DBuf<__half> tab_h[kFamilies], tab_l[kFamilies];
     int texp[kFamilies] = {0, 0, 0, 0, 0};
     CUtensorMap tmaps[kFamilies][2];
     int64_t bytes() const {
-        int64_t b = m2m_d.bytes() + m2l_d.bytes() + l2l_d.bytes();
+        int64_t b = m2m_d.bytes() + m2l_d.bytes() + l2l_d.bytes() + surf_up.bytes();
         for (int f = 0; f < kFamilies; ++f) b += tab_h[f].bytes() + tab_l[f].bytes();
         return b;
     }

@@ -70,3 +70,64 @@ def test_forest_arguments_rejected_without_a_gpu(lib):
     a = np.zeros(2, dtype=np.int64)
     assert f(fake, 10, a.ctypes.data, 0, 16, None, ctypes.byref(out)) == -1        # no instances
     assert f(None, 10, a.ctypes.data, 1, 16, None, ctypes.byref(out)) == -1        # NULL points
+
+
+def _unit_surface(p):
+    """The boundary points of the p x p x p grid on [-1, 1]^3, x outermost, then y, then z
+    (the numbering include/kifmm.h states for kifmm_up_skeleton)."""
+    import numpy as np
+    g = np.linspace(-1.0, 1.0, p)
+    return np.array([(x, y, z) for x in g for y in g for z in g
+                     if min(abs(abs(x) - 1), abs(abs(y) - 1), abs(abs(z) - 1)) < 1e-12])
+
+
+def _check_potentials(p, n, seed):
+    """Potentials at the up-check surface (2.95 half-widths) of n unit monopoles and n
+    unit dipoles at random points inside the box: two Q x n matrices, by numpy."""
+    import numpy as np
+    c = 2.95 * _unit_surface(p)
+    rng = np.random.default_rng(seed)
+    y = rng.uniform(-1.0, 1.0, (n, 3))
+    nrm = rng.standard_normal((n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    d = c[:, None, :] - y[None, :, :]
+    r = np.sqrt((d * d).sum(-1))
+    return 1.0 / r, (d * nrm[None]).sum(-1) / r ** 3
+
+
+def test_up_skeleton_interpolates_source_potentials(lib):
+    """The S2U skeleton (kifmm_up_skeleton, an interpolative decomposition the mixed
+    form uses in place of the paper's full check surface) reproduces, from its k
+    points, the potential of sources inside the box at every one of the Q check points:
+    exactly at k = Q, to about 1e-9 (monopoles) and 1e-7 (dipoles) of the largest value
+    at the k = 384 that p = 10 plans use, and less well with fewer points."""
+    import numpy as np
+    from paper_1605_01715_gb300 import kifmm_up_skeleton
+    p = 10
+    Q = 6 * (p - 1) ** 2 + 2
+    mono, dip = _check_potentials(p, 1500, seed=11)
+    errs = {}
+    for k in (300, 384, Q):
+        idx, E, kt = kifmm_up_skeleton(p, k)
+        assert idx.shape == (k,) and E.shape == (Q, k)
+        assert len(set(idx.tolist())) == k and idx.min() >= 0 and idx.max() < Q
+        assert np.array_equal(E[idx], np.eye(k))          # skeleton rows interpolate themselves
+        assert 0 < kt <= Q
+        errs[k] = [float((np.abs(A - E @ A[idx]).max(0) / np.abs(A).max(0)).max()) for A in (mono, dip)]
+    assert errs[Q][0] < 1e-12 and errs[Q][1] < 1e-12
+    assert errs[384][0] < 2e-8 and errs[384][1] < 5e-7
+    assert errs[300][0] > errs[384][0] and errs[300][1] > errs[384][1]
+
+
+def test_up_skeleton_sizes_and_arguments(lib):
+    """Pivot counts above 1e-9: every point at low order (p = 6: Q = 152), fewer than Q
+    from p = 8 on.  Out-of-range p or k are rejected on the host."""
+    from paper_1605_01715_gb300 import KifmmError, kifmm_up_skeleton
+    kts = {p: kifmm_up_skeleton(p, 1)[2] for p in (6, 8, 10, 11)}
+    assert kts[6] == 152
+    for p in (8, 10, 11):
+        assert kts[p] < 6 * (p - 1) ** 2 + 2
+    assert kts[8] < kts[10] < kts[11]
+    for p, k in ((1, 1), (17, 1), (10, 0), (10, 489)):
+        with pytest.raises(KifmmError):
+            kifmm_up_skeleton(p, k)

@@ -133,11 +133,12 @@ def test_mixed_orders(p, tol):
 def test_factored_m2l_widths():
     """The mixed form applies M2L' between projections (from Pu's range, width = its
     rank, to Pd's range, rows = its rank; both below Q and the same for every plan at
-    one order); FP64 applies the Q x Q form."""
+    one order); FP64 applies the Q x Q form.  S2U: FP64 evaluates all Q up-check points,
+    the mixed form a skeleton of 384 at p = 10 (all 152 at p = 6 and all 296 at p = 8)."""
     from paper_1605_01715_gb300 import Plan, Tree
     m, h, (xyz, w, nrm), sig, refs = case("sphere")
     tree = Tree(xyz, max_leaf=40)
-    for p in (6, 10):
+    for p in (6, 8, 10):
         Q = 6 * (p - 1) ** 2 + 2
         mx = Plan(tree, kernel="dl", p=p, precision="mixed", src_nrm=nrm, pinv_cutoff=1e-8).stats()
         fp = Plan(tree, kernel="dl", p=p, precision="fp64", src_nrm=nrm, pinv_cutoff=1e-8).stats()
@@ -145,6 +146,8 @@ def test_factored_m2l_widths():
         assert (mx["m2l_width"], mx["m2l_rows"]) == (mx["rank_up"], mx["rank_down"])
         assert (fp["m2l_width"], fp["m2l_rows"]) == (Q, Q)
         assert (fp["rank_up"], fp["rank_down"]) == (mx["rank_up"], mx["rank_down"])
+        assert fp["s2u_points"] == Q
+        assert mx["s2u_points"] == {6: Q, 8: Q, 10: 384}[p]
 
 
 @pytest.mark.parametrize("prec", ["mixed", "mixed_cn"])
