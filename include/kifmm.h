@@ -203,6 +203,28 @@ int kifmm_fmm_matvec(kifmm_plan plan, const double* q, double* out, void* stream
  */
 int kifmm_fmm_matvec_graph(kifmm_plan plan, const double* q, double* out, void* stream);
 
+/*
+ * The matvec with q and out in host memory (no counterpart in the paper; for callers
+ * whose densities live on the host).
+ *   q      n_src FP64, input order.  Page-locked host memory (cudaHostAlloc,
+ *          cudaHostRegister, a pinned torch tensor): the first kernel reads it in place,
+ *          each element once and in order (on Grace systems over NVLink-C2C, with no
+ *          separate copy).  Pageable host memory: copied to a device staging buffer by
+ *          cudaMemcpyAsync.  Device memory: read as kifmm_fmm_matvec reads it.
+ *   out    n_trg FP64, input order, overwritten.  Page-locked: the last kernel writes
+ *          it in place, each element once and in order.  Pageable: copied back from
+ *          a device staging buffer after the matvec.  Device: written as by
+ *          kifmm_fmm_matvec.
+ *   graph  0: launch the kernels; 1: replay a graph captured for this (q, out) pair,
+ *          as kifmm_fmm_matvec_graph does (captured again when the pair changes).
+ * Asynchronous on `stream` for page-locked and device buffers: synchronize before
+ * reading out or refilling q.  The first call allocates the inverse permutations and
+ * the staging buffers (plan memory: 16 bytes per source and target).  The results are
+ * kifmm_fmm_matvec's, up to the order of its atomic sums (which varies from run to run
+ * in either).  Errors: INVALID_ARG, OOM, CUDA.
+ */
+int kifmm_fmm_matvec_host(kifmm_plan plan, const double* q, double* out, int graph, void* stream);
+
 typedef struct {
     int32_t kernel, p, q_points, precision;
     double  pinv_cutoff;

@@ -83,6 +83,7 @@ _SIGS = {
                          ctypes.POINTER(_P)], ctypes.c_int),
     "kifmm_fmm_matvec": ([_P, _P, _P, _P], ctypes.c_int),
     "kifmm_fmm_matvec_graph": ([_P, _P, _P, _P], ctypes.c_int),
+    "kifmm_fmm_matvec_host": ([_P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "kifmm_plan_get_stats": ([_P, ctypes.POINTER(PlanStats)], ctypes.c_int),
     "kifmm_up_skeleton": ([ctypes.c_int, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "kifmm_plan_profile": ([_P, ctypes.c_int, _P], ctypes.c_int),
@@ -143,6 +144,15 @@ def _dev(t, n=None, name="tensor"):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
     if n is not None and t.numel() != n:
+        raise ValueError("%s must have %d elements, has %d" % (name, n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(t, n, name="tensor"):
+    if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CPU tensor" % name)
+    if t.numel() != n:
         raise ValueError("%s must have %d elements, has %d" % (name, n, t.numel()))
     return ctypes.c_void_p(t.data_ptr())
 
@@ -260,6 +270,15 @@ class Plan:
         ``out`` by address (both must stay allocated; refill ``q`` in place)."""
         _check(lib().kifmm_fmm_matvec_graph(self.handle, _dev(q, self.n_src, "q"),
                                             _dev(out, self.n_trg, "out"), _stream(stream)))
+        return out
+
+    def matvec_host(self, q, out, graph=True, stream=None):
+        """kifmm_fmm_matvec_host: ``q`` and ``out`` are CPU float64 tensors.  Pinned
+        ones are read and written in place by the first and last kernels (asynchronous:
+        synchronize the stream before reading ``out``), pageable ones staged.  ``graph``
+        replays a matvec captured for this pair."""
+        _check(lib().kifmm_fmm_matvec_host(self.handle, _host(q, self.n_src, "q"), _host(out, self.n_trg, "out"),
+                                           1 if graph else 0, _stream(stream)))
         return out
 
     def check(self):

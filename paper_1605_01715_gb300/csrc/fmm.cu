@@ -64,6 +64,32 @@ __global__ void k_gather_q(const double* __restrict__ q, const int64_t* __restri
     }
 }
 
+// The same from q in input order (a host buffer: each element read once, in order)
+// scattered to the sorted positions iperm[i].
+template <typename Real>
+__global__ void k_scatter_q(const double* __restrict__ q, const int64_t* __restrict__ iperm, int64_t n,
+                            const double* __restrict__ snrm, Real* __restrict__ qs, bool lo) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = q[i];
+    const int64_t j = iperm[i];
+    if (snrm) {
+        for (int d = 0; d < 3; ++d) {
+            const double pd = v * snrm[d * n + j];
+            qs[d * n + j] = (Real)pd;
+            if (lo) qs[(3 + d) * n + j] = (Real)(pd - (double)(Real)pd);
+        }
+    } else {
+        qs[j] = (Real)v;
+    }
+}
+
+// iperm[perm[j]] = j
+__global__ void k_invert_perm(const int64_t* __restrict__ perm, int64_t n, int64_t* __restrict__ iperm) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < n) iperm[perm[j]] = j;
+}
+
 // ---------------------------------------------------------------- sources -> surface (S2U, X list)
 // One block per box; threads own surface points; sources of the CSR boxes staged in
 // shared memory relative to the box centre.  DIPOLE: n_j.(x - y)/|x - y|^3 q_j, else q_j/|x - y|.
@@ -955,6 +981,15 @@ __global__ void k_add_far(const int64_t* __restrict__ tperm, const float* __rest
     if (t < nt) out[tperm[t]] += (double)res[t];
 }
 
+// f[i] = near[i] + res[itperm[i]] in input order (res null: f[i] = near[i]), written
+// once and in order, so f may be a host buffer.
+__global__ void k_add_far_io(const int64_t* __restrict__ itperm, const float* __restrict__ res,
+                             const double* __restrict__ near, int64_t nt, double* __restrict__ f) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    f[i] = res ? near[i] + (double)res[itperm[i]] : near[i];
+}
+
 // ---------------------------------------------------------------- set-up kernels
 // x = hi + lo with hi = fl32(x), lo = fl32(x - hi): 6 x n SoA (hi x|y|z, lo x|y|z).
 __global__ void k_split_xyz(const double* __restrict__ xyz, int64_t n, float* __restrict__ out) {
@@ -1754,8 +1789,12 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
                               P.max_trg_leaf <= kP2PWarpMaxLeaf;
     const bool dl = P.kernel == KIFMM_KERNEL_DL;
     KF_TRY(mark(0));
-    k_gather_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, T.sperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q,
-                                                       P.cnear && dl);
+    if (P.io_in)
+        k_scatter_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, P.isperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q,
+                                                            P.cnear && dl);
+    else
+        k_gather_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, T.sperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q,
+                                                           P.cnear && dl);
     KF_CHECK_LAUNCH();
     ++launches;
     const cudaStream_t s_in = s;                  // the caller's stream
@@ -1855,8 +1894,16 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         s = s_in;
         KF_CHECK_CUDA(cudaStreamWaitEvent(s, P.ev_far, 0));
         KF_CHECK_CUDA(cudaStreamWaitEvent(s, P.ev_join, 0));
-        k_add_far<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(T.same ? T.sperm.p : T.tperm.p,
-                                                              reinterpret_cast<const float*>(B.res), T.nt, out);
+        if (P.io_out)
+            k_add_far_io<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(P.itperm.p, reinterpret_cast<const float*>(B.res),
+                                                                     out, T.nt, P.io_out);
+        else
+            k_add_far<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(T.same ? T.sperm.p : T.tperm.p,
+                                                                  reinterpret_cast<const float*>(B.res), T.nt, out);
+        KF_CHECK_LAUNCH();
+        ++launches;
+    } else if (P.io_out) {
+        k_add_far_io<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(P.itperm.p, nullptr, out, T.nt, P.io_out);
         KF_CHECK_LAUNCH();
         ++launches;
     }
@@ -1924,47 +1971,156 @@ extern "C" int kifmm_fmm_matvec(kifmm_plan plan, const double* q, double* out, v
     return plan_matvec(plan->P, q, out, (cudaStream_t)stream);
 }
 
+namespace kifmm {
+namespace {
+
+// Capture the launches of one matvec (q, out as plan_matvec takes them; no profiling
+// events inside the graph) and instantiate them into *exec (destroyed first if set).
+int capture_matvec(Plan& P, const double* q, double* out, cudaGraphExec_t* exec) {
+    if (*exec) {
+        KF_CHECK_CUDA(cudaGraphExecDestroy(*exec));
+        *exec = nullptr;
+    }
+    if (!P.cap_stream) KF_CHECK_CUDA(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+    const bool prof = P.profile;
+    const int launches = P.launches;
+    P.profile = false;
+    KF_CHECK_CUDA(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = plan_matvec(P, q, out, P.cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(P.cap_stream, &g);
+    P.profile = prof;
+    P.launches = launches;
+    if (rc != KIFMM_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (rc == KIFMM_OK) {
+            set_error("matvec capture failed: %s", cudaGetErrorString(ce));
+            rc = KIFMM_ERR_CUDA;
+        }
+        cudaGetLastError();
+        return rc;
+    }
+    // keep the stream priorities of the overlapped near and far fields
+    cudaError_t ie = cudaGraphInstantiate(exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        *exec = nullptr;
+        set_error("matvec graph instantiation failed: %s", cudaGetErrorString(ie));
+        return KIFMM_ERR_CUDA;
+    }
+    return KIFMM_OK;
+}
+
+// Where a buffer of the host-buffer matvec lives: 0 pageable host memory, 1 page-locked
+// host memory (*dev: the address kernels use for it), 2 device or managed memory.
+int buffer_kind(const void* p, const void** dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *dev = a.devicePointer;
+        return 1;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        *dev = p;
+        return 2;
+    }
+    return 0;
+}
+
+// First use of the host-buffer matvec: inverse permutations and the staging of the
+// near sums (q's staging is allocated when a pageable q first arrives).
+int ensure_host_io(Plan& P, cudaStream_t s) {
+    const Tree& T = P.tree->t;
+    if (P.isperm.p || (T.ns == 0 && T.nt == 0)) return KIFMM_OK;
+    KF_TRY(P.isperm.alloc(std::max<int64_t>(T.ns, 1)));
+    KF_TRY(P.itperm.alloc(std::max<int64_t>(T.nt, 1)));
+    KF_TRY(P.out_stage.alloc(std::max<int64_t>(T.nt, 1)));
+    if (T.ns) k_invert_perm<<<(unsigned)div_up(T.ns, 256), 256, 0, s>>>(T.sperm.p, T.ns, P.isperm.p);
+    if (T.nt)
+        k_invert_perm<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(T.same ? T.sperm.p : T.tperm.p, T.nt,
+                                                                   P.itperm.p);
+    KF_CHECK_LAUNCH();
+    return KIFMM_OK;
+}
+
+}  // namespace
+}  // namespace kifmm
+
 extern "C" int kifmm_fmm_matvec_graph(kifmm_plan plan, const double* q, double* out, void* stream) {
     clear_error();
     KF_ARG(plan && q && out, "NULL plan, q or out");
     Plan& P = plan->P;
     if (!P.gexec || P.g_q != q || P.g_out != out) {
-        if (P.gexec) {
-            KF_CHECK_CUDA(cudaGraphExecDestroy(P.gexec));
-            P.gexec = nullptr;
-        }
-        if (!P.cap_stream) KF_CHECK_CUDA(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
-        // capture the launches of one matvec (no profiling events inside the graph)
-        const bool prof = P.profile;
-        const int launches = P.launches;
-        P.profile = false;
-        KF_CHECK_CUDA(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = plan_matvec(P, q, out, P.cap_stream);
-        cudaGraph_t g = nullptr;
-        cudaError_t ce = cudaStreamEndCapture(P.cap_stream, &g);
-        P.profile = prof;
-        P.launches = launches;
-        if (rc != KIFMM_OK || ce != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            if (rc == KIFMM_OK) {
-                set_error("matvec capture failed: %s", cudaGetErrorString(ce));
-                rc = KIFMM_ERR_CUDA;
-            }
-            cudaGetLastError();
-            return rc;
-        }
-        // keep the stream priorities of the overlapped near and far fields
-        cudaError_t ie = cudaGraphInstantiate(&P.gexec, g, cudaGraphInstantiateFlagUseNodePriority);
-        cudaGraphDestroy(g);
-        if (ie != cudaSuccess) {
-            P.gexec = nullptr;
-            set_error("matvec graph instantiation failed: %s", cudaGetErrorString(ie));
-            return KIFMM_ERR_CUDA;
-        }
+        KF_TRY(capture_matvec(P, q, out, &P.gexec));
         P.g_q = q;
         P.g_out = out;
     }
     KF_CHECK_CUDA(cudaGraphLaunch(P.gexec, (cudaStream_t)stream));
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_fmm_matvec_host(kifmm_plan plan, const double* q, double* out, int graph, void* stream) {
+    clear_error();
+    KF_ARG(plan && q && out, "NULL plan, q or out");
+    Plan& P = plan->P;
+    const Tree& T = P.tree->t;
+    cudaStream_t s = (cudaStream_t)stream;
+    KF_TRY(ensure_host_io(P, s));
+    const void* qd = nullptr;
+    const void* od = nullptr;
+    const int kq = buffer_kind(q, &qd), ko = buffer_kind(out, &od);
+    // input: page-locked q is read in place (in input order) by the first kernel
+    const double* q_use = q;
+    bool in_host = false;
+    if (kq == 1) {
+        q_use = static_cast<const double*>(qd);
+        in_host = true;
+    } else if (kq == 0) {
+        if (!P.q_stage.p) KF_TRY(P.q_stage.alloc(std::max<int64_t>(T.ns, 1)));
+        if (T.ns)
+            KF_CHECK_CUDA(cudaMemcpyAsync(P.q_stage.p, q, T.ns * sizeof(double), cudaMemcpyHostToDevice, s));
+        q_use = P.q_stage.p;
+    }
+    // output: the near sums go to the staging buffer; the last kernel writes f into a
+    // page-locked out directly, a pageable one is copied after the matvec
+    double* out_use = out;
+    double* io_out = nullptr;
+    if (ko == 1) {
+        out_use = P.out_stage.p;
+        io_out = static_cast<double*>(const_cast<void*>(od));
+    } else if (ko == 0) {
+        out_use = P.out_stage.p;
+    }
+    P.io_in = in_host;
+    P.io_out = io_out;
+    int rc = KIFMM_OK;
+    if (graph) {
+        if (!P.hexec || P.h_q != q_use || P.h_out != out_use || P.h_io_out != io_out) {
+            rc = capture_matvec(P, q_use, out_use, &P.hexec);
+            if (rc == KIFMM_OK) {
+                P.h_q = q_use;
+                P.h_out = out_use;
+                P.h_io_out = io_out;
+            }
+        }
+        if (rc == KIFMM_OK) {
+            cudaError_t e = cudaGraphLaunch(P.hexec, s);
+            if (e != cudaSuccess) {
+                set_error("%s", cudaGetErrorString(e));
+                rc = KIFMM_ERR_CUDA;
+            }
+        }
+    } else {
+        rc = plan_matvec(P, q_use, out_use, s);
+    }
+    P.io_in = false;
+    P.io_out = nullptr;
+    if (rc != KIFMM_OK) return rc;
+    if (ko == 0 && T.nt)
+        KF_CHECK_CUDA(cudaMemcpyAsync(out, P.out_stage.p, T.nt * sizeof(double), cudaMemcpyDeviceToHost, s));
     return KIFMM_OK;
 }
 

@@ -128,11 +128,26 @@ struct Plan {
     const double* g_q = nullptr;
     double* g_out = nullptr;
 
+    // host buffers (kifmm_fmm_matvec_host), set up on first use: inverse permutations
+    // (input index -> sorted position) of sources and targets, device staging of a
+    // pageable q and of the near sums; while a call runs, io_in (the first kernel reads
+    // q in input order and scatters it) and io_out (the last kernel writes f there, in
+    // input order); the graph captured for one (q, out) pair of such calls
+    DBuf<int64_t> isperm, itperm;
+    DBuf<double> q_stage, out_stage;
+    bool io_in = false;
+    double* io_out = nullptr;
+    cudaGraphExec_t hexec = nullptr;
+    const double* h_q = nullptr;
+    double* h_out = nullptr;
+    double* h_io_out = nullptr;
+
     ~Plan() {
         for (auto& sl : ev_slots)
             for (auto e : sl)
                 if (e) cudaEventDestroy(e);
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (hexec) cudaGraphExecDestroy(hexec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);

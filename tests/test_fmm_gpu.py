@@ -217,6 +217,46 @@ def test_target_source_model():
         assert rel(plan.matvec(q).cpu().numpy(), ref) < tol
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_matvec_host_buffers(prec):
+    """kifmm_fmm_matvec_host reproduces kifmm_fmm_matvec up to the order of the matvec's
+    atomic sums, which varies from run to run: FP32 in the mixed far field (1e-6 of the
+    largest value allowed), FP64 otherwise (1e-13).  q and out may be pinned host
+    tensors (read and written in place by the first and last kernels) or pageable ones
+    (staged), with or without graph replay, for sources that are the targets (DL) and
+    for separate targets (ADL).  The mixed DL result is also checked against the
+    oracle."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    m, h, (xyz, w, nrm), sig, refs = case("cube")
+    rng = np.random.default_rng(9)
+    trg = rng.uniform(-0.7, 0.7, size=(3, 2049))
+    tnrm = rng.normal(size=(3, 2049))
+    tnrm /= np.linalg.norm(tnrm, axis=0)
+    q = torch.from_numpy(sig).to(DEV) * w
+    p = 10 if prec == "mixed" else 6
+    cases = [("dl", Tree(xyz, max_leaf=48), None),
+             ("adl", Tree(xyz, torch.from_numpy(trg).to(DEV), max_leaf=48), torch.from_numpy(tnrm).to(DEV))]
+    for kernel, tree, tn in cases:
+        plan = Plan(tree, kernel=kernel, p=p, precision=prec, src_nrm=nrm, trg_nrm=tn)
+        ref = plan.matvec(q).cpu()
+        n_out = ref.numel()
+        tol = (1e-6 if prec == "mixed" else 1e-13) * float(ref.abs().max())
+        for pinned in (True, False):
+            for graph in (False, True):
+                qh = q.cpu()
+                oh = torch.full((n_out,), float("nan"), dtype=torch.float64)
+                if pinned:
+                    qh, oh = qh.pin_memory(), oh.pin_memory()
+                for _ in range(2):                # a second call reuses the captured graph
+                    plan.matvec_host(qh, oh, graph=graph)
+                    torch.cuda.synchronize()
+                    diff = float((oh - ref).abs().max())
+                    assert diff <= tol, (kernel, pinned, graph, diff, int(oh.isnan().sum()))
+                    oh.fill_(float("nan"))
+        if kernel == "dl" and prec == "mixed":
+            assert rel(ref.numpy(), refs["dl"]) < 2e-6
+
+
 def test_tolerance_radius_and_tiny_inputs():
     from paper_1605_01715_gb300 import Plan, Tree
     # one source: its own target is excluded -> 0
