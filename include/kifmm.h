@@ -219,7 +219,8 @@ int kifmm_fmm_matvec_graph(kifmm_plan plan, const double* q, double* out, void* 
  *          as kifmm_fmm_matvec_graph does (captured again when the pair changes).
  * Asynchronous on `stream` for page-locked and device buffers: synchronize before
  * reading out or refilling q.  The first call allocates the inverse permutations and
- * the staging buffers (plan memory: 16 bytes per source and target).  The results are
+ * the staging buffer of the near sums (8 bytes per source, 16 per target), the first
+ * pageable q a staging buffer of 8 bytes per source.  The results are
  * kifmm_fmm_matvec's, up to the order of its atomic sums (which varies from run to run
  * in either).  Errors: INVALID_ARG, OOM, CUDA.
  */
