@@ -248,6 +248,10 @@ typedef struct {
                                          profiled phase time spans the overlap         */
     int32_t s2u_points;               /* up-check points S2U evaluates: q_points (FP64)
                                          or the skeleton of kifmm_up_skeleton (mixed)  */
+    int64_t m2l_chain_pairs;          /* mixed: V pairs in M2L chains -- runs of at most
+                                         128 targets of one level whose V lists hold the
+                                         same offsets, whose products over all of those
+                                         offsets are summed on chip and written once    */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);

@@ -56,7 +56,7 @@ class PlanStats(ctypes.Structure):
                 ("rank_down", ctypes.c_int32), ("m2l_width", ctypes.c_int32),
                 ("m2l_rows", ctypes.c_int32), ("near_units", ctypes.c_int32),
                 ("near_split_leaves", ctypes.c_int32), ("near_overlap", ctypes.c_int32),
-                ("s2u_points", ctypes.c_int32)]
+                ("s2u_points", ctypes.c_int32), ("m2l_chain_pairs", ctypes.c_int64)]
 
 
 def _as_dict(st):

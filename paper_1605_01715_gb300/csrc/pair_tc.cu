@@ -151,7 +151,7 @@ template <int SLABS, int N>
 static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int M, int Mr, int Kp,
                         int ostride, const int4* tiles, int ntiles, const int* pin, const int* pout,
                         const int* bexp, const __half* in_hi, const __half* in_lo, float* out, int* err,
-                        cudaStream_t s) {
+                        const int* kcount, cudaStream_t s) {
     using S = tc::Shape<SLABS, N>;
     auto kern = which == 0   ? tc::k_u2u_tc<SLABS, N>
                 : which == 1 ? tc::k_m2l_tc<SLABS, N>
@@ -168,7 +168,7 @@ static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo,
     KF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = nitems < nsm ? nitems : nsm;
     kern<<<grid, tc::kThreads, S::kSmemBytes, s>>>(hi, lo, M, Kp, ostride, Mr, mgroups, nitems, tiles, pin, pout,
-                                                    bexp, texp, in_hi, in_lo, out, err);
+                                                    bexp, texp, in_hi, in_lo, out, err, kcount);
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }
@@ -178,13 +178,14 @@ static int launch_shape(int which, const CUtensorMap& hi, const CUtensorMap& lo,
 // (tc_box_split, Kp per box) of every box a pair reads; out: ostride per box.
 int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int texp, int M, int Mr, int Kp,
                    int ostride, const int4* tiles, int ntiles, const int* pin, const int* pout, const int* bexp,
-                   const __half* in_hi, const __half* in_lo, float* out, int* err, cudaStream_t s) {
+                   const __half* in_hi, const __half* in_lo, float* out, int* err, cudaStream_t s,
+                   const int* kcount) {
     if (ntiles <= 0) return KIFMM_OK;
     if (Mr <= 128)
         return launch_shape<1, 256>(which, hi, lo, texp, M, Mr, Kp, ostride, tiles, ntiles, pin, pout, bexp, in_hi,
-                                    in_lo, out, err, s);
+                                    in_lo, out, err, kcount, s);
     return launch_shape<2, 128>(which, hi, lo, texp, M, Mr, Kp, ostride, tiles, ntiles, pin, pout, bexp, in_hi,
-                                in_lo, out, err, s);
+                                in_lo, out, err, kcount, s);
 }
 
 }  // namespace kifmm

@@ -227,8 +227,10 @@ __device__ __forceinline__ uint32_t sw64_off(int r, int c) {
     return (uint32_t)(r * kRowBytes + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
-// tiles[t] = (op, first pair, count, 0); work item w = (tile w / mgroups, row group
-// w % mgroups).  map_hi / map_lo: 2-D tensor maps of the split FP16 operator tables
+// tiles[t] = (op, first pair, count, chain); work item w = (tile w / mgroups, row group
+// w % mgroups).  chain = 1 (only with mgroups = 1): item w + gridDim.x, this CTA's next,
+// has the same output box in every column and its products are added to this item's
+// before they are written.  kcount (null: all items c + k G) holds each CTA's item count.  map_hi / map_lo: 2-D tensor maps of the split FP16 operator tables
 // (scaled by 2^texp), rows = op * Mr + row (Mr rows per operator), columns Kp, box = 32
 // columns x kRows rows, 64-byte swizzle.  in_hi / in_lo: the input vectors of all boxes
 // scaled by 2^bexp[box] and split, Kp FP16 per box.  out: ostride floats per box, of
@@ -240,10 +242,12 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
                                              const int* __restrict__ pin, const int* __restrict__ pout,
                                              const int* __restrict__ bexp, const __half* __restrict__ in_hi,
                                              const __half* __restrict__ in_lo, float* __restrict__ out,
-                                             int* __restrict__ err) {
+                                             int* __restrict__ err, const int* __restrict__ kcount) {
     using S = Shape<SLABS, N>;
     const int G = gridDim.x;
-    const int K = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + G - 1) / G : 0;  // items of this CTA
+    // items of this CTA: every G-th from blockIdx.x, or the first kcount[blockIdx.x] of them
+    const int K = kcount ? kcount[blockIdx.x]
+                         : (nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + G - 1) / G : 0);
     if (K == 0) return;                   // uniform: nothing allocated yet
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -255,7 +259,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
     __shared__ uint64_t drain_bar;            // all MMAs of the CTA done
     __shared__ uint32_t tmem_base;
     __shared__ int s_out[N];
-    __shared__ float s_oscale[N];             // output unscale per pair
+    __shared__ __align__(16) float s_oscale[N];   // output unscale per pair
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -444,10 +448,20 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
         };
         load_meta(0);
         bar_named(kFoldBar, kFoldThreads);
+        // A chain: consecutive items of this CTA with the same output box in every column
+        // (tile.w = 1: the next item of this CTA continues it).  Its sums stay in acc
+        // across its items and are written once, after the last.  Each fold adds its
+        // columns already unscaled (by powers of two, so the sums round as if unscaled
+        // at the end).
+        bool cont_prev = false;
+        const float4* osc4 = reinterpret_cast<const float4*>(s_oscale + my_col0);
         for (int k = 0; k < K; ++k) {
             const int w = (int)blockIdx.x + k * G;
+            const bool cont = mgroups == 1 && tiles[w / mgroups].w != 0;
+            if (!cont_prev) {
 #pragma unroll
-            for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+                for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+            }
             bool ok = true;
             for (int j = 0; j < nfg; ++j) {
                 const int f = k * nfg + j, b = f & 1;
@@ -462,20 +476,27 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
                     float v[16];
                     tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)j0, v);
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) acc[j0 + jj] += v[jj];
+                    for (int jj = 0; jj < 16; jj += 4) {
+                        const float4 sc = osc4[(j0 + jj) >> 2];
+                        acc[j0 + jj] = fmaf(v[jj], sc.x, acc[j0 + jj]);
+                        acc[j0 + jj + 1] = fmaf(v[jj + 1], sc.y, acc[j0 + jj + 1]);
+                        acc[j0 + jj + 2] = fmaf(v[jj + 2], sc.z, acc[j0 + jj + 2]);
+                        acc[j0 + jj + 3] = fmaf(v[jj + 3], sc.w, acc[j0 + jj + 3]);
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(&acc_empty[b]);
             }
             if (bar_named_or(kFoldBar, kFoldThreads, !ok)) break;   // uniform across the fold warps
             const int row = (w % mgroups) * S::kRows + my_slab * 128 + quarter * 32 + lane;
-            if (row < M) {
+            if (!cont && row < M) {
 #pragma unroll
                 for (int j = 0; j < 128; ++j) {
                     const int ob = s_out[my_col0 + j];
-                    if (ob >= 0) atomicAdd(out + (size_t)ob * ostride + row, acc[j] * s_oscale[my_col0 + j]);
+                    if (ob >= 0) atomicAdd(out + (size_t)ob * ostride + row, acc[j]);
                 }
             }
+            cont_prev = cont;
             if (k + 1 < K) {
                 bar_named(kFoldBar, kFoldThreads);   // every fold thread is done with item k's table
                 load_meta(k + 1);
@@ -501,9 +522,9 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
              int Kp, int ostride, int Mr, int mgroups, int nitems, const int4* __restrict__ tiles,               \
              const int* __restrict__ pin, const int* __restrict__ pout, const int* __restrict__ bexp, int texp,  \
              const __half* __restrict__ in_hi, const __half* __restrict__ in_lo, float* __restrict__ out,        \
-             int* __restrict__ err) {                                                                            \
+             int* __restrict__ err, const int* __restrict__ kcount) {                                            \
         pair_tc_body<SLABS, N, FOLD>(map_hi, map_lo, texp, M, Kp, ostride, Mr, mgroups, nitems, tiles, pin, pout,     \
-                               bexp, in_hi, in_lo, out, err);                                                    \
+                               bexp, in_hi, in_lo, out, err, kcount);                                            \
     }
 KF_TC_KERNEL(k_u2u_tc, kFoldStages)
 KF_TC_KERNEL(k_m2l_tc, kFoldStages)

@@ -12,8 +12,9 @@
 namespace kifmm {
 
 struct PairTiles {
-    DBuf<int4> tiles;               // (op, first pair, pair count, unused); count <= kPairTile
+    DBuf<int4> tiles;               // (op, first pair, pair count, chain flag); count <= the tile cap
     DBuf<int> pin, pout;            // input box, output box per pair
+    DBuf<int> kcount;               // mixed M2L with chains: tiles per CTA (else empty)
     std::vector<int> level_tile;    // per level: [level_tile[l], level_tile[l+1]) tiles (U2U/L2L)
     int ntiles = 0;
     int64_t npairs = 0;
@@ -95,6 +96,7 @@ struct Plan {
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
     PairTiles u2u, m2l, l2l;
+    int64_t m2l_chain_pairs = 0;    // mixed: V pairs in chains (targets written once per chain)
     PairTiles proj_up, proj_x;      // mixed: (box -> box) projections of the S2U leaves'
                                     // up-check and the X-list boxes' down-check potentials
     DBuf<float> zu, zd;             // mixed: projected check potentials, nbox x Ku / Kd

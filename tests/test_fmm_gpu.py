@@ -217,6 +217,40 @@ def test_target_source_model():
         assert rel(plan.matvec(q).cpu().numpy(), ref) < tol
 
 
+def test_m2l_chains_on_flat_faces():
+    """M2L chains: runs of up to 128 targets of one level whose V lists hold the same
+    offsets, whose products over all those offsets are summed on chip and written once.
+    The 270k-point cube's flat faces give long runs, so most V pairs are chained.  The
+    chained mixed matvec agrees with the FP64 matvec over every target, and with the
+    oracle on a seeded sample, to the mixed form's accuracy.  The sphere of the other
+    tests, with no two targets alike, keeps the plain offset-sorted list."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    m = synth.workload("demag_cube_270k")["mesh"]
+    xyz, w, nrm = gpu_points(m)
+    q = (nrm[2] * w).contiguous()                 # sigma = n . z-hat
+    tree = Tree(xyz, max_leaf=64)
+    mx = Plan(tree, kernel="dl", p=10, precision="mixed", src_nrm=nrm)
+    st = mx.stats()
+    assert st["m2l_chain_pairs"] > 0.2 * st["m2l_pairs"], st
+    a = mx.matvec(q)
+    mx.check()
+    fp = Plan(tree, kernel="dl", p=10, precision="fp64", src_nrm=nrm)
+    assert fp.stats()["m2l_chain_pairs"] == 0
+    b = fp.matvec(q)
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    err_fp = rel(a, b)
+    h = quadrature_points(m.tri, m.sph)
+    idx = np.random.default_rng(5).choice(m.n, 2048, replace=False)
+    ref = oracle.direct("dl", h[0], h[0], (h[2][2] * h[1]), src_nrm=h[2], idx=idx)
+    err_or = rel(a[idx], ref)
+    print("270k cube DL: %d of %d V pairs chained, vs FP64 %.2e, vs oracle %.2e"
+          % (st["m2l_chain_pairs"], st["m2l_pairs"], err_fp, err_or))
+    assert err_fp < 1e-6 and err_or < 1e-6
+    m5, _, (sx, sw, sn), _, _ = case("sphere")
+    ps = Plan(Tree(sx, max_leaf=40), kernel="dl", p=10, precision="mixed", src_nrm=sn)
+    assert ps.stats()["m2l_chain_pairs"] == 0
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_matvec_host_buffers(prec):
     """kifmm_fmm_matvec_host reproduces kifmm_fmm_matvec up to the order of the matvec's
