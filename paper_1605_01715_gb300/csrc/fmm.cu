@@ -1072,7 +1072,9 @@ void make_tiles(std::vector<Triple>& tr, std::vector<int4>& tiles, std::vector<i
 // each target once per chain instead of once per offset.  The other pairs form tiles
 // by offset as before.  Chains (longest first), then those tiles in offset order, go
 // to the CTA with the fewest tiles.  (Counting a chained tile as half a plain one, for
-// the scatter it skips, measured slower: 0.564 against 0.535 ms on the 1M cube.)
+// the scatter it skips, measured slower: 0.564 against 0.535 ms on the 1M cube.)  A
+// chain longer than a CTA's share of all tiles is cut into near-equal pieces, each
+// written once, so no CTA waits on one long chain.
 // kcount receives each CTA's tile count, and the interleaved list is padded with empty
 // tiles that no CTA reads.  With no chain the plain offset-sorted list is kept (kcount
 // empty).
@@ -1125,6 +1127,20 @@ void m2l_schedule(std::vector<Triple>& tr, const std::vector<int>& level, int ca
     std::vector<int4> single;
     std::vector<int> spin, spout;
     make_tiles(rest, single, spin, spout, cap);
+    size_t total = single.size();
+    for (const auto& ch : chains) total += ch.size();
+    const size_t share = std::max<size_t>(2, total / (size_t)G);
+    std::vector<std::vector<int4>> pieces;
+    for (auto& ch : chains) {
+        const size_t np = (ch.size() + share - 1) / share;
+        for (size_t q = 0; q < np; ++q) {
+            const size_t a = ch.size() * q / np, b = ch.size() * (q + 1) / np;
+            std::vector<int4> pc(ch.begin() + a, ch.begin() + b);
+            pc.back().w = 0;                              // the piece's targets are written here
+            pieces.push_back(std::move(pc));
+        }
+    }
+    chains.swap(pieces);
     // pair lists: the chains' first, then the others'
     const int sbase = (int)cpin.size();
     pin = cpin;
