@@ -53,6 +53,9 @@ def test_null_arguments_rejected_without_a_gpu(lib):
     assert lib.kifmm_fmm_matvec(None, None, None, None) == -1
     lib.kifmm_tree_destroy.argtypes = [ctypes.c_void_p]
     assert lib.kifmm_tree_destroy(None) == 0
+    lib.kifmm_fmm_matvec_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_void_p]
+    assert lib.kifmm_fmm_matvec_host(None, None, None, 1, None) == -1
 
 
 def test_forest_arguments_rejected_without_a_gpu(lib):
