@@ -15,6 +15,14 @@ field at the centre of a disc of area a_j on a surface of mean curvature H_j
 carrying unit density (pi rho H with rho = sqrt(a_j/pi)).  ``self_scale='literal'``
 uses the printed sqrt(a_j/pi) H_j instead.  H_j = 1/R on a sphere, 0 when flat.
 
+Field and force (Sec. II.C, Eqs. Eb and pol_discret, the force on a body and its
+surface force density), for total surface charge sigma = sigma_f + sigma_b:
+
+    E^j   = E0 + (1/4pi) [ sum_{k != j} (r_j - r_k)/|r_j - r_k|^3 sigma_k a_k + c_j sigma_j n_j ]
+    F_b   = sum_{j in body b} eps_m sigma_j E^j a_j                             (f = eps_m sigma E)
+
+with E0 the applied uniform field (the free-volume-charge term of Eq. Ef is absent).
+
 Demagnetization (Sec. II.B and III.A.1):
 
     phi_2(r_i) = (1/4pi) sum_j n_j.(r_i - r_j)/|r_i - r_j|^3 phi_1(r_j) w_j
@@ -57,6 +65,51 @@ def polarization_operator(xyz, nrm, area, eps_in, eps_out, curvature, self_scale
         return ebar * sigma + deps * (adl + c * sigma) / FOUR_PI
 
     return matvec
+
+
+def field(trg, src, q):
+    """The raw field sum f_i = sum_j (r_i - r_j)/|r_i - r_j|^3 q_j, (3, n_trg): component
+    k is the adjoint-double-layer sum with the constant target normal e_k (Eq. kernel_pol
+    is the gradient kernel; dotted with e_k it is that component)."""
+    trg = np.asarray(trg, dtype=np.float64)
+    out = np.empty((3, trg.shape[1]))
+    for k in range(3):
+        e = np.zeros_like(trg)
+        e[k] = 1.0
+        out[k] = direct("adl", trg, src, q, trg_nrm=e)
+    return out
+
+
+def polarization_field(xyz, nrm, area, sigma, curvature, e0=(0.0, 0.0, 0.0), self_scale="disc"):
+    """E^j at the elements (3, n) for total surface charge sigma (Eq. pol_discret with
+    the self-patch term c_j sigma_j n_j) plus the applied field E0."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    c = self_coefficient(area, curvature, self_scale)
+    E = (field(xyz, xyz, sigma * area) + c * sigma * np.asarray(nrm)) / FOUR_PI
+    return E + np.asarray(e0, dtype=np.float64)[:, None]
+
+
+def polarization_force(xyz, nrm, area, sigma, curvature, body, eps_out, e0=(0.0, 0.0, 0.0), self_scale="disc"):
+    """Force on each body, (n_body, 3): F_b = sum_{j in b} eps_m sigma_j E^j a_j."""
+    E = polarization_field(xyz, nrm, area, sigma, curvature, e0, self_scale)
+    f = eps_out * sigma * area * E
+    body = np.asarray(body)
+    nb = int(body.max()) + 1
+    return np.stack([np.bincount(body, weights=f[k], minlength=nb) for k in range(3)], axis=1)
+
+
+def polarization_rhs(xyz, nrm, area, eps_in, eps_out, curvature, e0=(0.0, 0.0, 0.0), sigma_f=None,
+                     self_scale="disc"):
+    """b = (1 - ebar) sigma_f - deps (E_f . n)  (Eq. rhs): E_f the applied field plus the
+    field of the free surface charge sigma_f (Eq. Ef without its volume term), at the
+    elements as in Eq. pol_discret."""
+    eps_in = np.asarray(eps_in, dtype=np.float64)
+    ebar = 0.5 * (eps_in + eps_out)
+    deps = eps_out - eps_in
+    nrm = np.asarray(nrm, dtype=np.float64)
+    sf = np.zeros(nrm.shape[1]) if sigma_f is None else np.asarray(sigma_f, dtype=np.float64)
+    Ef = polarization_field(xyz, nrm, area, sf, curvature, e0, self_scale)
+    return (1.0 - ebar) * sf - deps * (Ef * nrm).sum(axis=0)
 
 
 def polarization_rhs_uniform_field(nrm, eps_in, eps_out, e0):

@@ -273,3 +273,92 @@ def test_dielectric_sphere_in_uniform_field():
     assert err[(16, "disc")] < 1e-3
     assert err[(16, "disc")] < 0.5 * err[(8, "disc")]
     assert err[(16, "literal")] > 5 * err[(16, "disc")]
+
+
+# ---------------------------------------------------------------- field and force (Sec. II.C)
+def test_field_of_a_charged_sphere():
+    """Field sum of a uniformly charged unit sphere: zero inside, Q/(4 pi r^2) r-hat
+    outside with Q = 4 pi sigma (the 1/4pi of Eq. Eb applied), converging as h^2.  Each
+    component is checked, so a swapped axis or sign fails."""
+    errs = []
+    for f in (16, 32):
+        xyz, w, n = sphere(f)
+        Ein = bie.field(INTERIOR, xyz, w) / PI4
+        Eout = bie.field(EXTERIOR, xyz, w) / PI4
+        r = np.linalg.norm(EXTERIOR, axis=0)
+        errs.append(max(np.abs(Ein).max(), np.abs(Eout - EXTERIOR / r**3).max()))
+    assert errs[1] < 1e-3
+    assert errs[1] < 0.3 * errs[0]
+
+
+def test_surface_field_is_the_average_of_both_sides():
+    """At the elements of a charged sphere (sigma = 1) the normal component of the
+    discrete field with its self-patch term tends to the mean of the outer (sigma) and
+    inner (0) normal fields, E^j . n_j -> 1/2 (the principal value), at O(h).  (The
+    one-point rule does not resolve the tangential part at an element: neighbours at
+    distance h each contribute O(1) there.  Summed over a body, those pair terms cancel
+    two by two, which the force tests below rely on.)"""
+    errs = []
+    for f in (16, 32):
+        xyz, w, n = sphere(f)
+        E = bie.polarization_field(xyz, n, w, np.ones(w.size), np.ones(w.size))
+        errs.append(np.abs((E * n).sum(axis=0) - 0.5).max())
+    assert errs[1] < 0.01
+    assert errs[1] < 0.6 * errs[0]
+
+
+def _solve_pack(centres, radii, eps_in_body, f, e0=(0.0, 0.0, 0.0), charges=None, eps_out=1.0):
+    m = synth.pack_mesh(np.asarray(centres, float), np.asarray(radii, float), f)
+    xyz, w, n = quadrature_points(m.tri, m.sph)
+    eps = np.asarray(eps_in_body, float)[m.body]
+    curv = 1.0 / m.sph[:, 3]
+    sf = np.zeros(m.n)
+    if charges is not None:
+        sf = np.asarray(charges, float)[m.body] / (PI4 * np.asarray(radii, float)[m.body] ** 2)
+    A = bie.polarization_operator(xyz, n, w, eps, eps_out, curv)
+    b = bie.polarization_rhs(xyz, n, w, eps, eps_out, curv, e0, sf)
+    sb, _, _, ok = gmres(A, b, tol=1e-12, restart=60)
+    assert ok
+    F = bie.polarization_force(xyz, n, w, sf + sb, curv, m.body, eps_out, e0)
+    return m, sf, sb, F
+
+
+def test_uncharged_sphere_feels_no_force_in_a_uniform_field():
+    """A neutral dielectric sphere in a uniform field: its bound charge is odd under
+    inversion and the field even, so sigma E is odd and the net force vanishes (the
+    geodesic mesh is centrally symmetric)."""
+    m, sf, sb, F = _solve_pack([[0.0, 0.0, 0.0]], [1.0], [10.0], 8, e0=(0.3, -0.2, 1.0))
+    scale = np.abs(sb).max() ** 2 * PI4
+    assert np.abs(F).max() < 1e-10 * scale
+    assert abs((sb * quadrature_points(m.tri, m.sph)[1]).sum()) < 1e-10 * scale   # no net bound charge
+
+
+@pytest.mark.parametrize("eps_in", [2.0, 10.0])
+def test_charged_spheres_coulomb_limit(eps_in):
+    """Two charged spheres of radius 1 at distance 20 in a medium eps_m = 2.
+    - eps_in = eps_m: the solve gives sigma_b = -sigma_f / 2 exactly (Eq. Ax and Eq.
+      rhs with deps = 0), so each body carries Q_i / eps_m in all;
+    - eps_in = 10: the same total charge up to the one-point rule's O(h) error in the
+      surface field (f = 8 vs f = 16 checked to converge);
+    and F = eps_m q1 q2 / (4 pi d^2) along the axis with q_i those totals (the shell
+    theorem: the force on a uniform shell is that on its centre), equal and opposite.
+    With eps_in = eps_m the charge is uniform and that holds to the solve's tolerance.
+    With eps_in = 10 it holds up to the induced-dipole terms, (R/d)^3 ~ 1e-4 relative,
+    and the self-patch term c_j sigma_j n_j: on the now uneven charge it leaves an O(h)
+    net self-force, which halves from f = 8 to f = 16."""
+    d, Q1, Q2, em = 20.0, 3.0, 2.0, 2.0
+    errs, ferr = [], []
+    for f in (8, 16):
+        m, sf, sb, F = _solve_pack([[0.0, 0.0, 0.0], [d, 0.0, 0.0]], [1.0, 1.0], [eps_in, eps_in], f,
+                                   charges=[Q1, Q2], eps_out=em)
+        w = quadrature_points(m.tri, m.sph)[1]
+        tot = [((sf + sb) * w)[m.body == b].sum() for b in (0, 1)]
+        errs.append(max(abs(tot[0] - Q1 / em) / Q1, abs(tot[1] - Q2 / em) / Q2))
+        coul = em * tot[0] * tot[1] / (PI4 * d * d)
+        ferr.append(max(abs(F[1, 0] - coul), abs(F[0, 0] + coul)) / coul)
+        assert np.abs(F[:, 1:]).max() < 1e-6 * coul
+    if eps_in == em:
+        assert max(errs) < 1e-9 and max(ferr) < 3e-4
+    else:
+        assert errs[1] < 0.6 * errs[0] and errs[1] < 5e-3
+        assert ferr[1] < 0.6 * ferr[0] and ferr[1] < 0.01
