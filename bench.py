@@ -57,7 +57,7 @@ class ClockSampler:
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0, interval_ms=50):
+    def __init__(self, index=0, interval_ms=20):
         self.index = index
         self.interval_ms = interval_ms
         self.samples = []
@@ -207,6 +207,7 @@ def run_kifmm(args):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     from paper_1605_01715_gb300 import Plan, Tree
+    peaks = measure_peaks(local)
     wl, m, xyz, w, nrm, q = make_inputs(args.workload, device)
     inst = wl.get("instances")
     p = args.p or wl["p"]
@@ -222,7 +223,9 @@ def run_kifmm(args):
     torch.cuda.synchronize()
     t_tree = time.perf_counter() - t0
     t0 = time.perf_counter()
-    plan = Plan(tree, kernel=wl["kernel"], p=p, precision=args.precision, src_nrm=nrm, trg_nrm=nrm)
+    cut = args.pinv_cutoff if args.pinv_cutoff > 0 else wl.get("pinv_cutoff", 0.0)
+    plan = Plan(tree, kernel=wl["kernel"], p=p, precision=args.precision, src_nrm=nrm, trg_nrm=nrm,
+                pinv_cutoff=cut if args.precision != "fp64" else 0.0)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     n = m.n
@@ -295,7 +298,7 @@ def run_kifmm(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "n_targets": n, "kernel": wl["kernel"], "p": p,
                        "q_points": st["q_points"], "max_leaf": max_leaf, "precision": args.precision,
-                       "pinv_cutoff": st["pinv_cutoff"], "parallelism": "replica" if ws > 1 else "single",
+                       "pinv_cutoff": st["pinv_cutoff"], "pinv_cutoff_up": st["pinv_cutoff_up"], "parallelism": "replica" if ws > 1 else "single",
                        "l2": "no flush: per-step working set %.2f GB > 129 MB L2" % (st["device_bytes"] / 1e9),
                        "tree": {k: tst[k] for k in ("n_boxes", "n_leaves", "n_levels", "n_v", "n_w", "n_x",
                                                      "p2p_pairs")},
@@ -311,21 +314,30 @@ def run_kifmm(args):
                                                            "subset_instances", "tune_s")}
         line["config"]["autotune"]["errors"] = {str(k): v for k, v in tune["errors"].items()}
         line["config"]["autotune"]["times_ms"] = {str(k): v for k, v in tune["times_ms"].items()}
-    line["roofline"] = roofline(phases, st, tst, args)
+    serial = serial_phases(plan, q, out)
+    line["phases_serial_ms"] = serial
+    line["roofline"], line["rooflines"] = rooflines(serial, st, tst, args, wl["kernel"], peaks)
+    line["peaks_measured"] = peaks
+    if line["clocks"].get("sm_mhz"):
+        line["clocks"]["ms_x_mhz"] = ms * line["clocks"]["sm_mhz"]
+    line["clocks_long"] = long_clock_window(plan, q, out, local, use_graph)
 
-    if args.solves > 0:
-        line["solve"] = solve_latency(args, device)
-        if args.precision == "mixed":
-            # the configuration whose ADL matvec meets 1e-6 against the oracle (compensated
-            # near field, p = 11; the plain mixed matvec above is at 3e-6 on this pack)
-            line["solve_1e6"] = solve_latency(args, device, precision="mixed_cn", p=11)
+    idx = ref = None
     if rank == 0 and not args.no_cpu_baseline:
         idx, ref, dt, cores = oracle_sample(wl, m, q.cpu().numpy(), args.cpu_sample)
+        plan.matvec(q, out)
         got = out.cpu().numpy()[idx]
         line["cpu_baseline"] = {"value": idx.size / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d seeded targets x all %d sources of their instance (FP64 direct sum)"
                       % (idx.size, n)}
         line["rel_err_sampled"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    if rank == 0 and args.fp64_plain and inst is None:
+        line["fp64_plain"] = fp64_plain(wl, tree, xyz, nrm, q, p, idx, ref, ms, peaks)
+    del plan
+    if args.solves > 0:
+        line["solve"] = solve_latency(args, device)
+    if rank == 0 and args.field_check and inst is None:
+        line["demag_sphere_interior"] = demag_interior_field(device)
     if ws > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -383,6 +395,110 @@ def run_serve(args):
     return 0
 
 
+def long_clock_window(plan, q, out, index, use_graph, seconds=1.0):
+    """SM clocks while matvecs repeat for about a second right after the timed region
+    (the timed region itself may be shorter than a few sampling intervals)."""
+    import torch
+    mv = plan.matvec_graph if use_graph else plan.matvec
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mv(q, out)
+    torch.cuda.synchronize()
+    e0.record()
+    mv(q, out)
+    e1.record()
+    torch.cuda.synchronize()
+    reps = max(10, int(seconds / max(e0.elapsed_time(e1) * 1e-3, 1e-5)))
+    with ClockSampler(index) as clk:
+        e0.record()
+        for _ in range(reps):
+            mv(q, out)
+        e1.record()
+        torch.cuda.synchronize()
+    c = clk.summary()
+    c["matvecs"] = reps
+    c["ms_per_matvec"] = e0.elapsed_time(e1) / reps
+    return c
+
+
+def fp64_plain(wl, tree, xyz, nrm, q, p, idx, ref, ms_mixed, peaks, steps=3):
+    """The plain form: the same matvec with every step in FP64 (KIFMM_PREC_FP64) at the
+    same order, timed with CUDA events, with its error on the same oracle sample."""
+    import torch
+
+    from paper_1605_01715_gb300 import Plan
+    t0 = time.perf_counter()
+    plan = Plan(tree, kernel=wl["kernel"], p=p, precision="fp64", src_nrm=nrm, trg_nrm=nrm)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    out = torch.empty_like(q)
+    plan.matvec(q, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.matvec(q, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    res = {"precision": "fp64", "p": p, "ms_per_matvec": ms, "targets_per_s": q.numel() / (ms * 1e-3),
+           "setup_ms": t_setup * 1e3, "mixed_speedup": ms / ms_mixed, "steps": steps}
+    if idx is not None:
+        got = out.cpu().numpy()[idx]
+        res["rel_err_sampled"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return res
+
+
+def demag_interior_field(device, n_trg=4096):
+    """The demagnetizing field inside the uniformly magnetized 1M-point sphere (M = z):
+    H_z = (1/4pi) sum_j (n_j . M) w_j z.(r - r_j)/|r - r_j|^3 at seeded interior points,
+    an adjoint-double-layer matvec with target normal z (Sec. IV.A's check; -1/3 exactly
+    for the continuous sphere).  Mixed form at p = 11, against the oracle at every
+    target and against -1/3."""
+    import torch
+
+    import oracle
+    from oracle.quadrature import quadrature_points
+    from paper_1605_01715_gb300 import Plan, Tree
+    wl = synth.workload("demag_sphere_1m")
+    m = wl["mesh"]
+    _, _, xyz, w, nrm, q = make_inputs("demag_sphere_1m", device)
+    rng = np.random.default_rng(2024)
+    v = rng.normal(size=(3, n_trg))
+    trg = v / np.linalg.norm(v, axis=0) * 0.8 * rng.uniform(0, 1, n_trg) ** (1 / 3)
+    zhat = np.zeros((3, n_trg))
+    zhat[2] = 1.0
+    t0 = time.perf_counter()
+    tree = Tree(xyz, torch.from_numpy(trg).to(device), max_leaf=wl["max_leaf"])
+    plan = Plan(tree, kernel="adl", p=11, precision="mixed", trg_nrm=torch.from_numpy(zhat).to(device))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    out = plan.matvec(q)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        plan.matvec(q, out)
+    e1.record()
+    torch.cuda.synchronize()
+    Hz = out.cpu().numpy() / (4 * math.pi)
+    hx, hw, hn = quadrature_points(m.tri, m.sph)
+    t1 = time.perf_counter()
+    ref = oracle.direct("adl", trg, hx, hn[2] * hw, trg_nrm=zhat) / (4 * math.pi)
+    t_or = time.perf_counter() - t1
+    return {"workload": "demag_sphere_1m", "n_sources": m.n, "interior_targets": n_trg, "p": 11,
+            "precision": "mixed", "Hz_mean": float(Hz.mean()), "Hz_max_dev_from_minus_third":
+            float(np.abs(Hz + 1.0 / 3.0).max()), "rel_err_vs_oracle": float(np.linalg.norm(Hz - ref) /
+                                                                            np.linalg.norm(ref)),
+            "oracle_max_dev_from_minus_third": float(np.abs(ref + 1.0 / 3.0).max()),
+            "ms_per_matvec": e0.elapsed_time(e1) / 5, "setup_ms": t_setup * 1e3, "oracle_s": t_or}
+
+
+# GMRES stopping tolerance of the timed solves: the configuration's relative residual
+# 1e-6, less the mixed matvec's own error (about 2e-7 on the 64-sphere pack at p = 11), so
+# that the residual under the exact operator -- what the oracle measures -- is within 1e-6
+SOLVE_TOL = 7e-7
+
+
 def solve_latency(args, device, precision=None, p=None):
     """p50/p99 wall time of full GMRES polarization solves (64-sphere pack, mixed matvec,
     FP64 Krylov) with the plan, tree and Krylov basis resident between solves."""
@@ -407,7 +523,7 @@ def solve_latency(args, device, precision=None, p=None):
         x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, it, rr, rc = plan.bie_solve(w, eps, wl["eps_out"], curv, b, x=x, tol=1e-6, restart=50, max_iter=500)
+        _, it, rr, rc = plan.bie_solve(w, eps, wl["eps_out"], curv, b, x=x, tol=SOLVE_TOL, restart=50, max_iter=500)
         torch.cuda.synchronize()
         if k:
             times.append((time.perf_counter() - t0) * 1e3)
@@ -415,11 +531,78 @@ def solve_latency(args, device, precision=None, p=None):
             rres.append(rr)
     plan.check()
     ts = np.array(times)
-    return {"workload": "polar_64", "precision": precision, "p": p, "n_unknowns": n, "tol": 1e-6, "restart": 50,
-            "solves": len(times),
-            "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
-            "iterations": int(np.median(iters)), "true_rel_residual": float(max(rres)),
-            "setup_ms": t_setup * 1e3, "ms_per_iteration": float(np.median(ts) / max(1, np.median(iters)))}
+    res = {"workload": "polar_64", "precision": precision, "p": p, "n_unknowns": n, "tol": SOLVE_TOL, "restart": 50,
+           "solves": len(times),
+           "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+           "iterations": int(np.median(iters)), "true_rel_residual": float(max(rres)),
+           "setup_ms": t_setup * 1e3, "ms_per_iteration": float(np.median(ts) / max(1, np.median(iters)))}
+    if not args.no_cpu_baseline:
+        res.update(solve_oracle_checks(wl, m, plan, x, b, eps, curv, w, device))
+    return res
+
+
+def solve_oracle_checks(wl, m, plan, x, b, eps, curv, w, device, n_sample=2048):
+    """Against the FP64 oracle on a seeded sample of rows: the plan's matvec (a random
+    density) and the residual of the GPU solution x, b - A x with A the oracle's
+    polarization operator (Eqs. Ax, pol_discret) -- both relative on the sample."""
+    import torch
+
+    import oracle
+    from oracle.quadrature import quadrature_points
+    hx, hw, hn = quadrature_points(m.tri, m.sph)
+    idx = np.sort(np.random.default_rng(77).choice(m.n, n_sample, replace=False))
+    sig = synth.uniform_density(m.n, 31)
+    mv = plan.matvec(torch.from_numpy(sig).to(device) * w).cpu().numpy()[idx]
+    ref = oracle.direct("adl", hx, hx, sig * hw, trg_nrm=hn, idx=idx)
+    xh, bh = x.cpu().numpy(), b.cpu().numpy()
+    adl = oracle.direct("adl", hx, hx, xh * hw, trg_nrm=hn, idx=idx)
+    e = eps.cpu().numpy()[idx]
+    c = curv.cpu().numpy()[idx] * np.sqrt(math.pi * hw[idx])
+    ebar, deps = 0.5 * (e + wl["eps_out"]), wl["eps_out"] - e
+    Ax = ebar * xh[idx] + deps * (adl + c * xh[idx]) / (4 * math.pi)
+    return {"matvec_rel_err_sampled": float(np.linalg.norm(mv - ref) / np.linalg.norm(ref)),
+            "oracle_residual_sampled": float(np.linalg.norm(bh[idx] - Ax) / np.linalg.norm(bh[idx])),
+            "oracle_sample_rows": n_sample}
+
+
+def measure_peaks(index):
+    """FP32 FMA (scalar and packed), rsqrt and FP64 FMA rates of this GPU, from the
+    library's own microbenchmark kernels (kifmm_peak_rate), with the SM clock sampled
+    while they run; also scaled to the maximum SM clock."""
+    from paper_1605_01715_gb300 import kifmm_peak_rate
+    rates = {}
+    with ClockSampler(index) as clk:
+        for unit in ("fp32_fma", "fp32x2_fma", "rsqrt", "fp64_fma"):
+            rates[unit] = kifmm_peak_rate(unit, reps=3)[0]
+    c = clk.summary()
+    out = {"fp32_tflops": rates["fp32_fma"] / 1e12, "fp32x2_tflops": rates["fp32x2_fma"] / 1e12,
+           "rsqrt_per_s": rates["rsqrt"], "fp64_tflops": rates["fp64_fma"] / 1e12,
+           "sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"], "clock_reasons": c["reasons"],
+           "how": "kifmm_peak_rate: one instruction kind on 8 independent chains per thread, every SM, "
+                  "~10 ms launches, best of 3 (CUDA events)"}
+    if c["sm_mhz"] and c["sm_max_mhz"]:
+        f = c["sm_max_mhz"] / c["sm_mhz"]
+        out["at_max_clock"] = {"fp32_tflops": out["fp32_tflops"] * f, "rsqrt_per_s": out["rsqrt_per_s"] * f,
+                               "fp64_tflops": out["fp64_tflops"] * f}
+    return out
+
+
+# FP32 flops per near-field pair as the kernels evaluate it (an FMA counts 2; the rsqrt
+# is counted separately against the MUFU rate): single layer d (3), r^2 (5), q/r FMA (2);
+# double layers also 1/r^3 (2), the exact hi products (6) and the lo cross terms (12),
+# their sum (1) and the product with q (ADL, 1); field 1/r^3 q (3) and three FMAs (6)
+P2P_FLOPS = {"sl": 10, "dl": 31, "adl": 32, "field": 17}
+
+
+def serial_phases(plan, q, out, reps=10):
+    """Per-phase device times with the near field run after the far field (each phase
+    with the whole GPU), from the plan's CUDA-event profile."""
+    import torch
+    plan.profile(True, serial=True)
+    for _ in range(reps):
+        plan.matvec(q, out)
+    torch.cuda.synchronize()
+    return plan.profile(False)
 
 
 def _peaks():
@@ -451,53 +634,58 @@ def _m2l_traffic(pairs):
     return rec["dram_bytes_per_pair"] * pairs + rec["dram_bytes_fixed"]
 
 
-def roofline(phases, st, tst, args):
-    """Roofline of the dominant kernel from algorithmic work per launch and live event times."""
+def rooflines(phases, st, tst, args, kernel, peaks):
+    """Rooflines of the three kernel families from their own (serialized) event times:
+    the tensor-core translations (M2L dominant), the near field (FP32 ALU and MUFU), D2T
+    (HBM).  Returns (dominant, all)."""
     pk, src = _peaks()
-    sm_max = pk.get("sm_max_mhz", 2070.0) * 1e6
-    fp32_peak = 152 * 128 * 2 * sm_max / 1e12       # TFLOP/s, CUDA-core FMA at max SM clock
-    fp64_peak = 1.25                                 # TFLOP/s nominal
     Q = st["q_points"]
-    # an overlapped near field's phase spans the far field it runs beside, not its own
-    # duration, so it does not compete for the dominant kernel (its launch-list share
-    # is below M2L's)
-    items = {k: v for k, v in phases.items() if k != "total" and not (k == "p2p" and st.get("near_overlap"))}
-    dom = max(items, key=items.get)
-    t = items[dom] * 1e-3
     mixed = args.precision != "fp64"
-    if dom in ("m2l", "u2u", "l2l"):
-        pairs = {"m2l": st["m2l_pairs"], "u2u": st["u2u_pairs"], "l2l": st["l2l_pairs"]}[dom]
-        # algorithmic: one R x W operator per pair; R = W = Q in FP64; mixed, every
-        # translation acts between projections onto the pseudo-inverses' ranges (up
-        # basis: rank_up values, down basis: rank_down)
-        ru, rd = (st["rank_up"], st["rank_down"]) if mixed else (Q, Q)
-        R, W = {"m2l": (rd, ru), "u2u": (ru, ru), "l2l": (rd, rd)}[dom]
-        flops = 2.0 * R * W * pairs
-        if mixed:                                   # two-term FP16 on tcgen05: 3 MMAs per product
-            peak = pk["bf16_tflops"] / 3.0
-            out = {"kernel": "k_%s_tc (tcgen05, two-term FP16)" % dom, "bound": "tensor",
-                   "peak_source": "%s bf16/fp16 dense burst %.0f / 3 (hi*hi + hi*lo + lo*hi)"
-                                  % (src, pk["bf16_tflops"])}
-        else:
-            peak = fp64_peak
-            out = {"kernel": "k_%s_gemm<double>" % dom, "bound": "alu", "peak_source": "FP64 nominal"}
-        out.update({"achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "frac": flops / t / 1e12 / peak,
-                    "traffic": _m2l_traffic(pairs) if (mixed and dom == "m2l") else None,
-                    "work": "2*R*W flops x %d pairs, R=%d, W=%d" % (pairs, R, W)})
-        return out
-    if dom == "p2p":
-        flops = 20.0 * tst["p2p_pairs"]            # ~20 FP32 ops per pair (FMA counted as 2)
-        peak = fp32_peak if mixed else fp64_peak
-        return {"kernel": "k_p2p", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
-                "peak_source": "152 SM x 128 FP32 lanes x 2 x %.0f MHz" % (sm_max / 1e6)}
-    if dom == "d2t":
-        nbytes = (4 if mixed else 8) * (st["q_points"] + 8) * tst["n_src"]
-        return {"kernel": "k_d2t", "bound": "hbm", "achieved": nbytes / t / 1e9, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": nbytes / t / 1e9 / pk["hbm_gbs"], "traffic": None, "peak_source": src}
-    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None}
+    out = {}
+    # M2L
+    t = phases["m2l"] * 1e-3
+    pairs = st["m2l_pairs"]
+    ru, rd = (st["rank_up"], st["rank_down"]) if mixed else (Q, Q)
+    flops = 2.0 * rd * ru * pairs
+    if mixed:                                       # two-term FP16 on tcgen05: 3 MMAs per product
+        peak = pk["bf16_tflops"] / 3.0
+        out["m2l"] = {"kernel": "k_m2l_tc (tcgen05, two-term FP16)", "bound": "tensor",
+                      "peak_source": "%s bf16/fp16 dense burst %.0f / 3 (hi*hi + hi*lo + lo*hi)"
+                                     % (src, pk["bf16_tflops"])}
+    else:
+        peak = peaks["fp64_tflops"]
+        out["m2l"] = {"kernel": "k_m2l_gemm<double>", "bound": "alu",
+                      "peak_source": "measured FP64 FMA rate (kifmm_peak_rate)"}
+    out["m2l"].update({"achieved": flops / t / 1e12 if t > 0 else None, "peak": peak, "unit": "TFLOP/s",
+                       "frac": flops / t / 1e12 / peak if t > 0 else None,
+                       "traffic": _m2l_traffic(pairs) if mixed else None, "ms": phases["m2l"],
+                       "work": "2*R*W flops x %d pairs, R=%d, W=%d" % (pairs, rd, ru)})
+    # near field
+    t = phases["p2p"] * 1e-3
+    npairs = st["near_pairs"] if mixed and st.get("near_pairs") else tst["p2p_pairs"]
+    if mixed:
+        fpp = P2P_FLOPS[kernel]
+        peak = peaks["fp32_tflops"]
+        out["p2p"] = {"kernel": "k_p2p_warp<%d> (FP32x2)" % {"sl": 0, "dl": 1, "adl": 2, "field": 3}[kernel],
+                      "bound": "alu", "achieved": fpp * npairs / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                      "frac": fpp * npairs / t / 1e12 / peak, "traffic": None, "ms": phases["p2p"],
+                      "pairs": npairs, "flops_per_pair": fpp, "pairs_per_s": npairs / t,
+                      "mufu_frac": npairs / t / peaks["rsqrt_per_s"],
+                      "peak_source": "measured FP32 FMA rate (kifmm_peak_rate) at %.0f MHz" % (peaks["sm_mhz"] or 0)}
+    else:
+        out["p2p"] = {"kernel": "k_p2p<double>", "bound": "alu", "ms": phases["p2p"], "pairs": npairs,
+                      "achieved": 20.0 * npairs / t / 1e12, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                      "frac": 20.0 * npairs / t / 1e12 / peaks["fp64_tflops"], "traffic": None,
+                      "peak_source": "measured FP64 FMA rate (kifmm_peak_rate)"}
+    # D2T: rows (Kd FP32, or Qp FP64) streamed once per target and component
+    t = phases["d2t"] * 1e-3
+    K = (rd + 15) // 16 * 16 if mixed else (Q + 15) // 16 * 16
+    nbytes = (4 if mixed else 8) * (K + 1) * tst["n_trg"] * (3 if kernel == "field" else 1)
+    out["d2t"] = {"kernel": "k_d2t", "bound": "hbm", "achieved": nbytes / t / 1e9, "peak": pk["hbm_gbs"],
+                  "unit": "GB/s", "frac": nbytes / t / 1e9 / pk["hbm_gbs"], "traffic": None, "ms": phases["d2t"],
+                  "peak_source": src, "work": "%d B of rows + 4 B result per target" % ((4 if mixed else 8) * K)}
+    dom = max(("m2l", "p2p", "d2t"), key=lambda k: out[k]["ms"])
+    return dict(out[dom]), out
 
 
 def main():
@@ -507,9 +695,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="kifmm", choices=["kifmm", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_cn", "fp64"],
-                    help="mixed_cn: mixed with the compensated DL/ADL near field")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--pinv-cutoff", type=float, default=0.0,
+                    help="pseudo-inverse truncation (0: the workload's, else the library default)")
     ap.add_argument("--max-leaf", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--ref-sample", type=int, default=2048)
@@ -525,6 +714,10 @@ def main():
     ap.add_argument("--serve-p", type=int, default=10)
     ap.add_argument("--serve-mem-gb", type=float, default=96.0)
     ap.add_argument("--solves", type=int, default=5, help="timed polarization solves (0: skip)")
+    ap.add_argument("--no-fp64-plain", dest="fp64_plain", action="store_false",
+                    help="skip timing the FP64 plain form of the same matvec")
+    ap.add_argument("--no-field-check", dest="field_check", action="store_false",
+                    help="skip the interior demagnetizing field of the 1M sphere")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

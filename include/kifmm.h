@@ -9,6 +9,9 @@
  *   KIFMM_KERNEL_SL  : K = 1/|r_i - r_j|                             the 1/r kernel (Sec. III.A.1)
  *   KIFMM_KERNEL_DL  : K = n_j.(r_i - r_j)/|r_i - r_j|^3             Eq. kernel (source normal)
  *   KIFMM_KERNEL_ADL : K = n_i.(r_i - r_j)/|r_i - r_j|^3             Eq. kernel_pol . n_i (Eq. Ax)
+ *   KIFMM_KERNEL_FIELD: K = (r_i - r_j)/|r_i - r_j|^3, three outputs   Eq. kernel_pol (Eq. Eb, the
+ *                      per target (x, y, z components, each an         field vector the force
+ *                      n_trg block of the output)                      integrand needs)
  * with q_j = sigma_j w_j (density times quadrature weight) and the pair skipped
  * when |r_i - r_j| < 1e-5 (the tolerance radius of Sec. III.A.1).
  *
@@ -49,16 +52,20 @@ extern "C" {
 #define KIFMM_KERNEL_SL  0
 #define KIFMM_KERNEL_DL  1
 #define KIFMM_KERNEL_ADL 2
+#define KIFMM_KERNEL_FIELD 3
 
 #define KIFMM_PREC_FP64  0   /* every step in FP64 (the plain form)                        */
-#define KIFMM_PREC_MIXED 1   /* FP32 near field and translations, FP64 set-up and output   */
-#define KIFMM_PREC_MIXED_CN 2 /* as MIXED, with the double- and adjoint-double-layer near
-                                 field compensated: positions as FP32 hi + lo pairs, the
-                                 n.(x - y) products and sums error-free (FMA two-products,
-                                 two-sums).  On curved surfaces the plain FP32 form loses
-                                 digits there to cancellation between close neighbours.
-                                 Target leaves above 64 targets use the plain FP32 block
-                                 kernel.                                                  */
+#define KIFMM_PREC_MIXED 1   /* FP32 near field and translations, FP64 set-up and output.
+                                The double layers' near field forms n.(x - y) from hi + lo
+                                splits whose hi products are exact in FP32, so that close
+                                neighbours on curved surfaces lose nothing to cancellation. */
+
+/* OR'ed into the precision argument of kifmm_fmm_setup: the far field by Chebyshev
+   interpolation (the black-box FMM of the paper's ScalFMM: Sec. I and Sec. III.A.1, Eq.
+   p2m) instead of equivalent densities, with p Chebyshev nodes per dimension in every
+   box (Q = p^3, p in [2, 8]).  FP64 only.  The near field, the tree, the lists and the
+   matvec's other steps are the same.                                                   */
+#define KIFMM_ENGINE_CHEB 16
 
 typedef struct kifmm_tree_s* kifmm_tree;
 typedef struct kifmm_plan_s* kifmm_plan;
@@ -171,10 +178,13 @@ int kifmm_tree_destroy(kifmm_tree tree);
  * folded into every operator, so the matvec only moves check potentials.
  * The double-layer normal is applied at the source-to-check step (Sec. III.A.1,
  * Eq. p2m, the "second method"); the adjoint target normal at evaluation.
- *   kernel      KIFMM_KERNEL_SL / DL / ADL.
+ *   kernel      KIFMM_KERNEL_SL / DL / ADL / FIELD.
  *   p           2..16.
- *   precision   KIFMM_PREC_FP64, KIFMM_PREC_MIXED or KIFMM_PREC_MIXED_CN.
- *   pinv_cutoff > 0 and < 1, or 0 for the default (1e-8 mixed, 1e-9 FP64).
+ *   precision   KIFMM_PREC_FP64 or KIFMM_PREC_MIXED; KIFMM_PREC_FP64 | KIFMM_ENGINE_CHEB
+ *               selects the Chebyshev-interpolation far field (p: nodes per dimension).
+ *   pinv_cutoff > 0 and < 1: both pseudo-inverses truncated there; or 0 for the
+ *               defaults: FP64 1e-9; mixed 1e-8, except Pu of the double layer at 1e-9
+ *               (the dipole sources' upward densities need those directions).
  *   src_nrm     device 3*n_src SoA; required for DL, else ignored (may be NULL).
  *   trg_nrm     device 3*n_trg SoA; required for ADL, else ignored (may be NULL).
  * Errors: INVALID_ARG, OOM, CUDA.
@@ -186,7 +196,8 @@ int kifmm_fmm_setup(kifmm_tree tree, int kernel, int p, int precision, double pi
 /*
  * f = K q for all targets (see the top of this file).
  *   q    device, n_src FP64 (density times weight), input order.
- *   out  device, n_trg FP64, input order (overwritten).
+ *   out  device, n_trg FP64, input order (overwritten); KIFMM_KERNEL_FIELD: 3 n_trg,
+ *        the x components of all targets, then y, then z.
  * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA.
  */
 int kifmm_fmm_matvec(kifmm_plan plan, const double* q, double* out, void* stream);
@@ -228,7 +239,7 @@ int kifmm_fmm_matvec_host(kifmm_plan plan, const double* q, double* out, int gra
 
 typedef struct {
     int32_t kernel, p, q_points, precision;
-    double  pinv_cutoff;
+    double  pinv_cutoff;              /* truncation of the downward pseudo-inverse Pd   */
     int64_t device_bytes;             /* device memory held by the plan      */
     int64_t m2l_pairs, u2u_pairs, l2l_pairs, s2u_leaves, x_pairs;
     int32_t launches_per_matvec;      /* kernels one kifmm_fmm_matvec enqueues */
@@ -252,6 +263,17 @@ typedef struct {
                                          128 targets of one level whose V lists hold the
                                          same offsets, whose products over all of those
                                          offsets are summed on chip and written once    */
+    double  pinv_cutoff_up;           /* truncation of the upward pseudo-inverse Pu     */
+    int64_t near_corr_ranges;         /* mixed: near-field source ranges with a pair closer
+                                         than 1/32 of the range's extent or within 4x the
+                                         tolerance radius, evaluated with the distance
+                                         corrected for the FP32 offsets' rounding         */
+    int64_t near_pairs;               /* mixed: (target, source) pairs of the near field
+                                         (U, W and leaf X lists) per matvec              */
+    int32_t near_axis_units;          /* mixed DL: near-field units whose source normals
+                                         all lie along one coordinate axis (flat faces
+                                         normal to an axis), evaluated with the one-term
+                                         n.(x - y) of those normals                      */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);
@@ -283,7 +305,11 @@ int kifmm_up_skeleton(int p, int k, int32_t* idx, double* E, int32_t* k_tol);
  * events between its phases on its stream (no host synchronization).  A call with
  * phases != NULL (host, >= 9 doubles) waits for the recorded events and returns the
  * mean per matvec since the previous read: {gather, s2u, u2u, x, m2l, l2l, d2t, p2p,
- * total}; then recording is switched on (enable != 0) or off.
+ * total}; then recording is switched on (enable != 0) or off.  enable = 2 also runs
+ * the near field after the far field on the matvec's stream instead of beside it, so
+ * that p2p is the near field's own time with the whole GPU (a roofline measurement;
+ * the results do not change); enable = 1 keeps the overlapped schedule, in which p2p
+ * spans the far field it runs beside.
  */
 int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases);
 
@@ -363,6 +389,49 @@ int kifmm_bie_apply(kifmm_plan plan, const double* area, const double* eps_in, d
                     const double* curv, const double* x, double* y, void* stream);
 
 /*
+ * Right-hand side of the polarization system with free surface charge (Eq. rhs, with
+ * Eq. Ef without its volume term -- no free charge in the medium):
+ *   b_j = (1 - ebar_j) sf_j - deps_j [ E0 . n_j + (1/4pi) ( ADL(sf * a)_j + c_j sf_j ) ]
+ * the free charge's own field at the elements discretized as Eq. pol_discret (with the
+ * self-patch term of kifmm_bie_solve), on a plan built with KIFMM_KERNEL_ADL on
+ * targets = sources.  With sf = 0 this is kifmm_polarization_rhs.
+ *   area, eps_in, curv, sigma_f, b (output): device, n FP64;  nrm device 3n SoA;
+ *   e0 host, 3 doubles.  Asynchronous.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+int kifmm_polarization_rhs_free(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
+                                const double* curv, const double* nrm, const double* sigma_f,
+                                const double e0[3], double* b, void* stream);
+
+/*
+ * Electrostatic field at the surface elements (Sec. II.C, Eq. Eb discretized as Eq.
+ * pol_discret, with the applied uniform field E0):
+ *   E^j = E0 + (1/4pi) [ sum_{k != j} (r_j - r_k)/|r_j - r_k|^3 sigma_k a_k + c_j sigma_j n_j ]
+ * c_j = H_j sqrt(pi a_j) as in kifmm_bie_solve; sigma is the total surface charge
+ * (free plus bound).  On a plan built with KIFMM_KERNEL_FIELD on targets = sources.
+ *   area, curv, sigma: device, n FP64;  nrm device 3n SoA;  e0 host, 3 doubles;
+ *   E: device, 3n FP64 (output, x of all elements, then y, then z).
+ * Asynchronous.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+int kifmm_polarization_field(kifmm_plan plan, const double* area, const double* curv, const double* nrm,
+                             const double* sigma, const double e0[3], double* E, void* stream);
+
+/*
+ * Electrostatic force on each body (Sec. II.C: F_i = integral over body i of the surface
+ * force density f = eps_m sigma E), with the one-point rule:
+ *   F_b = sum over the elements j of body b of eps_out sigma_j E^j a_j
+ * and E^j of kifmm_polarization_field (same plan and arguments).
+ *   body: device, n int32, the body of each element (elements outside [0, n_body) are
+ *         skipped);  n_body >= 1.
+ *   F: device, 3 n_body FP64 (output): F[3 b + k] is component k of body b's force.
+ * Asynchronous; uses 3n doubles of the plan's scratch.  The per-body sums meet by FP64
+ * atomics, so their rounding order varies from run to run.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int kifmm_polarization_force(kifmm_plan plan, const double* area, const double* curv, const double* nrm,
+                             const double* sigma, double eps_out, const double e0[3], const int32_t* body,
+                             int n_body, double* F, void* stream);
+
+/*
  * Demagnetizing-field boundary potential of the Fredkin-Koehler split (Sec. II.B,
  * Eq. fk_integral_discrete):
  *   phi2_i = (1/4pi) sum_j n_j.(r_i - r_j)/|r_i - r_j|^3 phi1_j w_j + (Omega_i/4pi - 1) phi1_i
@@ -382,13 +451,38 @@ int kifmm_demag_phi2(kifmm_plan plan, const double* phi1, const double* w,
  * 2^20 doubles (8 MiB) that every device holds while the library is loaded.
  *  - Plans with more than 2^20 targets are rejected with KIFMM_ERR_INVALID_ARG.
  *  - The first call on a device looks up that array's device address (once per
- *    device); make that first call before any stream capture begins.
+ *    device); make that first call before any stream capture begins.  With lazy
+ *    module loading (the CUDA default) that first call may also be what loads the
+ *    library's module on the device, and so what reserves the array's 8 MiB (a driver
+ *    allocation).  From the second call on, nothing is allocated.
  *  - All calls share the one array, so calls that can overlap on the GPU (different
  *    streams, or different plans without ordering between them) race on it.
  *  - No cudaMalloc, cudaFree or allocating library routine is called.  Asynchronous.
  */
 int kifmm_demag_phi2_noalloc(kifmm_plan plan, const double* phi1, const double* w,
                              const double* omega, double* phi2, void* stream);
+
+/*
+ * Peak-rate microbenchmark (no counterpart in the paper: it measures the
+ * denominators of the roofline fractions the library's kernels are reported
+ * against).  One kernel per unit issues only that arithmetic instruction, on eight
+ * independent chains per thread, from every resident thread of every SM of the
+ * current device; the launch is sized to about 10 ms and timed with CUDA events on
+ * `stream`, `reps` times.
+ *   unit  KIFMM_PEAK_FP32_FMA (fmaf), KIFMM_PEAK_FP32X2_FMA (packed __ffma2_rn),
+ *         KIFMM_PEAK_RSQRT (rsqrtf, the near field's reciprocal square root),
+ *         KIFMM_PEAK_FP64_FMA (fma on doubles).
+ *   rate  host, receives the best rate: flops/s for the FMA units (an FMA counts 2,
+ *         a packed FMA 4), reciprocal square roots/s for KIFMM_PEAK_RSQRT.
+ *   ms    host or NULL, receives the best launch time.
+ * Synchronizes `stream`.  Allocates 2 KB of device memory for the kernels' sink.
+ * Errors: INVALID_ARG (unit outside 0..3, reps outside 1..100), OOM, CUDA.
+ */
+#define KIFMM_PEAK_FP32_FMA   0
+#define KIFMM_PEAK_FP32X2_FMA 1
+#define KIFMM_PEAK_RSQRT      2
+#define KIFMM_PEAK_FP64_FMA   3
+int kifmm_peak_rate(int unit, int reps, double* rate, double* ms, void* stream);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,7 @@ from .capi import (  # noqa: F401
     Solver,
     Tree,
     exported_symbols,
+    kifmm_peak_rate,
     kifmm_polarization_rhs,
     kifmm_quadrature_points,
     kifmm_up_skeleton,

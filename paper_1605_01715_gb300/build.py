@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libkifmm.so")
-SOURCES = ["capi.cu", "tree.cu", "operators.cu", "fmm.cu", "pair_tc.cu", "bie.cu"]
+SOURCES = ["capi.cu", "tree.cu", "operators.cu", "fmm.cu", "pair_tc.cu", "bie.cu", "peaks.cu", "cheb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O3"] + ARCH

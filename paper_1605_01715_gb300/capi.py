@@ -19,8 +19,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkifmm.so")
 
-KERNELS = {"sl": 0, "dl": 1, "adl": 2}
-PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_cn": 2}
+KERNELS = {"sl": 0, "dl": 1, "adl": 2, "field": 3}
+PRECISIONS = {"fp64": 0, "mixed": 1, "cheb_fp64": 16}   # cheb_fp64: Chebyshev far field, FP64
 LISTS = {"U": 0, "V": 1, "W": 2, "X": 3}
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED",
           -5: "TIMEOUT", -6: "BREAKDOWN", -7: "UNSUPPORTED"}
@@ -56,7 +56,9 @@ class PlanStats(ctypes.Structure):
                 ("rank_down", ctypes.c_int32), ("m2l_width", ctypes.c_int32),
                 ("m2l_rows", ctypes.c_int32), ("near_units", ctypes.c_int32),
                 ("near_split_leaves", ctypes.c_int32), ("near_overlap", ctypes.c_int32),
-                ("s2u_points", ctypes.c_int32), ("m2l_chain_pairs", ctypes.c_int64)]
+                ("s2u_points", ctypes.c_int32), ("m2l_chain_pairs", ctypes.c_int64),
+                ("pinv_cutoff_up", ctypes.c_double), ("near_corr_ranges", ctypes.c_int64),
+                ("near_pairs", ctypes.c_int64), ("near_axis_units", ctypes.c_int32)]
 
 
 def _as_dict(st):
@@ -101,6 +103,11 @@ _SIGS = {
     "kifmm_bie_apply": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, _P], ctypes.c_int),
     "kifmm_demag_phi2": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "kifmm_demag_phi2_noalloc": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "kifmm_polarization_rhs_free": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "kifmm_polarization_field": ([_P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "kifmm_polarization_force": ([_P, _P, _P, _P, _P, ctypes.c_double, _P, _P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "kifmm_peak_rate": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
 }
 
 
@@ -256,12 +263,13 @@ class Plan:
         self.n_src = st["n_src"]
         self.n_trg = st["n_trg"]
         self.kernel = kernel
+        self.n_out = self.n_trg * (3 if kernel == "field" else 1)   # the field: x, y, z blocks
         self._lib = lib()
 
     def matvec(self, q, out=None, stream=None):
         if out is None:
-            out = torch.empty(self.n_trg, dtype=torch.float64, device=q.device)
-        _check(lib().kifmm_fmm_matvec(self.handle, _dev(q, self.n_src, "q"), _dev(out, self.n_trg, "out"),
+            out = torch.empty(self.n_out, dtype=torch.float64, device=q.device)
+        _check(lib().kifmm_fmm_matvec(self.handle, _dev(q, self.n_src, "q"), _dev(out, self.n_out, "out"),
                                       _stream(stream)))
         return out
 
@@ -269,7 +277,7 @@ class Plan:
         """kifmm_fmm_matvec_graph: replay a captured matvec reading ``q`` and writing
         ``out`` by address (both must stay allocated; refill ``q`` in place)."""
         _check(lib().kifmm_fmm_matvec_graph(self.handle, _dev(q, self.n_src, "q"),
-                                            _dev(out, self.n_trg, "out"), _stream(stream)))
+                                            _dev(out, self.n_out, "out"), _stream(stream)))
         return out
 
     def matvec_host(self, q, out, graph=True, stream=None):
@@ -277,7 +285,7 @@ class Plan:
         ones are read and written in place by the first and last kernels (asynchronous:
         synchronize the stream before reading ``out``), pageable ones staged.  ``graph``
         replays a matvec captured for this pair."""
-        _check(lib().kifmm_fmm_matvec_host(self.handle, _host(q, self.n_src, "q"), _host(out, self.n_trg, "out"),
+        _check(lib().kifmm_fmm_matvec_host(self.handle, _host(q, self.n_src, "q"), _host(out, self.n_out, "out"),
                                            1 if graph else 0, _stream(stream)))
         return out
 
@@ -290,9 +298,11 @@ class Plan:
         _check(lib().kifmm_plan_get_stats(self.handle, ctypes.byref(st)))
         return _as_dict(st)
 
-    def profile(self, enable=True):
+    def profile(self, enable=True, serial=False):
+        """kifmm_plan_profile: the per-phase means since the last call, then recording
+        on or off; ``serial`` runs the near field after the far field (its own time)."""
         ph = (ctypes.c_double * 9)()
-        _check(lib().kifmm_plan_profile(self.handle, int(enable), ph))
+        _check(lib().kifmm_plan_profile(self.handle, (2 if serial else 1) if enable else 0, ph))
         names = ["gather", "s2u", "u2u", "x", "m2l", "l2l", "d2t", "p2p", "total"]
         return dict(zip(names, list(ph)))
 
@@ -319,6 +329,44 @@ class Plan:
         if rc != 0 and raise_on_failure:
             _check(rc)
         return x, it.value, rr.value, rc
+
+    def polarization_rhs_free(self, area, eps_in, eps_out, curv, nrm, sigma_f, e0, b=None, stream=None):
+        """kifmm_polarization_rhs_free (ADL plan): b with free surface charge sigma_f."""
+        n = self.n_trg
+        if b is None:
+            b = torch.empty(n, dtype=torch.float64, device=area.device)
+        e = (ctypes.c_double * 3)(*[float(v) for v in e0])
+        _check(lib().kifmm_polarization_rhs_free(self.handle, _dev(area, n, "area"), _dev(eps_in, n, "eps_in"),
+                                                 float(eps_out), _dev(curv, n, "curv"), _dev(nrm, 3 * n, "nrm"),
+                                                 _dev(sigma_f, n, "sigma_f"), e, _dev(b, n, "b"), _stream(stream)))
+        return b
+
+    def polarization_field(self, area, curv, nrm, sigma, e0=(0.0, 0.0, 0.0), E=None, stream=None):
+        """kifmm_polarization_field (FIELD plan): E^j at the elements, (3, n)."""
+        n = self.n_trg
+        if E is None:
+            E = torch.empty((3, n), dtype=torch.float64, device=area.device)
+        e = (ctypes.c_double * 3)(*[float(v) for v in e0])
+        _check(lib().kifmm_polarization_field(self.handle, _dev(area, n, "area"), _dev(curv, n, "curv"),
+                                              _dev(nrm, 3 * n, "nrm"), _dev(sigma, n, "sigma"), e,
+                                              _dev(E, 3 * n, "E"), _stream(stream)))
+        return E
+
+    def polarization_force(self, area, curv, nrm, sigma, eps_out, body, n_body, e0=(0.0, 0.0, 0.0), F=None,
+                           stream=None):
+        """kifmm_polarization_force (FIELD plan): the force on each body, (n_body, 3)."""
+        n = self.n_trg
+        if not (isinstance(body, torch.Tensor) and body.is_cuda and body.dtype == torch.int32
+                and body.is_contiguous() and body.numel() == n):
+            raise TypeError("body must be a contiguous int32 CUDA tensor of n elements")
+        if F is None:
+            F = torch.empty((int(n_body), 3), dtype=torch.float64, device=area.device)
+        e = (ctypes.c_double * 3)(*[float(v) for v in e0])
+        _check(lib().kifmm_polarization_force(self.handle, _dev(area, n, "area"), _dev(curv, n, "curv"),
+                                              _dev(nrm, 3 * n, "nrm"), _dev(sigma, n, "sigma"), float(eps_out), e,
+                                              ctypes.c_void_p(body.data_ptr()), int(n_body),
+                                              _dev(F, 3 * int(n_body), "F"), _stream(stream)))
+        return F
 
     def demag_phi2(self, phi1, w, omega, out=None, stream=None):
         n = self.n_trg
@@ -360,6 +408,18 @@ def kifmm_up_skeleton(p, k):
     _check(lib().kifmm_up_skeleton(int(p), int(k), idx.ctypes.data_as(_P), E.ctypes.data_as(_P),
                                    ctypes.byref(kt)))
     return idx, E, kt.value
+
+
+PEAK_UNITS = {"fp32_fma": 0, "fp32x2_fma": 1, "rsqrt": 2, "fp64_fma": 3}
+
+
+def kifmm_peak_rate(unit, reps=3, stream=None):
+    """kifmm_peak_rate: (rate, ms) of one microbenchmark unit on the current device --
+    flops/s for the FMA units, reciprocal square roots/s for "rsqrt"."""
+    rate, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().kifmm_peak_rate(PEAK_UNITS[unit], int(reps), ctypes.byref(rate), ctypes.byref(ms),
+                                 _stream(stream)))
+    return rate.value, ms.value
 
 
 def kifmm_polarization_rhs(nrm, eps_in, eps_out, e0, out=None, stream=None):

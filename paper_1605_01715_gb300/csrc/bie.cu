@@ -6,12 +6,18 @@
 // The self term of Eq. pol_discret is read as c_j s_j: the principal-value normal
 // field at the centre of a disc of area a_j on a surface of mean curvature H_j with
 // unit density is pi rho H, rho = sqrt(a_j/pi).
+// Surface field and body force (Sec. II.C, Eq. Eb with the discretization of Eq.
+// pol_discret, and the force on a body from its surface force density eps_m sigma E):
+//   E^j = E0 + (1/4pi) [ FIELD(sigma * a)_j + c_j sigma_j n_j ],  F_b = sum_{j in b} eps_out sigma_j E^j a_j
+// Right-hand side with free surface charge (Eq. rhs, Eq. Ef without its volume term):
+//   b_j = (1 - ebar_j) sf_j - deps_j [ E0 . n_j + (1/4pi) ( ADL(sf * a)_j + c_j sf_j ) ]
 // Demagnetization (Sec. II.B, Eq. fk_integral_discrete):
 //   phi2_i = DL(phi1 * w)_i / 4pi + (Omega_i/4pi - 1) phi1_i
 // GMRES (Sec. III: PETSc GMRES in matrix-free form; here restarted GMRES(m) of Saad &
 // Schultz with classical Gram-Schmidt applied twice) keeps its Krylov basis, the
 // orthogonalization and the residuals in FP64 on the device; only the small
 // Hessenberg least-squares problem runs on the host.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <utility>
@@ -45,6 +51,59 @@ __global__ void k_polar_combine(const double* __restrict__ x, const double* __re
     double ebar = 0.5 * (eps_in[i] + eps_out), deps = eps_out - eps_in[i];
     double c = curv[i] * sqrt(kPi * area[i]);
     y[i] = ebar * x[i] + deps * (y[i] + c * x[i]) / (4.0 * kPi);
+}
+
+// E[k n + i] = e0_k + (E[k n + i] + c_i sigma_i n_k,i) / 4pi: the raw field sum of
+// sigma a (already in E) completed with the self-patch term and the applied field.
+__global__ void k_field_combine(const double* __restrict__ sigma, const double* __restrict__ area,
+                                const double* __restrict__ curv, const double* __restrict__ nrm, double ex, double ey,
+                                double ez, int64_t n, double* __restrict__ E) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double cs = curv[i] * sqrt(kPi * area[i]) * sigma[i];
+    const double e0[3] = {ex, ey, ez};
+    for (int k = 0; k < 3; ++k) E[k * n + i] = e0[k] + (E[k * n + i] + cs * nrm[k * n + i]) / (4.0 * kPi);
+}
+
+// F[3 b + k] += eps_out sigma_i E_k,i a_i over the elements i of body b.  Bodies up to
+// kForceBins are summed per block in shared memory first (one FP64 atomic per body and
+// block), more go straight to global FP64 atomics.
+constexpr int kForceBins = 1024;
+__global__ void __launch_bounds__(256) k_force(const double* __restrict__ sigma, const double* __restrict__ area,
+                                               const double* __restrict__ E, const int* __restrict__ body,
+                                               double eps_out, int64_t n, int n_body, double* __restrict__ F) {
+    __shared__ double bins[3 * kForceBins];
+    const bool shared = n_body <= kForceBins;
+    if (shared)
+        for (int k = threadIdx.x; k < 3 * n_body; k += blockDim.x) bins[k] = 0.0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = body[i];
+        if (b < 0 || b >= n_body) continue;
+        const double s = eps_out * sigma[i] * area[i];
+        for (int k = 0; k < 3; ++k) {
+            const double f = s * E[k * n + i];
+            if (shared) atomicAdd(&bins[3 * b + k], f);
+            else atomicAdd(&F[3 * b + k], f);
+        }
+    }
+    __syncthreads();
+    if (shared)
+        for (int k = threadIdx.x; k < 3 * n_body; k += blockDim.x)
+            if (bins[k] != 0.0) atomicAdd(&F[k], bins[k]);
+}
+
+// b = (1 - ebar) sf - deps (E0 . n + (adl + c sf)/4pi), adl (the raw ADL sum of sf a) in b.
+__global__ void k_rhs_free(const double* __restrict__ nrm, const double* __restrict__ eps_in, double eps_out,
+                           const double* __restrict__ sf, const double* __restrict__ area,
+                           const double* __restrict__ curv, double ex, double ey, double ez, int64_t n,
+                           double* __restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double ebar = 0.5 * (eps_in[i] + eps_out), deps = eps_out - eps_in[i];
+    const double c = curv[i] * sqrt(kPi * area[i]);
+    const double en = ex * nrm[i] + ey * nrm[n + i] + ez * nrm[2 * n + i];
+    b[i] = (1.0 - ebar) * sf[i] - deps * (en + (b[i] + c * sf[i]) / (4.0 * kPi));
 }
 
 __global__ void k_demag_combine(const double* __restrict__ phi1, const double* __restrict__ omega, int64_t n,
@@ -141,7 +200,9 @@ struct Gmres {
 
 int check_plan_for(kifmm_plan plan, int kernel) {
     KF_ARG(plan != nullptr, "NULL plan");
-    KF_ARG(plan->P.kernel == kernel, kernel == KIFMM_KERNEL_ADL ? "plan kernel must be ADL" : "plan kernel must be DL");
+    KF_ARG(plan->P.kernel == kernel, kernel == KIFMM_KERNEL_ADL     ? "plan kernel must be ADL"
+                                     : kernel == KIFMM_KERNEL_FIELD ? "plan kernel must be FIELD"
+                                                                    : "plan kernel must be DL");
     KF_ARG(plan->P.tree->t.same, "plan must have targets = sources");
     return KIFMM_OK;
 }
@@ -556,5 +617,68 @@ extern "C" int kifmm_solver_finish(kifmm_solver solver, int* done, int* iters, d
 extern "C" int kifmm_solver_destroy(kifmm_solver solver) {
     clear_error();
     delete solver;
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_polarization_field(kifmm_plan plan, const double* area, const double* curv, const double* nrm,
+                                        const double* sigma, const double e0[3], double* E, void* stream) {
+    clear_error();
+    KF_TRY(check_plan_for(plan, KIFMM_KERNEL_FIELD));
+    KF_ARG(area && curv && nrm && sigma && e0 && E, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan& P = plan->P;
+    const int64_t n = P.tree->t.nt;
+    if (n == 0) return KIFMM_OK;
+    BieScratch& S = scratch_of(plan);
+    KF_TRY(ensure(S.q, n));
+    k_mul<<<div_up(n, 256), 256, 0, s>>>(sigma, area, n, S.q.p);
+    KF_CHECK_LAUNCH();
+    KF_TRY(plan_matvec(P, S.q.p, E, s));
+    k_field_combine<<<div_up(n, 256), 256, 0, s>>>(sigma, area, curv, nrm, e0[0], e0[1], e0[2], n, E);
+    KF_CHECK_LAUNCH();
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_polarization_force(kifmm_plan plan, const double* area, const double* curv, const double* nrm,
+                                        const double* sigma, double eps_out, const double e0[3], const int32_t* body,
+                                        int n_body, double* F, void* stream) {
+    clear_error();
+    KF_TRY(check_plan_for(plan, KIFMM_KERNEL_FIELD));
+    KF_ARG(area && curv && nrm && sigma && e0 && body && F, "NULL pointer");
+    KF_ARG(n_body >= 1, "n_body < 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan& P = plan->P;
+    const int64_t n = P.tree->t.nt;
+    BieScratch& S = scratch_of(plan);
+    KF_TRY(ensure(S.r, 3 * (size_t)std::max<int64_t>(n, 1)));
+    KF_CHECK_CUDA(cudaMemsetAsync(F, 0, 3 * (size_t)n_body * sizeof(double), s));
+    if (n == 0) return KIFMM_OK;
+    KF_TRY(kifmm_polarization_field(plan, area, curv, nrm, sigma, e0, S.r.p, stream));
+    int dev = 0, nsm = 0;
+    KF_CHECK_CUDA(cudaGetDevice(&dev));
+    KF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = (int)std::min<int64_t>(div_up(n, 256), 4 * (int64_t)nsm);
+    k_force<<<grid, 256, 0, s>>>(sigma, area, S.r.p, body, eps_out, n, n_body, F);
+    KF_CHECK_LAUNCH();
+    return KIFMM_OK;
+}
+
+extern "C" int kifmm_polarization_rhs_free(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
+                                           const double* curv, const double* nrm, const double* sigma_f,
+                                           const double e0[3], double* b, void* stream) {
+    clear_error();
+    KF_TRY(check_plan_for(plan, KIFMM_KERNEL_ADL));
+    KF_ARG(area && eps_in && curv && nrm && sigma_f && e0 && b, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan& P = plan->P;
+    const int64_t n = P.tree->t.nt;
+    if (n == 0) return KIFMM_OK;
+    BieScratch& S = scratch_of(plan);
+    KF_TRY(ensure(S.q, n));
+    k_mul<<<div_up(n, 256), 256, 0, s>>>(sigma_f, area, n, S.q.p);
+    KF_CHECK_LAUNCH();
+    KF_TRY(plan_matvec(P, S.q.p, b, s));
+    k_rhs_free<<<div_up(n, 256), 256, 0, s>>>(nrm, eps_in, eps_out, sigma_f, area, curv, e0[0], e0[1], e0[2], n, b);
+    KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }

@@ -22,6 +22,7 @@
 #include <queue>
 #include <type_traits>
 
+#include "cheb.cuh"
 #include "common.cuh"
 #include "operators.cuh"
 #include "plan.cuh"
@@ -47,9 +48,13 @@ template <> struct RT<double> {
     static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 };
 
+// Kernels whose target side is a gradient (ADL: along the target normal; the field: all
+// three components).  Only the variation of a down-check potential reaches them.
+inline bool gradient_kernel(int kernel) { return kernel == KIFMM_KERNEL_ADL || kernel == KIFMM_KERNEL_FIELD; }
+
 // ---------------------------------------------------------------- gather
-// lo: also write the rounding remainders of the dipoles (3 more rows, compensated
-// near field)
+// lo: also write the rounding remainders of the dipoles (3 more rows, read by the
+// mixed near field's exact products)
 template <typename Real>
 __global__ void k_gather_q(const double* __restrict__ q, const int64_t* __restrict__ perm, int64_t n,
                            const double* __restrict__ snrm, Real* __restrict__ qs, bool lo) {
@@ -175,16 +180,21 @@ k_src2surf(const int* __restrict__ boxes, const int* __restrict__ off, const int
 // per-box table (bcf: 3 float4 per box).  The tolerance-radius test is dropped for a
 // source box whose cube is provably farther than 2 delta from the check surface in
 // the max-norm (outside the surface's cube, or inside it).
-template <bool NEAR, bool DIPOLE, int NP>
+// DIFF (monopoles only): q (1/|p - y| - 1/|y|), the potential less its value at the box
+// centre, as q (2 p.y - |p|^2) / (|p - y| |y| (|p - y| + |y|)) -- exact for the variation
+// across the check surface, which is all a gradient kernel's far field keeps (sd holds
+// 1/|y| and |y| per source; pp the |p|^2 of each packed check point pair).
+template <bool NEAR, bool DIPOLE, int NP, bool DIFF = false>
 __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const float4* __restrict__ sd, int cnt,
-                                           const float2* px, const float2* py, const float2* pz, float2* acc) {
+                                           const float2* px, const float2* py, const float2* pz, float2* acc,
+                                           const float2* pp = nullptr) {
     const float d2 = (float)(kDelta * kDelta);
 #pragma unroll 2
     for (int jj = 0; jj < cnt; ++jj) {
         const float4 y = sp[jj];
         const float2 nx = make_float2(-y.x, -y.x), ny = make_float2(-y.y, -y.y), nz = make_float2(-y.z, -y.z);
         float2 qa = make_float2(y.w, y.w), qb, qc;
-        if (DIPOLE) {
+        if (DIPOLE || DIFF) {
             const float4 dq = sd[jj];
             qb = make_float2(dq.x, dq.x);
             qc = make_float2(dq.y, dq.y);
@@ -195,7 +205,16 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
             float2 v;
-            if (DIPOLE) {
+            if (DIFF) {
+                // |y|^2 - |p - y|^2 = 2 p.y - |p|^2; |p - y| = r2 inv
+                const float2 dot = __ffma2_rn(pz[m], make_float2(y.z, y.z),
+                                   __ffma2_rn(py[m], make_float2(y.y, y.y), __fmul2_rn(px[m], make_float2(y.x, y.x))));
+                const float2 dp = __ffma2_rn(make_float2(2.f, 2.f), dot, make_float2(-pp[m].x, -pp[m].y));
+                const float2 a = __fmul2_rn(r2, inv);
+                const float2 sum = __fadd2_rn(a, qc);                        // |p - y| + |y|
+                const float2 rs = make_float2(__fdividef(1.f, sum.x), __fdividef(1.f, sum.y));
+                v = __fmul2_rn(__fmul2_rn(__fmul2_rn(qa, dp), __fmul2_rn(inv, qb)), rs);
+            } else if (DIPOLE) {
                 const float2 num = __ffma2_rn(qc, dz, __ffma2_rn(qb, dy, __fmul2_rn(qa, dx)));
                 v = __fmul2_rn(num, __fmul2_rn(__fmul2_rn(inv, inv), inv));
             } else {
@@ -215,18 +234,21 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
 // for the tensor-core projection that follows: the potential scaled by the power of two
 // that puts its largest entry into [2^14, 2^15) (exponent in bexp[b]) and split into
 // FP16 hi and lo terms (Qp per box, zero past Q) -- the box split done in the producer.
-template <bool DIPOLE, int NP, int NT>
+// DIFF: the X list of a gradient kernel -- each check potential less the sources'
+// potential at the box centre (see surf_pairs), so that FP32 and the split keep the
+// variation across a box far smaller than its distance to the sources.
+template <bool DIPOLE, int NP, int NT, bool DIFF = false>
 __global__ void __launch_bounds__(NT)
 k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx, int down,
          const float4* __restrict__ bcf, const int64_t* __restrict__ rng, const float* __restrict__ sxf, int64_t ns,
          const float* __restrict__ qs, const float* __restrict__ surf, int Q, int Qp, __half* __restrict__ vin_h,
          __half* __restrict__ vin_l, int* __restrict__ bexp) {
     __shared__ float4 sp[NT];
-    __shared__ float4 sd[DIPOLE ? NT : 1];
+    __shared__ float4 sd[(DIPOLE || DIFF) ? NT : 1];
     const int b = boxes[blockIdx.x];
     const float4 bh = bcf[3 * b], bl = bcf[3 * b + 1], br = bcf[3 * b + 2];
     const float rf = down ? br.y : br.x;
-    float2 px[NP], py[NP], pz[NP], acc[NP];
+    float2 px[NP], py[NP], pz[NP], acc[NP], pp[DIFF ? NP : 1];
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         float c[2][3];
@@ -240,6 +262,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
         px[m] = make_float2(c[0][0], c[1][0]);
         py[m] = make_float2(c[0][1], c[1][1]);
         pz[m] = make_float2(c[0][2], c[1][2]);
+        if (DIFF) pp[m] = __ffma2_rn(pz[m], pz[m], __ffma2_rn(py[m], py[m], __fmul2_rn(px[m], px[m])));
         acc[m] = make_float2(0.f, 0.f);
     }
     const float margin = (float)(2.0 * kDelta);
@@ -258,13 +281,19 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
                                               (sxf[ns + j] - bh.y) + (sxf[4 * ns + j] - bl.y),
                                               (sxf[2 * ns + j] - bh.z) + (sxf[5 * ns + j] - bl.z), qs[j]);
                 if (DIPOLE) sd[threadIdx.x] = make_float4(qs[ns + j], qs[2 * ns + j], 0.f, 0.f);
+                if (DIFF) {
+                    const float4 y = sp[threadIdx.x];
+                    const float yy = fmaf(y.z, y.z, fmaf(y.y, y.y, y.x * y.x));
+                    const float ry = sqrtf(yy);
+                    sd[threadIdx.x] = make_float4(1.0f / ry, ry, 0.f, 0.f);
+                }
             }
             __syncthreads();
             const int cnt = (int)((se - j0) < (int64_t)NT ? (se - j0) : (int64_t)NT);
             if (near)
-                surf_pairs<true, DIPOLE, NP>(sp, sd, cnt, px, py, pz, acc);
+                surf_pairs<true, DIPOLE, NP, DIFF>(sp, sd, cnt, px, py, pz, acc, pp);
             else
-                surf_pairs<false, DIPOLE, NP>(sp, sd, cnt, px, py, pz, acc);
+                surf_pairs<false, DIPOLE, NP, DIFF>(sp, sd, cnt, px, py, pz, acc, pp);
             __syncthreads();
         }
     }
@@ -352,11 +381,17 @@ int launch_surf(const Plan& P, const Tree& T, bool dl, int nbox, const int* boxe
         const int npts = down ? P.Q : P.ops->ks, stride = down ? P.Qp : P.ops->ks;
         const float* sf = down ? P.surf_f.p : P.ops->surf_up.p;
         const int slots = down ? surf_slots_full(P.Q) : surf_slots(npts);
+        const bool diff = down && !dl && gradient_kernel(P.kernel);
         switch (slots * 2 + (dl ? 1 : 0)) {
 #define KF_SURF(NP, NT)                                                                                          \
     case 2 * (2 * NP * NT):                                                                                      \
-        k_surf_f<false, NP, NT><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, q, sf,   \
-                                                    npts, stride, P.sin_h.p, P.sin_l.p, P.sexp.p);               \
+        if (diff)                                                                                                \
+            k_surf_f<false, NP, NT, true><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p,  \
+                                                              T.ns, q, sf, npts, stride, P.sin_h.p, P.sin_l.p,   \
+                                                              P.sexp.p);                                         \
+        else                                                                                                     \
+            k_surf_f<false, NP, NT><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, q,  \
+                                                        sf, npts, stride, P.sin_h.p, P.sin_l.p, P.sexp.p);       \
         break;                                                                                                   \
     case 2 * (2 * NP * NT) + 1:                                                                                  \
         k_surf_f<true, NP, NT><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, q, sf,    \
@@ -529,7 +564,8 @@ k_d2t(const int* __restrict__ leaves, const int64_t* __restrict__ rng, const Rea
 // ---------------------------------------------------------------- P2P (U and W lists) + scatter
 // One block per target leaf, one thread per target; source boxes staged in shared
 // memory relative to the target leaf's centre.
-// KIND 0: q/r   1: (q n_j).(x - y)/r^3   2: q n_i.(x - y)/r^3
+// KIND 0: q/r   1: (q n_j).(x - y)/r^3   2: q n_i.(x - y)/r^3   3: q (x - y)/r^3 (three
+// components, written to out[tperm[t] + c nt] with the far field res[t + c nt])
 template <typename Real, int KIND>
 __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ off, const int* __restrict__ idx,
                       const int64_t* __restrict__ rng, const double* __restrict__ ctr,
@@ -559,7 +595,7 @@ __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ of
             ny = tnrm[nt + tt];
             nz = tnrm[2 * nt + tt];
         }
-        Real acc = 0;
+        Real acc = 0, acc2 = 0, acc3 = 0;
         for (int e = off[blockIdx.x]; e < off[blockIdx.x + 1]; ++e) {
             int a = idx[e];
             int64_t sb = rng[4 * a], se = rng[4 * a + 1];
@@ -582,6 +618,13 @@ __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ of
                     Real r2 = dx * dx + dy * dy + dz * dz;
                     Real inv = RT<Real>::rsq(r2);
                     Real v;
+                    if (KIND == 3) {
+                        const Real w = (r2 >= d2) ? s0[jj] * (inv * inv * inv) : (Real)0;
+                        acc += w * dx;
+                        acc2 += w * dy;
+                        acc3 += w * dz;
+                        continue;
+                    }
                     if (KIND == 0) v = s0[jj] * inv;
                     else if (KIND == 1) v = (s0[jj] * dx + s1[jj] * dy + s2[jj] * dz) * (inv * inv * inv);
                     else v = s0[jj] * (nx * dx + ny * dy + nz * dz) * (inv * inv * inv);
@@ -590,386 +633,485 @@ __global__ void k_p2p(const int* __restrict__ leaves, const int* __restrict__ of
                 __syncthreads();
             }
         }
-        if (valid) out[tperm[t]] = (double)(acc + res[t]);
+        if (valid) {
+            out[tperm[t]] = (double)(acc + res[t]);
+            if (KIND == 3) {
+                out[tperm[t] + nt] = (double)(acc2 + res[t + nt]);
+                out[tperm[t] + 2 * nt] = (double)(acc3 + res[t + 2 * nt]);
+            }
+        }
     }
 }
 
-// FP32 near field, one warp per target leaf.  Lanes form 4 source groups of 8: lane
-// (g, r) holds targets t0 + 8 i + r (i < T) of the current pass of at most 64 targets and
-// takes sources j = g, g + 4, ... of every 32 staged by the warp; the four partial sums
-// of a target meet by shuffles at the end.  Staged sources are float4 (position relative
-// to the leaf centre and q -- or q n_j for the double layer, spread over two float4), so
-// one shared-memory broadcast load feeds T pair evaluations.  Source positions come as
-// FP32 hi/lo pairs (split once per plan) and the offset from the leaf centre is formed
-// from them in FP32, to within 2 ulp of that offset, with no FP64 arithmetic per pair or
-// per staged source.  A lane's targets are packed in pairs (the last pair of an odd
-// count repeats a target and drops it), so each step is one FP32x2 instruction for two
-// pair evaluations, with the scalar form's round-to-nearest operations.
-// Work is split into units of at most kP2PUnitSrc sources of one leaf (its U- and
-// W-list source ranges, cut where needed) and the units run heaviest first: on
-// adaptive geometries a few leaves next to dense regions carry W lists of tens of
-// thousands of sources, and one warp per leaf left them running alone at the end.  A
-// leaf with several units adds into its outputs with FP64 atomics (the output is
-// zeroed first); the first unit also adds the far field.
+// FP32 near field (mixed form), one warp per work unit.  A unit is at most kP2PUnitSrc
+// sources of one target leaf (pieces of its U-, W- and X-list source ranges); units run
+// heaviest first, and a leaf spread over several units adds into its zeroed outputs
+// with FP64 atomics (the first unit also adds the far field).  Lanes form 4 source
+// groups of 8: lane (g, r) holds targets t0 + 8 i + r (i < T) of the current pass of
+// at most 8 T targets, packed in pairs so that every step is one FP32x2 instruction for
+// two pair evaluations, and takes sources g, g + 4, ... of each chunk of 32; the four
+// partial sums of a target meet by shuffles at the end.
+//
+// Chunks are double-buffered: while one chunk is evaluated, cp.async copies the next
+// chunk's raw source data (FP32 hi/lo coordinates and densities or dipoles) into shared
+// memory; each lane then turns its source into the staged form the pair loop reads by
+// shared-memory broadcast, every value already duplicated as a float2 pair.
+//
+// Accuracy (Sec. III.A.1 asks for the discrete sum; these are the steps that keep the
+// FP32 evaluation at the single layer's accuracy for all three kernels):
+//  - Offsets are taken from the leaf centre.  Each range has an exponent E with every
+//    coordinate offset of the leaf's targets and the range's sources below 2^E (from
+//    the boxes' extents).  For the double layers an offset is split as hi + lo, hi on the
+//    grid g = 2^(E-10) (11 significant bits), lo the FP32 remainder; normals (ADL) and
+//    dipoles q n_j (DL) likewise, on the grid 2^-10 or 2^(k-10) with 2^k above the
+//    dipole's largest component.  Products of two hi parts have at most 22 significant
+//    bits on a common grid, so the sums n_hi . t_hi - n_hi . s_hi (ADL) and
+//    m_hi . t_hi - m_hi . s_hi (DL) are exact in FP32.  The rest, m_hi . (t_lo - s_lo) +
+//    m_lo . (t - s) with the full FP32 offsets t and s in the second product (the lo
+//    parts of close points are not small next to their separation), is 2^-10 smaller
+//    and carries FP32 rounding only.  On a curved surface n . (x - y) between neighbours
+//    is about |x - y|^2 / 2R, and this is what keeps it from cancellation.  A unit's
+//    ranges are ordered by E and the targets split once per exponent.
+//  - The tolerance radius (pair skipped when r^2 < 1e-10) is tested only on ranges
+//    flagged kRangeExcl at set-up, which an FP64 scan found to hold a pair within 4
+//    delta (the leaf's own range always does: each target is among its sources).
+//  - r^2 from FP32 offsets is good to 2^-24 of the offsets, not of the separation.
+//    Ranges flagged kRangeCorr (by the same scan: a pair closer than 2^(E-5) -- a target
+//    close to a source relative to the boxes, such as a volume target near the surface
+//    -- or between delta/2 and 4 delta) are skipped here and evaluated by a second launch
+//    of this kernel, CORR, one range per unit, which adds to each difference of FP32
+//    offsets the difference of their exact rounding errors (t - s = (tf - sf) + (te - se),
+//    the first term exact for close points).  Coincident points (closer than delta/2: a
+//    target among its own sources) are excluded in either launch.
 constexpr int kP2PWarps = 8;
-constexpr long long kFarRange = 1LL << 62;   // range flag: W/X sources, not adjacent to the leaf
+// range flags, in the start index's high bits: a pair may lie within 4 delta (test the
+// tolerance radius); a pair is close (the corrected-distance launch); the range's offset
+// exponent E + 128 (bits 48..55)
+constexpr long long kRangeExcl = 1LL << 62;
+constexpr long long kRangeCorr = 1LL << 61;
+constexpr long long kRangeIdx = (1LL << 48) - 1;
+// a range takes the corrected distance when a pair lies closer than 2^(Er - kCloseBits)
+constexpr int kCloseBits = 5;
+__host__ __device__ inline int range_exp(long long fl) { return (int)((fl >> 48) & 255) - 128; }
 constexpr int kP2PUnitSrc = 2048;
-// Larger target leaves go to the block kernel (a thread per target, sources staged once
-// per leaf): at leaf 128 on the 64-sphere pack it takes 2.56 ms against 4.04 ms for two
-// 64-target passes of this kernel, and 3.70 ms for a packed variant with two targets
-// per thread and half the threads.
+// Larger target leaves of the single layer and the field go to the block kernel (a
+// thread per target, sources staged once per leaf): at leaf 128 on the 64-sphere pack it
+// takes 2.56 ms against 4.04 ms for two 64-target passes of the warp kernel.  The double
+// layers always take the warp kernel, in passes, for its exact products.
 constexpr int kP2PWarpMaxLeaf = 64;
+// unit flags (int4 .w): bit 0 the leaf's first unit, bit 1 the leaf spans several units;
+// bits 8..9 the dipoles' axis of a KIND 4 unit
+constexpr int kUnitFirst = 1, kUnitSplit = 2;
 
-template <int KIND, int T>
-__device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlong2* __restrict__ ranges,
-                                         int flags, double cx, double cy, double cz,
-                                         const float* __restrict__ sxf, int64_t ns,
-                                         const double* __restrict__ txyz, int64_t nt,
-                                         const float* __restrict__ qs, const float* __restrict__ tnrm,
-                                         const float* __restrict__ res, const int64_t* __restrict__ tperm,
-                                         double* __restrict__ out, int64_t t0, int64_t te, float4* st) {
-    const int g = lane >> 3, r = lane & 7;
+// targets per lane per pass (plain and corrected-distance launches) and float4 entries
+// staged per source, by kernel: as many targets as keep each kernel within 128
+// registers, so two blocks share an SM
+template <int KIND> struct NearShape;
+template <> struct NearShape<0> { static constexpr int kMaxT = 8, kMaxTCorr = 6, kStage = 4, kRaw = 7; };
+template <> struct NearShape<1> { static constexpr int kMaxT = 4, kMaxTCorr = 4, kStage = 7, kRaw = 12; };
+template <> struct NearShape<2> { static constexpr int kMaxT = 4, kMaxTCorr = 2, kStage = 7, kRaw = 7; };
+template <> struct NearShape<3> { static constexpr int kMaxT = 8, kMaxTCorr = 6, kStage = 4, kRaw = 7; };
+// 4: the double layer on a unit whose dipoles all lie along one coordinate axis (flat
+// faces normal to an axis): n . (x - y) has one term, no cancellation between terms
+template <> struct NearShape<4> { static constexpr int kMaxT = 8, kMaxTCorr = 1, kStage = 2, kRaw = 9; };
+
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+// 2^k as a float (k in [-126, 127])
+__device__ __forceinline__ float exp2i(int k) { return __int_as_float((k + 127) << 23); }
+// x rounded to the grid of quantum g (|x| < 2^22 g), by adding and removing
+// magic = 1.5 * 2^23 * g
+__device__ __forceinline__ float grid_round(float x, float magic) { return __fsub_rn(__fadd_rn(x, magic), magic); }
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// A source's offset from the leaf centre, from FP32 hi/lo coordinates (ph, pl) and the
+// centre's (ch, cl): a + rest with a = fl(ph - ch) and rest its error plus pl - cl.
+__device__ __forceinline__ void src_offset(float ph, float pl, float ch, float cl, float& a, float& rest) {
+    a = __fsub_rn(ph, ch);
+    const float bb = __fsub_rn(a, ph);
+    const float err = __fadd_rn(__fsub_rn(ph, __fsub_rn(a, bb)), __fsub_rn(-ch, bb));
+    rest = __fadd_rn(__fsub_rn(pl, cl), err);
+}
+
+// One point's offset from the leaf centre in the forms the pair loop uses: full FP32
+// offset f, its exact rounding error e (f + e = the offset to FP32^2 accuracy) and, for
+// the double layers, the split hi (on the grid of magic) + lo with f = fl(hi + lo).
+template <bool SPLIT>
+__device__ __forceinline__ void offset_forms(float a, float rest, float magic, float& f, float& e, float& hi,
+                                             float& lo) {
+    if (SPLIT) {
+        hi = grid_round(a, magic);
+        lo = __fadd_rn(__fsub_rn(a, hi), rest);
+        f = __fadd_rn(hi, lo);
+        e = __fsub_rn(lo, __fsub_rn(f, hi));          // exact: |hi| >= |lo| or hi = 0
+    } else {
+        f = __fadd_rn(a, rest);                       // two-sum of a and rest
+        const float bb = __fsub_rn(f, a);
+        e = __fadd_rn(__fsub_rn(a, __fsub_rn(f, bb)), __fsub_rn(rest, bb));
+        hi = f;
+        lo = 0.f;
+    }
+}
+
+template <int KIND, int T, bool CORR>
+__device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlong2* __restrict__ ranges, int flags,
+                                         float4 cb0, float4 cb1, const float* __restrict__ sxf, int64_t ns,
+                                         const float* __restrict__ txf, int64_t nt, const float* __restrict__ qs,
+                                         const float* __restrict__ tnrm_f, const float* __restrict__ res,
+                                         const int64_t* __restrict__ tperm, double* __restrict__ out, int64_t t0,
+                                         int64_t te, float4* __restrict__ st, float* __restrict__ raw) {
+    using S = NearShape<KIND>;
     constexpr int TP = (T + 1) / 2;
-    float2 tx[TP], ty[TP], tz[TP], acc[TP], nx[TP], ny[TP], nz[TP];
-#pragma unroll
-    for (int m = 0; m < TP; ++m) {
-        float c[2][6];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int64_t t = t0 + 8 * (2 * m + h) + r;
-            t = t < te ? t : t0;                  // padding slots evaluate a real target, unused
-            c[h][0] = (float)(txyz[t] - cx);
-            c[h][1] = (float)(txyz[nt + t] - cy);
-            c[h][2] = (float)(txyz[2 * nt + t] - cz);
-            if (KIND == 2) {
-                c[h][3] = tnrm[t];
-                c[h][4] = tnrm[nt + t];
-                c[h][5] = tnrm[2 * nt + t];
-            }
-        }
-        tx[m] = make_float2(c[0][0], c[1][0]);
-        ty[m] = make_float2(c[0][1], c[1][1]);
-        tz[m] = make_float2(c[0][2], c[1][2]);
-        if (KIND == 2) {
-            nx[m] = make_float2(c[0][3], c[1][3]);
-            ny[m] = make_float2(c[0][4], c[1][4]);
-            nz[m] = make_float2(c[0][5], c[1][5]);
-        }
-        acc[m] = make_float2(0.f, 0.f);
-    }
-    // the leaf centre as FP32 hi + lo; a source's offset from it is (yh - ch) + (yl - cl)
-    const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
-    const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
+    constexpr bool ACC = KIND == 1 || KIND == 2;     // double layers: exact hi products
+    constexpr int NC = KIND == 3 ? 3 : 1;            // output components
+    const int g = lane >> 3, r = lane & 7;
+    const float chx = cb0.x, chy = cb0.y, chz = cb0.z, clx = cb1.x, cly = cb1.y, clz = cb1.z;
     const float d2 = (float)(kDelta * kDelta);
-    // chunks of 32 sources over the leaf's source boxes, the next one prefetched into
-    // registers while the current one is evaluated
-    int e = e0;
-    int64_t j0 = 0, se = 0;
-    if (e < e1) {
-        j0 = ranges[e].x & ~kFarRange;
-        se = ranges[e].y;
-    }
-    float ph[3], pl[3], pq[3];
-    auto fetch = [&](int64_t jb, int64_t je) {
-        const int64_t j = jb + lane;
-        if (j < je) {
+    const int axis = (flags >> 8) & 3;                   // KIND 4: the dipoles' axis, made the third
+                                                         // coordinate of targets and sources
+
+    // targets: offsets from the leaf centre, formed from FP32 hi/lo coordinates exactly as
+    // the sources' below (a target and the same point as a source agree bit for bit), and
+    // for the double layers split on the grid of the current range's exponent
+    float2 tfx[TP], tfy[TP], tfz[TP], acc[TP], acc2[NC > 1 ? TP : 1], acc3[NC > 1 ? TP : 1];
+    float2 thx[ACC ? TP : 1], thy[ACC ? TP : 1], thz[ACC ? TP : 1];   // DL: t hi;  ADL: n hi
+    float2 tlx[ACC ? TP : 1], tly[ACC ? TP : 1], tlz[ACC ? TP : 1];   // DL: t lo;  ADL: -n lo
+    float2 tca[KIND == 2 ? TP : 1], tcb[KIND == 2 ? TP : 1];          // ADL: -n_hi.t_hi, -(n_hi.t_lo + n_lo.t)
+    float2 tex[CORR ? TP : 1], tey[CORR ? TP : 1], tez[CORR ? TP : 1]; // rounding errors of tf
+    auto split_targets = [&](float magic) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                ph[d] = sxf[d * ns + j];
-                pl[d] = sxf[(3 + d) * ns + j];
+        for (int m = 0; m < TP; ++m) {
+            float c[2][14];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int64_t t = t0 + 8 * (2 * m + h) + r;
+                t = t < te ? t : t0;              // padding slots evaluate a real target, unused
+                float a[3], rest[3], th[3], tl[3];
+                src_offset(txf[t], txf[3 * nt + t], chx, clx, a[0], rest[0]);
+                src_offset(txf[nt + t], txf[4 * nt + t], chy, cly, a[1], rest[1]);
+                src_offset(txf[2 * nt + t], txf[5 * nt + t], chz, clz, a[2], rest[2]);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) offset_forms<ACC>(a[d], rest[d], magic, c[h][d], c[h][11 + d], th[d], tl[d]);
+                if (KIND == 4) {
+                    const float ck = axis == 0 ? c[h][0] : (axis == 1 ? c[h][1] : c[h][2]);
+                    if (axis == 0) c[h][0] = c[h][2];
+                    else if (axis == 1) c[h][1] = c[h][2];
+                    c[h][2] = ck;
+                }
+                if (KIND == 1) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        c[h][3 + d] = th[d];
+                        c[h][6 + d] = tl[d];
+                    }
+                } else if (KIND == 2) {
+                    // the normal on the grid 2^-10 (magic 1.5 * 2^13) and its remainder
+                    float nh[3], nl[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        nh[d] = grid_round(tnrm_f[d * nt + t], 12288.0f);
+                        nl[d] = __fadd_rn(__fsub_rn(tnrm_f[d * nt + t], nh[d]), tnrm_f[(3 + d) * nt + t]);
+                        c[h][3 + d] = nh[d];
+                        c[h][6 + d] = -nl[d];
+                    }
+                    // n_hi . t_hi exact (22-bit products on one grid); n_hi . t_lo + n_lo . t
+                    c[h][9] = -__fmaf_rn(nh[2], th[2], __fmaf_rn(nh[1], th[1], __fmul_rn(nh[0], th[0])));
+                    c[h][10] = -__fmaf_rn(nl[2], c[h][2], __fmaf_rn(nl[1], c[h][1], __fmaf_rn(nl[0], c[h][0],
+                               __fmaf_rn(nh[2], tl[2], __fmaf_rn(nh[1], tl[1], __fmul_rn(nh[0], tl[0]))))));
+                }
             }
-            pq[0] = qs[j];
-            if (KIND == 1) {
-                pq[1] = qs[ns + j];
-                pq[2] = qs[2 * ns + j];
+            tfx[m] = make_float2(c[0][0], c[1][0]);
+            tfy[m] = make_float2(c[0][1], c[1][1]);
+            tfz[m] = make_float2(c[0][2], c[1][2]);
+            if (ACC) {
+                thx[m] = make_float2(c[0][3], c[1][3]);
+                thy[m] = make_float2(c[0][4], c[1][4]);
+                thz[m] = make_float2(c[0][5], c[1][5]);
+                tlx[m] = make_float2(c[0][6], c[1][6]);
+                tly[m] = make_float2(c[0][7], c[1][7]);
+                tlz[m] = make_float2(c[0][8], c[1][8]);
+            }
+            if (KIND == 2) {
+                tca[m] = make_float2(c[0][9], c[1][9]);
+                tcb[m] = make_float2(c[0][10], c[1][10]);
+            }
+            if (CORR) {
+                tex[m] = make_float2(c[0][11], c[1][11]);
+                tey[m] = make_float2(c[0][12], c[1][12]);
+                tez[m] = make_float2(c[0][13], c[1][13]);
             }
         }
     };
-    while (e < e1) {
-        fetch(j0, se);
-        const int64_t j = j0 + lane;
-        if (j < se) {
-            st[lane] = make_float4((ph[0] - chx) + (pl[0] - clx), (ph[1] - chy) + (pl[1] - cly),
-                                   (ph[2] - chz) + (pl[2] - clz), pq[0]);
-            if (KIND == 1) st[32 + lane] = make_float4(pq[1], pq[2], 0.f, 0.f);
-        }
-        const int cnt = (int)(se - j0 < 32 ? se - j0 : 32);
-        // advance to the next chunk and prefetch it
-        j0 += 32;
-        while (j0 >= se && ++e < e1) {
-            j0 = ranges[e].x & ~kFarRange;
-            se = ranges[e].y;
-        }
-        __syncwarp();
-#pragma unroll 1
-        for (int jj = g; jj < cnt; jj += 4) {
-            const float4 sp = st[jj];
-            float4 sd = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (KIND == 1) sd = st[32 + jj];
-            const float2 mx = make_float2(-sp.x, -sp.x), my = make_float2(-sp.y, -sp.y),
-                         mz = make_float2(-sp.z, -sp.z), qa = make_float2(sp.w, sp.w);
-#pragma unroll
-            for (int m = 0; m < TP; ++m) {
-                const float2 dx = __fadd2_rn(tx[m], mx), dy = __fadd2_rn(ty[m], my), dz = __fadd2_rn(tz[m], mz);
-                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-                const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-                float2 v;
-                if (KIND == 0) {
-                    v = __fmul2_rn(qa, inv);
-                } else {
-                    const float2 i3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
-                    float2 num;
-                    if (KIND == 1)
-                        num = __ffma2_rn(make_float2(sd.y, sd.y), dz,
-                                         __ffma2_rn(make_float2(sd.x, sd.x), dy, __fmul2_rn(qa, dx)));
-                    else
-                        num = __fmul2_rn(qa, __ffma2_rn(nz[m], dz, __ffma2_rn(ny[m], dy, __fmul2_rn(nx[m], dx))));
-                    v = __fmul2_rn(num, i3);
-                }
-                v.x = r2.x >= d2 ? v.x : 0.f;
-                v.y = r2.y >= d2 ? v.y : 0.f;
-                acc[m] = __fadd2_rn(acc[m], v);
-            }
-        }
-        __syncwarp();
-    }
-#pragma unroll
-    for (int i = 0; i < T; ++i) {
-        float v = (i & 1) ? acc[i >> 1].y : acc[i >> 1].x;
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        const int64_t t = t0 + 8 * i + r;
-        if (g == 0 && t < te) {
-            // res (the far field) is added here, or later by the caller when null
-            const float far = res ? res[t] : 0.f;
-            if (!(flags & 2)) out[tperm[t]] = (double)(v + far);                          // the leaf's only unit
-            else atomicAdd(out + tperm[t], (double)((flags & 1) ? v + far : v));         // one of several
-        }
-    }
-}
-
-// ---- compensated near field (KIFMM_PREC_MIXED_CN), double and adjoint double layer.
-// On a curved surface n.(x - y) between close neighbours is about |x - y|^2 / (2 R),
-// far below |x - y|: plain FP32 loses the digits to cancellation (positions rounded to
-// 2^-24 of the leaf size, normals or dipoles to 2^-24).  Here every offset from the
-// leaf centre is a pair hi + lo with hi on a grid of 2^(e-19) (e: the leaf half-width's
-// binade), so the difference of two hi parts is exact in FP32; normals and dipoles are
-// hi + lo pairs too; the dot product of the hi parts is formed with error-free
-// transformations (FMA two-products, two-sums) and the cross terms are added in FP32.
-// W- and X-list sources (ranges flagged kFarRange) are not adjacent to the leaf, so
-// there the plain FP32 evaluation (of the same hi + lo offsets) is accurate enough.
-__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
-
-// a . b (3-vectors, packed pairs) as hi + lo
-__device__ __forceinline__ void dot3_ef(float2 ax, float2 ay, float2 az, float2 bx, float2 by, float2 bz,
-                                        float2& hi, float2& lo) {
-    const float2 p1 = __fmul2_rn(ax, bx), p2 = __fmul2_rn(ay, by), p3 = __fmul2_rn(az, bz);
-    const float2 e1 = __ffma2_rn(ax, bx, f2neg(p1)), e2 = __ffma2_rn(ay, by, f2neg(p2)),
-                 e3 = __ffma2_rn(az, bz, f2neg(p3));
-    const float2 s = __fadd2_rn(p1, p2), z = __fadd2_rn(s, f2neg(p1));
-    const float2 t1 = __fadd2_rn(__fadd2_rn(p1, f2neg(__fadd2_rn(s, f2neg(z)))), __fadd2_rn(p2, f2neg(z)));
-    const float2 u = __fadd2_rn(s, p3), z2 = __fadd2_rn(u, f2neg(s));
-    const float2 t2 = __fadd2_rn(__fadd2_rn(s, f2neg(__fadd2_rn(u, f2neg(z2)))), __fadd2_rn(p3, f2neg(z2)));
-    hi = u;
-    lo = __fadd2_rn(__fadd2_rn(__fadd2_rn(e1, e2), __fadd2_rn(e3, t1)), t2);
-}
-
-// x rounded to the grid of quantum g (|x| < 2^22 g), by the magic-number sum
-__device__ __forceinline__ float grid_round(float x, float magic) { return __fsub_rn(__fadd_rn(x, magic), magic); }
-
-// A source's offset from the leaf centre as hi (on the grid) + lo, from its FP32
-// hi/lo coordinates and the centre's.
-__device__ __forceinline__ void src_offset_ef(float ph, float pl, float ch, float cl, float magic, float& oh,
-                                              float& ol) {
-    const float a = __fsub_rn(ph, ch);                         // two-sum of ph and -ch
-    const float bb = __fsub_rn(a, ph);
-    const float err = __fadd_rn(__fsub_rn(ph, __fsub_rn(a, bb)), __fsub_rn(-ch, bb));
-    const float rest = __fadd_rn(__fsub_rn(pl, cl), err);
-    oh = grid_round(a, magic);
-    ol = __fadd_rn(__fsub_rn(a, oh), rest);
-}
-
-template <int KIND, int T>
-__device__ __forceinline__ void p2p_pass_cn(int lane, int e0, int e1, const longlong2* __restrict__ ranges,
-                                            int flags, double cx, double cy, double cz, float hbox,
-                                            const float* __restrict__ sxf, int64_t ns,
-                                            const double* __restrict__ txyz, int64_t nt,
-                                            const float* __restrict__ qs, const double* __restrict__ tnrm_d,
-                                            const float* __restrict__ res, const int64_t* __restrict__ tperm,
-                                            double* __restrict__ out, int64_t t0, int64_t te, float4* st) {
-    static_assert(KIND == 1 || KIND == 2, "compensated form for the double layers");
-    const int g = lane >> 3, r = lane & 7;
-    constexpr int TP = (T + 1) / 2;
-    const double quantum = ldexp(1.0, ilogbf(hbox) - 19);
-    const float magic = (float)(1.5 * 8388608.0 * quantum);    // 1.5 * 2^23 * quantum
-    float2 thx[TP], thy[TP], thz[TP], tlx[TP], tly[TP], tlz[TP], acc[TP];
-    float2 nhx[TP], nhy[TP], nhz[TP], nlx[TP], nly[TP], nlz[TP];
 #pragma unroll
     for (int m = 0; m < TP; ++m) {
-        float c[2][12];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int64_t t = t0 + 8 * (2 * m + h) + r;
-            t = t < te ? t : t0;                  // padding slots evaluate a real target, unused
-            const double o[3] = {txyz[t] - cx, txyz[nt + t] - cy, txyz[2 * nt + t] - cz};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double oh = rint(o[d] / quantum) * quantum;
-                c[h][d] = (float)oh;
-                c[h][3 + d] = (float)(o[d] - oh);
-                if (KIND == 2) {
-                    const double nd = tnrm_d[d * nt + t];
-                    c[h][6 + d] = (float)nd;
-                    c[h][9 + d] = (float)(nd - (double)(float)nd);
-                }
-            }
-        }
-        thx[m] = make_float2(c[0][0], c[1][0]);
-        thy[m] = make_float2(c[0][1], c[1][1]);
-        thz[m] = make_float2(c[0][2], c[1][2]);
-        tlx[m] = make_float2(c[0][3], c[1][3]);
-        tly[m] = make_float2(c[0][4], c[1][4]);
-        tlz[m] = make_float2(c[0][5], c[1][5]);
-        if (KIND == 2) {
-            nhx[m] = make_float2(c[0][6], c[1][6]);
-            nhy[m] = make_float2(c[0][7], c[1][7]);
-            nhz[m] = make_float2(c[0][8], c[1][8]);
-            nlx[m] = make_float2(c[0][9], c[1][9]);
-            nly[m] = make_float2(c[0][10], c[1][10]);
-            nlz[m] = make_float2(c[0][11], c[1][11]);
-        }
         acc[m] = make_float2(0.f, 0.f);
+        if (NC > 1) acc2[m] = acc3[m] = make_float2(0.f, 0.f);
     }
-    const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
-    const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
-    const float d2 = (float)(kDelta * kDelta);
-    int e = e0;
-    int64_t j0 = 0, se = 0;
-    bool far = false;
-    if (e < e1) {
-        j0 = ranges[e].x & ~kFarRange;
-        far = (ranges[e].x & kFarRange) != 0;
-        se = ranges[e].y;
-    }
-    while (e < e1) {
-        const int64_t j = j0 + lane;
-        if (j < se) {
-            float oh[3], ol[3];
-            src_offset_ef(sxf[j], sxf[3 * ns + j], chx, clx, magic, oh[0], ol[0]);
-            src_offset_ef(sxf[ns + j], sxf[4 * ns + j], chy, cly, magic, oh[1], ol[1]);
-            src_offset_ef(sxf[2 * ns + j], sxf[5 * ns + j], chz, clz, magic, oh[2], ol[2]);
-            // A: (offset hi, q or dipole hi x), B: (offset lo, dipole hi y), C: (dipole hi z, dipole lo)
-            st[lane] = make_float4(oh[0], oh[1], oh[2], qs[j]);
-            if (KIND == 1) {
-                st[32 + lane] = make_float4(ol[0], ol[1], ol[2], qs[ns + j]);
-                st[64 + lane] = make_float4(qs[2 * ns + j], qs[3 * ns + j], qs[4 * ns + j], qs[5 * ns + j]);
+    if (!ACC) split_targets(0.f);
+
+    // raw rows per source: hi x|y|z, lo x|y|z, then q (SL, ADL, field) or q n_j hi x|y|z
+    // and lo x|y|z (DL)
+    auto issue = [&](int64_t jb, int64_t je, int buf) {
+        const int64_t j = jb + lane;
+        if (j < je) {
+            float* rw = raw + buf * (S::kRaw * 32) + lane;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) cp_async4(rw + 32 * d, sxf + d * ns + j);
+#pragma unroll
+            for (int d = 0; d < S::kRaw - 6; ++d) cp_async4(rw + 32 * (6 + d), qs + d * ns + j);
+        }
+        cp_async_commit();
+    };
+
+    // groups of ranges with one exponent (the unit's ranges are ordered by it); the double
+    // layers split their targets for each group's grid
+    for (int gb = e0; gb < e1;) {
+        const int E = range_exp(ranges[gb].x);
+        int ge = gb + 1;
+        if (ACC)
+            while (ge < e1 && range_exp(ranges[ge].x) == E) ++ge;
+        else
+            ge = e1;
+        const float magic = 1.5f * exp2i(E + 13);        // rounds to the grid 2^(E-10)
+        if (ACC) split_targets(magic);
+        int e = gb;
+        int64_t j0 = ranges[e].x & kRangeIdx, se = ranges[e].y;
+        long long fl = ranges[e].x & ~kRangeIdx;
+        issue(j0, se, 0);
+        int buf = 0;
+        while (e < ge) {
+            const int cnt = (int)(se - j0 < 32 ? se - j0 : 32);
+            const long long cfl = fl;
+            // the next chunk, whose copy overlaps this one's evaluation
+            j0 += 32;
+            while (j0 >= se && ++e < ge) {
+                j0 = ranges[e].x & kRangeIdx;
+                fl = ranges[e].x & ~kRangeIdx;
+                se = ranges[e].y;
+            }
+            if (e < ge) {
+                issue(j0, se, buf ^ 1);
+                cp_async_wait<1>();
             } else {
-                st[32 + lane] = make_float4(ol[0], ol[1], ol[2], 0.f);
+                cp_async_wait<0>();
             }
-        }
-        const int cnt = (int)(se - j0 < 32 ? se - j0 : 32);
-        const bool chunk_far = far;               // a chunk lies within one range
-        j0 += 32;
-        while (j0 >= se && ++e < e1) {
-            j0 = ranges[e].x & ~kFarRange;
-            far = (ranges[e].x & kFarRange) != 0;
-            se = ranges[e].y;
-        }
-        __syncwarp();
-#pragma unroll 1
-        for (int jj = g; jj < cnt; jj += 4) {
-            const float4 sa = st[jj], sb = st[32 + jj];
-            float4 sc = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (KIND == 1) sc = st[64 + jj];
-#pragma unroll
-            for (int m = 0; m < TP; ++m) {
-                // d = t - s as hi (exact: both on the grid) + lo
-                const float2 dhx = __fadd2_rn(thx[m], f2b(-sa.x)), dhy = __fadd2_rn(thy[m], f2b(-sa.y)),
-                             dhz = __fadd2_rn(thz[m], f2b(-sa.z));
-                const float2 dlx = __fadd2_rn(tlx[m], f2b(-sb.x)), dly = __fadd2_rn(tly[m], f2b(-sb.y)),
-                             dlz = __fadd2_rn(tlz[m], f2b(-sb.z));
-                const float2 dx = __fadd2_rn(dhx, dlx), dy = __fadd2_rn(dhy, dly), dz = __fadd2_rn(dhz, dlz);
-                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-                const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-                const float2 i3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
-                if (chunk_far) {                  // W/X sources: no cancellation worth the cost
-                    const float2 num = KIND == 1
-                        ? __ffma2_rn(f2b(sc.x), dz, __ffma2_rn(f2b(sb.w), dy, __fmul2_rn(f2b(sa.w), dx)))
-                        : __fmul2_rn(f2b(sa.w), __ffma2_rn(nhz[m], dz, __ffma2_rn(nhy[m], dy, __fmul2_rn(nhx[m], dx))));
-                    float2 v = __fmul2_rn(num, i3);
-                    v.x = r2.x >= d2 ? v.x : 0.f;
-                    v.y = r2.y >= d2 ? v.y : 0.f;
-                    acc[m] = __fadd2_rn(acc[m], v);
-                    continue;
-                }
-                float2 hi, lo, corr;
-                if (KIND == 1) {                  // (q n_j) . d, dipole hi (sa.w, sb.w, sc.x), lo (sc.y..w)
-                    dot3_ef(f2b(sa.w), f2b(sb.w), f2b(sc.x), dhx, dhy, dhz, hi, lo);
-                    corr = __ffma2_rn(f2b(sa.w), dlx, __ffma2_rn(f2b(sb.w), dly, __fmul2_rn(f2b(sc.x), dlz)));
-                    corr = __ffma2_rn(f2b(sc.y), dhx, __ffma2_rn(f2b(sc.z), dhy, __ffma2_rn(f2b(sc.w), dhz, corr)));
-                } else {                          // n_i . d, normal hi / lo per target
-                    dot3_ef(nhx[m], nhy[m], nhz[m], dhx, dhy, dhz, hi, lo);
-                    corr = __ffma2_rn(nhx[m], dlx, __ffma2_rn(nhy[m], dly, __fmul2_rn(nhz[m], dlz)));
-                    corr = __ffma2_rn(nlx[m], dhx, __ffma2_rn(nly[m], dhy, __ffma2_rn(nlz[m], dhz, corr)));
-                }
-                float2 v = __fadd2_rn(hi, __fadd2_rn(lo, corr));
-                v = KIND == 1 ? __fmul2_rn(v, i3) : __fmul2_rn(__fmul2_rn(f2b(sa.w), v), i3);
-                v.x = r2.x >= d2 ? v.x : 0.f;
-                v.y = r2.y >= d2 ? v.y : 0.f;
-                acc[m] = __fadd2_rn(acc[m], v);
+            __syncwarp();
+            // the corrected-distance ranges are this launch's in the CORR instance, and only there
+            if (((cfl & kRangeCorr) != 0) != CORR) {
+                __syncwarp();
+                buf ^= 1;
+                continue;
             }
+            // stage this lane's source of the chunk
+            if (lane < cnt) {
+                const float* rw = raw + buf * (S::kRaw * 32) + lane;
+                float a[3], rest[3], sf[3], se_[3], sh[3], sl[3];
+                src_offset(rw[0], rw[96], chx, clx, a[0], rest[0]);
+                src_offset(rw[32], rw[128], chy, cly, a[1], rest[1]);
+                src_offset(rw[64], rw[160], chz, clz, a[2], rest[2]);
+    #pragma unroll
+                for (int d = 0; d < 3; ++d) offset_forms<ACC>(a[d], rest[d], magic, sf[d], se_[d], sh[d], sl[d]);
+                if (KIND == 4) {
+                    const float sk = axis == 0 ? sf[0] : (axis == 1 ? sf[1] : sf[2]);
+                    if (axis == 0) sf[0] = sf[2];
+                    else if (axis == 1) sf[1] = sf[2];
+                    sf[2] = sk;
+                }
+                st[lane] = make_float4(-sf[0], -sf[0], -sf[1], -sf[1]);
+                if (KIND == 4) {
+                    const float mk = axis == 0 ? rw[192] : (axis == 1 ? rw[224] : rw[256]);
+                    st[32 + lane] = make_float4(-sf[2], -sf[2], mk, mk);
+                } else if (KIND == 0 || KIND == 3) {
+                    const float q = rw[192];
+                    st[32 + lane] = make_float4(-sf[2], -sf[2], q, q);
+                    if (CORR) {
+                        st[64 + lane] = make_float4(-se_[0], -se_[0], -se_[1], -se_[1]);
+                        st[96 + lane] = make_float4(-se_[2], -se_[2], 0.f, 0.f);
+                    }
+                } else if (KIND == 1) {
+                    const float mf[3] = {rw[192], rw[224], rw[256]}, ml[3] = {rw[288], rw[320], rw[352]};
+                    const float mmax = fmaxf(fabsf(mf[0]), fmaxf(fabsf(mf[1]), fabsf(mf[2])));
+                    // 2^k > mmax; k clamped so that the magic number stays a normal float
+                    int k = ((__float_as_int(mmax) >> 23) & 255) - 126;
+                    k = max(-120, min(k, 110));
+                    const float mmag = 1.5f * exp2i(k + 13);
+                    float mh[3], mlo[3];
+    #pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        mh[d] = grid_round(mf[d], mmag);
+                        mlo[d] = __fadd_rn(__fsub_rn(mf[d], mh[d]), ml[d]);
+                    }
+                    // a_j = m_hi . s_hi (exact), b_j = m_hi . s_lo + m_lo . s
+                    const float aj = __fmaf_rn(mh[2], sh[2], __fmaf_rn(mh[1], sh[1], __fmul_rn(mh[0], sh[0])));
+                    const float bj = __fmaf_rn(mlo[2], sf[2], __fmaf_rn(mlo[1], sf[1], __fmaf_rn(mlo[0], sf[0],
+                                     __fmaf_rn(mh[2], sl[2], __fmaf_rn(mh[1], sl[1], __fmul_rn(mh[0], sl[0]))))));
+                    st[32 + lane] = make_float4(-sf[2], -sf[2], -aj, -aj);
+                    st[64 + lane] = make_float4(mh[0], mh[0], mh[1], mh[1]);
+                    st[96 + lane] = make_float4(mh[2], mh[2], -bj, -bj);
+                    st[128 + lane] = make_float4(mlo[0], mlo[0], mlo[1], mlo[1]);
+                    st[160 + lane] = make_float4(mlo[2], mlo[2], -se_[0], -se_[0]);
+                    if (CORR) st[192 + lane] = make_float4(-se_[1], -se_[1], -se_[2], -se_[2]);
+                } else {
+                    const float q = rw[192];
+                    st[32 + lane] = make_float4(-sf[2], -sf[2], q, q);
+                    st[64 + lane] = make_float4(sh[0], sh[0], sh[1], sh[1]);
+                    st[96 + lane] = make_float4(sh[2], sh[2], sl[0], sl[0]);
+                    st[128 + lane] = make_float4(sl[1], sl[1], sl[2], sl[2]);
+                    if (CORR) {
+                        st[160 + lane] = make_float4(-se_[0], -se_[0], -se_[1], -se_[1]);
+                        st[192 + lane] = make_float4(-se_[2], -se_[2], 0.f, 0.f);
+                    }
+                }
+            }
+            __syncwarp();
+            const bool excl = (cfl & kRangeExcl) != 0;
+    #pragma unroll 1
+            for (int jj = g; jj < cnt; jj += 4) {
+                const float4 A = st[jj], B = st[32 + jj];
+                float4 C, D, F, G, H;
+                if (KIND == 1 || KIND == 2) {
+                    C = st[64 + jj];
+                    D = st[96 + jj];
+                    F = st[128 + jj];
+                }
+                if (KIND == 1) G = st[160 + jj];
+                // the sources' rounding errors -e (CORR): x in ex.x, y in ey.x, z in ez.x
+                float2 ex, ey, ez;
+                if (CORR) {
+                    if (KIND == 0 || KIND == 3) {
+                        C = st[64 + jj];
+                        D = st[96 + jj];
+                        ex = lo2(C), ey = hi2(C), ez = lo2(D);
+                    } else if (KIND == 1) {
+                        H = st[192 + jj];
+                        ex = hi2(G), ey = lo2(H), ez = hi2(H);
+                    } else {
+                        G = st[160 + jj];
+                        H = st[192 + jj];
+                        ex = lo2(G), ey = hi2(G), ez = lo2(H);
+                    }
+                }
+    #pragma unroll
+                for (int m = 0; m < TP; ++m) {
+                    float2 dx = __fadd2_rn(tfx[m], lo2(A)), dy = __fadd2_rn(tfy[m], hi2(A)),
+                           dz = __fadd2_rn(tfz[m], lo2(B));
+                    if (CORR) {
+                        // t - s = (tf - sf) + (te - se): the first difference is exact for close
+                        // points, the second carries what FP32 offsets dropped
+                        dx = __fadd2_rn(dx, __fadd2_rn(tex[m], ex));
+                        dy = __fadd2_rn(dy, __fadd2_rn(tey[m], ey));
+                        dz = __fadd2_rn(dz, __fadd2_rn(tez[m], ez));
+                    }
+                    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                    float2 w = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                    float2 num;
+                    if (KIND == 3) {
+                        // q (t - s) / r^3, three components
+                        float2 w3 = __fmul2_rn(__fmul2_rn(w, w), __fmul2_rn(w, hi2(B)));
+                        if (excl) {
+                            w3.x = r2.x >= d2 ? w3.x : 0.f;
+                            w3.y = r2.y >= d2 ? w3.y : 0.f;
+                        }
+                        acc[m] = __ffma2_rn(dx, w3, acc[m]);
+                        acc2[m] = __ffma2_rn(dy, w3, acc2[m]);
+                        acc3[m] = __ffma2_rn(dz, w3, acc3[m]);
+                        continue;
+                    }
+                    if (KIND == 0) {
+                        num = hi2(B);                                         // q
+                    } else if (KIND == 4) {
+                        w = __fmul2_rn(__fmul2_rn(w, w), w);                  // 1/r^3
+                        num = __fmul2_rn(hi2(B), dz);                         // m_k (t - s)_k
+                    } else if (KIND == 1) {
+                        w = __fmul2_rn(__fmul2_rn(w, w), w);                  // 1/r^3
+                        // m_hi . t_hi - a_j (exact) + m_hi . t_lo + m_lo . t - b_j
+                        const float2 nh = __ffma2_rn(lo2(D), thz[m], __ffma2_rn(hi2(C), thy[m],
+                                          __ffma2_rn(lo2(C), thx[m], hi2(B))));
+                        const float2 cr = __ffma2_rn(lo2(G), tfz[m], __ffma2_rn(hi2(F), tfy[m], __ffma2_rn(lo2(F), tfx[m],
+                                          __ffma2_rn(lo2(D), tlz[m], __ffma2_rn(hi2(C), tly[m],
+                                          __ffma2_rn(lo2(C), tlx[m], hi2(D)))))));
+                        num = __fadd2_rn(nh, cr);
+                    } else {
+                        w = __fmul2_rn(hi2(B), __fmul2_rn(__fmul2_rn(w, w), w));   // q/r^3
+                        // n_hi . s_hi - n_hi . t_hi (exact) + n_hi . s_lo + n_lo . s - b_i = -n . d
+                        // (the staged -s times the stored -n_lo)
+                        const float2 nh = __ffma2_rn(lo2(D), thz[m], __ffma2_rn(hi2(C), thy[m],
+                                          __ffma2_rn(lo2(C), thx[m], tca[m])));
+                        const float2 cr = __ffma2_rn(lo2(B), tlz[m], __ffma2_rn(hi2(A), tly[m], __ffma2_rn(lo2(A), tlx[m],
+                                          __ffma2_rn(hi2(F), thz[m], __ffma2_rn(lo2(F), thy[m],
+                                          __ffma2_rn(hi2(D), thx[m], tcb[m]))))));
+                        num = __fadd2_rn(nh, cr);
+                    }
+                    if (excl) {
+                        w.x = r2.x >= d2 ? w.x : 0.f;
+                        w.y = r2.y >= d2 ? w.y : 0.f;
+                    }
+                    acc[m] = __ffma2_rn(num, w, acc[m]);
+                }
+            }
+            __syncwarp();
+            buf ^= 1;
         }
-        __syncwarp();
+        gb = ge;
     }
 #pragma unroll
-    for (int i = 0; i < T; ++i) {
-        float v = (i & 1) ? acc[i >> 1].y : acc[i >> 1].x;
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        const int64_t t = t0 + 8 * i + r;
-        if (g == 0 && t < te) {
-            const float far = res ? res[t] : 0.f;
-            if (!(flags & 2)) out[tperm[t]] = (double)(v + far);
-            else atomicAdd(out + tperm[t], (double)((flags & 1) ? v + far : v));
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            const float2 a = c == 0 ? acc[i >> 1] : (c == 1 ? acc2[i >> 1] : acc3[i >> 1]);
+            float v = (i & 1) ? a.y : a.x;
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            if (KIND == 2) v = -v;
+            const int64_t t = t0 + 8 * i + r;
+            if (g == 0 && t < te) {
+                // res (the far field) is added here, or later by the caller when null; the
+                // corrected-range launch only adds its share
+                const float far = (res && !CORR) ? res[t + c * nt] : 0.f;
+                double* o = out + tperm[t] + c * nt;
+                if (CORR) atomicAdd(o, (double)v);
+                else if (!(flags & kUnitSplit)) *o = (double)(v + far);                   // the leaf's only unit
+                else atomicAdd(o, (double)((flags & kUnitFirst) ? v + far : v));         // one of several
+            }
         }
     }
 }
 
-template <int KIND, bool CN>
-__global__ void __launch_bounds__(32 * kP2PWarps)
+template <int KIND, bool CORR>
+__global__ void __launch_bounds__(32 * kP2PWarps, 2)
 k_p2p_warp(const int* __restrict__ leaves, int nunits, const int4* __restrict__ units,
-           const longlong2* __restrict__ ranges, const int64_t* __restrict__ rng, const double* __restrict__ ctr,
-           const float* __restrict__ sxf,
-           int64_t ns, const double* __restrict__ txyz, int64_t nt, const float* __restrict__ qs,
-           const float* __restrict__ tnrm, const double* __restrict__ tnrm_d, const float4* __restrict__ bcf,
-           const float* __restrict__ res, const int64_t* __restrict__ tperm, double* __restrict__ out) {
-    __shared__ float4 stage[kP2PWarps][CN ? (KIND == 1 ? 96 : 64) : (KIND == 1 ? 64 : 32)];
+           const longlong2* __restrict__ ranges, const int64_t* __restrict__ rng, const float4* __restrict__ bcf,
+           const float* __restrict__ sxf, int64_t ns, const float* __restrict__ txf, int64_t nt,
+           const float* __restrict__ qs, const float* __restrict__ tnrm_f, const float* __restrict__ res,
+           const int64_t* __restrict__ tperm, double* __restrict__ out) {
+    using S = NearShape<KIND>;
+    extern __shared__ float4 p2p_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ui = blockIdx.x * kP2PWarps + warp;
     if (ui >= nunits) return;                     // whole warp; no block-wide barrier below
     const int4 u = units[ui];                     // (leaf, first range, end range, flags)
     const int b = leaves[u.x];
-    const double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
+    const float4 cb0 = bcf[3 * b], cb1 = bcf[3 * b + 1];   // leaf centre, FP32 hi and lo
     const int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
-    const int e0 = u.y, e1 = u.z;
-    float4* st = stage[warp];
-    // passes of up to 8 kMaxT targets (the compensated form keeps four per lane)
-    constexpr int kMaxT = CN ? 4 : 8;
+    float4* st = p2p_smem + warp * (S::kStage * 32 + S::kRaw * 16);
+    float* raw = reinterpret_cast<float*>(st + S::kStage * 32);
+    constexpr int kMaxT = CORR ? S::kMaxTCorr : S::kMaxT;
     for (int64_t t0 = tb; t0 < te; t0 += 8 * kMaxT) {
         const int n = (int)(te - t0 < 8 * kMaxT ? te - t0 : 8 * kMaxT);
         const int64_t tend = t0 + n;
         switch ((n + 7) >> 3) {
-#define KF_PASS(TT)                                                                                        \
-    case TT:                                                                                               \
-        if constexpr (TT <= kMaxT) {                                                                       \
-            if constexpr (CN)                                                                              \
-                p2p_pass_cn<KIND == 0 ? 1 : KIND, TT>(lane, e0, e1, ranges, u.w, cx, cy, cz, bcf[3 * b].w, sxf, \
-                                                      ns, txyz, nt, qs, tnrm_d, res, tperm, out, t0, tend, st); \
-            else                                                                                           \
-                p2p_pass<KIND, TT>(lane, e0, e1, ranges, u.w, cx, cy, cz, sxf, ns, txyz, nt, qs, tnrm, res,  \
-                                   tperm, out, t0, tend, st);                                              \
-        }                                                                                                  \
+#define KF_PASS(TT)                                                                                              \
+    case TT:                                                                                                     \
+        if constexpr (TT <= kMaxT)                                                                               \
+            p2p_pass<KIND, TT, CORR>(lane, u.y, u.z, ranges, u.w, cb0, cb1, sxf, ns, txf, nt, qs, tnrm_f, res,   \
+                                     tperm, out, t0, tend, st, raw);                                             \
         break;
             KF_PASS(1) KF_PASS(2) KF_PASS(3) KF_PASS(4) KF_PASS(5) KF_PASS(6) KF_PASS(7) KF_PASS(8)
 #undef KF_PASS
@@ -977,20 +1119,91 @@ k_p2p_warp(const int* __restrict__ leaves, int nunits, const int4* __restrict__ 
     }
 }
 
-// out[tperm[t]] += res[t]: the far field, after a near field that ran beside it.
-__global__ void k_add_far(const int64_t* __restrict__ tperm, const float* __restrict__ res, int64_t nt,
+template <int KIND>
+constexpr size_t p2p_warp_smem() {
+    return (size_t)kP2PWarps * (NearShape<KIND>::kStage * 32 * sizeof(float4) + NearShape<KIND>::kRaw * 2 * 32 * sizeof(float));
+}
+
+// Dynamic shared memory of the near-field kernels (above the 48 KB default for some).
+int set_p2p_smem(int kind) {
+#define KF_SMEM(K)                                                                                              \
+    KF_CHECK_CUDA(cudaFuncSetAttribute(k_p2p_warp<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                       (int)p2p_warp_smem<K>()));                                              \
+    KF_CHECK_CUDA(cudaFuncSetAttribute(k_p2p_warp<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                       (int)p2p_warp_smem<K>()));
+    switch (kind) {
+    case 0: KF_SMEM(0) break;
+    case 1: KF_SMEM(1) break;
+    case 2: KF_SMEM(2) break;
+    case 3: KF_SMEM(3) break;
+    default: KF_SMEM(4) break;
+    }
+#undef KF_SMEM
+    return KIFMM_OK;
+}
+
+// Mixed plans evaluate the near field with the warp kernel, except single-layer and
+// field plans with a leaf above kP2PWarpMaxLeaf targets.
+inline bool warp_near(const Plan& P) {
+    const bool plain = P.kernel == KIFMM_KERNEL_SL || P.kernel == KIFMM_KERNEL_FIELD;
+    return !P.fp64 && (!plain || P.max_trg_leaf <= kP2PWarpMaxLeaf);
+}
+
+// Set-up scan of the near-field ranges: for range i (sources [ranges[i].x, .y) of the
+// target leaf leaves[rleaf[i]]), the smallest FP64 squared distance between one of the
+// leaf's targets and one of the range's sources, over all pairs (minr2[2i]) and over the
+// pairs at least delta/2 apart (minr2[2i + 1]; coincident points, a target among its own
+// sources above all, are skipped whatever the precision).  One warp per range.
+__global__ void k_range_min_r2(int nr, const longlong2* __restrict__ ranges, const int* __restrict__ rleaf,
+                               const int* __restrict__ leaves, const int64_t* __restrict__ rng,
+                               const double* __restrict__ sxyz, int64_t ns, const double* __restrict__ txyz,
+                               int64_t nt, double* __restrict__ minr2) {
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= nr) return;
+    const int64_t j0 = ranges[i].x & kRangeIdx, j1 = ranges[i].y;
+    const int b = leaves[rleaf[i]];
+    const int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
+    const double half2 = 0.25 * kDelta * kDelta;
+    double best = 1e300, best_far = 1e300;
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+        const double sx = sxyz[j], sy = sxyz[ns + j], sz = sxyz[2 * ns + j];
+        for (int64_t t = tb; t < te; ++t) {
+            const double dx = txyz[t] - sx, dy = txyz[nt + t] - sy, dz = txyz[2 * nt + t] - sz;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            best = fmin(best, r2);
+            if (r2 >= half2) best_far = fmin(best_far, r2);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+        best_far = fmin(best_far, __shfl_xor_sync(0xffffffffu, best_far, o));
+    }
+    if (lane == 0) {
+        minr2[2 * i] = best;
+        minr2[2 * i + 1] = best_far;
+    }
+}
+
+// out[tperm[t] + c nt] += res[t + c nt] for the nc output components: the far field,
+// after a near field that ran beside it.
+__global__ void k_add_far(const int64_t* __restrict__ tperm, const float* __restrict__ res, int64_t nt, int nc,
                           double* __restrict__ out) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < nt) out[tperm[t]] += (double)res[t];
+    if (t >= nt) return;
+    const int64_t o = tperm[t];
+    for (int c = 0; c < nc; ++c) out[o + c * nt] += (double)res[t + c * nt];
 }
 
 // f[i] = near[i] + res[itperm[i]] in input order (res null: f[i] = near[i]), written
 // once and in order, so f may be a host buffer.
 __global__ void k_add_far_io(const int64_t* __restrict__ itperm, const float* __restrict__ res,
-                             const double* __restrict__ near, int64_t nt, double* __restrict__ f) {
+                             const double* __restrict__ near, int64_t nt, int nc, double* __restrict__ f) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nt) return;
-    f[i] = res ? near[i] + (double)res[itperm[i]] : near[i];
+    const int64_t t = itperm[i];
+    for (int c = 0; c < nc; ++c) f[i + c * nt] = res ? near[i + c * nt] + (double)res[t + c * nt] : near[i + c * nt];
 }
 
 // ---------------------------------------------------------------- set-up kernels
@@ -1006,21 +1219,29 @@ __global__ void k_split_xyz(const double* __restrict__ xyz, int64_t n, float* __
     }
 }
 
+// Sorted normals: FP64 (outd) and FP32 (outf; with lo, also the FP32 remainders as rows
+// 3..5, which the mixed near field's exact products read).
 __global__ void k_gather_nrm(const double* __restrict__ nrm, const int64_t* __restrict__ perm, int64_t n,
-                             double* __restrict__ outd, float* __restrict__ outf) {
+                             double* __restrict__ outd, float* __restrict__ outf, bool lo) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t j = perm[i];
     for (int d = 0; d < 3; ++d) {
         double v = nrm[d * n + j];
         if (outd) outd[d * n + i] = v;
-        if (outf) outf[d * n + i] = (float)v;
+        if (outf) {
+            const float h = (float)v;
+            outf[d * n + i] = h;
+            if (lo) outf[(3 + d) * n + i] = (float)(v - (double)h);
+        }
     }
 }
 
 // D2T row descriptors: target position in its leaf's unit frame, its normal, scale.
+// grad: rows of the target-normal derivative, with the normal tnrm (ADL) or, tnrm
+// null, the unit vector of coordinate axis (field component).
 __global__ void k_d2t_rows(const int* __restrict__ tleaf_of, int64_t nt, const double* __restrict__ txyz,
-                           const double* __restrict__ tnrm, const int* __restrict__ lvl,
+                           const double* __restrict__ tnrm, int axis, const int* __restrict__ lvl,
                            const double* __restrict__ ctr, double root_h, bool adl, double* apts,
                            double* anrm, double* ascale, int64_t* orow) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1029,7 +1250,7 @@ __global__ void k_d2t_rows(const int* __restrict__ tleaf_of, int64_t nt, const d
     double r = ldexp(root_h, -lvl[b]);
     for (int d = 0; d < 3; ++d) {
         apts[3 * t + d] = (txyz[d * nt + t] - ctr[3 * b + d]) / r;
-        anrm[3 * t + d] = adl ? tnrm[d * nt + t] : 0.0;
+        anrm[3 * t + d] = adl ? (tnrm ? tnrm[d * nt + t] : (d == axis ? 1.0 : 0.0)) : 0.0;
     }
     ascale[t] = adl ? 1.0 / r : 1.0;
     orow[t] = t;
@@ -1247,7 +1468,28 @@ int build_ops(Plan& P, const HostPinv& h, double* m2m, double* m2l, double* l2l,
         KF_TRY(tmp.alloc((size_t)nops[which] * P.Qp * P.Qp));
         KF_CHECK_CUDA(cudaMemsetAsync(tmp.p, 0, tmp.bytes(), s));
         KF_TRY(translation_ops(P, h, which, P.Q, P.Qp, which == 2 ? dPd.p : dPu.p, tmp.p, s));
-        bool center = P.kernel == KIFMM_KERNEL_ADL && which != 0;
+        bool center = gradient_kernel(P.kernel) && which != 0;
+        dim3 grid(div_up(P.Qp, 128), nops[which]);
+        k_center_ops<double><<<grid, 128, 0, s>>>(tmp.p, P.Q, P.Qp, P.Qp, center, outs[which]);
+        KF_CHECK_LAUNCH();
+        KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    return KIFMM_OK;
+}
+
+// The Chebyshev engine's tables (cheb_host_tables), centred like build_ops's for the
+// gradient kernels: a constant shift of the node values moves the interpolant by that
+// constant, so the rows' mean carries no gradient.
+int build_cheb_ops(Plan& P, double* m2m, double* m2l, double* l2l, cudaStream_t s) {
+    std::vector<double> hm2m, hm2l, hl2l;
+    cheb_host_tables(P.p, P.Qp, hm2m, hm2l, hl2l);
+    const std::vector<double>* src[3] = {&hm2m, &hm2l, &hl2l};
+    double* outs[3] = {m2m, m2l, l2l};
+    const int nops[3] = {8, kNumOffsets, 8};
+    for (int which = 0; which < 3; ++which) {
+        DBuf<double> tmp;
+        KF_TRY(tmp.upload(*src[which], s));
+        const bool center = gradient_kernel(P.kernel) && which != 0;
         dim3 grid(div_up(P.Qp, 128), nops[which]);
         k_center_ops<double><<<grid, 128, 0, s>>>(tmp.p, P.Q, P.Qp, P.Qp, center, outs[which]);
         KF_CHECK_LAUNCH();
@@ -1309,7 +1551,7 @@ __global__ void k_left_mul(const double* __restrict__ L, const double* __restric
 int build_projected(Plan& P, const HostPinv& h, OpTables* t, const std::vector<double>& Eup, DBuf<float>* f32,
                     cudaStream_t s) {
     const int Q = P.Q, Qp = P.Qp, Ku = t->Ku, Kd = t->Kd;
-    const bool adl = P.kernel == KIFMM_KERNEL_ADL;
+    const bool adl = gradient_kernel(P.kernel);
     std::vector<double> Lu((size_t)Ku * Q, 0.0), Ld((size_t)Kd * Q, 0.0);
     for (int j = 0; j < h.ru; ++j)
         for (int i = 0; i < Q; ++i) Lu[(size_t)j * Q + i] = h.Uu[(size_t)i * h.ru + j];
@@ -1371,8 +1613,8 @@ int build_projected(Plan& P, const HostPinv& h, OpTables* t, const std::vector<d
 // Per-target evaluation rows G(x_t, 2.95 s) P: P = Pd (Q wide, stored Qp) or, factored,
 // Wd (rd wide, stored Kd).
 template <typename Real>
-int build_d2t(Plan& P, const HostPinv& h, bool factored, int Kd, const std::vector<int>& tleaf_of, Real* out,
-              cudaStream_t s) {
+int build_d2t(Plan& P, const HostPinv& h, bool factored, int Kd, const std::vector<int>& tleaf_of, int axis,
+              Real* out, cudaStream_t s) {
     const Tree& T = P.tree->t;
     int64_t nt = T.nt;
     DBuf<int> dleaf;
@@ -1389,9 +1631,10 @@ int build_d2t(Plan& P, const HostPinv& h, bool factored, int Kd, const std::vect
     KF_TRY(dPd.upload(factored ? h.Wd : h.Pd, s));
     const int C = factored ? h.rd : P.Q, Kc = factored ? Kd : P.Qp;
     const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
-    bool adl = P.kernel == KIFMM_KERNEL_ADL;
-    k_d2t_rows<<<div_up(nt, 256), 256, 0, s>>>(dleaf.p, nt, txyz, adl ? P.tnrm_d.p : nullptr, T.lvl.p,
-                                               T.ctr.p, T.root_h, adl, apts.p, anrm.p, ascale.p, orow.p);
+    const bool adl = gradient_kernel(P.kernel);
+    const double* tn = P.kernel == KIFMM_KERNEL_ADL ? P.tnrm_d.p : nullptr;
+    k_d2t_rows<<<div_up(nt, 256), 256, 0, s>>>(dleaf.p, nt, txyz, tn, axis, T.lvl.p, T.ctr.p, T.root_h, adl,
+                                               apts.p, anrm.p, ascale.p, orow.p);
     KF_CHECK_LAUNCH();
     // build in chunks of rows to bound the launch size
     const int64_t chunk = 1 << 20;
@@ -1417,7 +1660,7 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
     static std::vector<std::weak_ptr<OpTables>> cache;
     int dev = 0;
     KF_CHECK_CUDA(cudaGetDevice(&dev));
-    const bool centered = P.kernel == KIFMM_KERNEL_ADL;
+    const bool centered = gradient_kernel(P.kernel);
     std::lock_guard<std::mutex> lock(mu);
     for (auto it = cache.begin(); it != cache.end();) {
         std::shared_ptr<OpTables> t = it->lock();
@@ -1425,7 +1668,8 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
             it = cache.erase(it);
             continue;
         }
-        if (t->device == dev && t->p == P.p && t->cutoff == P.cutoff && t->fp64 == P.fp64 &&
+        if (t->device == dev && t->p == P.p && t->cut_up == P.cut_up && t->cut_dn == P.cut_dn && t->fp64 == P.fp64 &&
+            t->cheb == P.cheb &&
             t->centered == centered) {
             P.ops = t;
             return KIFMM_OK;
@@ -1435,7 +1679,9 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
     auto t = std::make_shared<OpTables>();
     t->device = dev;
     t->p = P.p;
-    t->cutoff = P.cutoff;
+    t->cut_up = P.cut_up;
+    t->cut_dn = P.cut_dn;
+    t->cheb = P.cheb;
     t->fp64 = P.fp64;
     t->centered = centered;
     const size_t QQ = (size_t)P.Qp * P.Qp;
@@ -1446,9 +1692,12 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
         KF_CHECK_CUDA(cudaMemsetAsync(t->m2m_d.p, 0, t->m2m_d.bytes(), s));
         KF_CHECK_CUDA(cudaMemsetAsync(t->m2l_d.p, 0, t->m2l_d.bytes(), s));
         KF_CHECK_CUDA(cudaMemsetAsync(t->l2l_d.p, 0, t->l2l_d.bytes(), s));
-        t->ru = h.ru;
-        t->rd = h.rd;
-        KF_TRY(build_ops(P, h, t->m2m_d.p, t->m2l_d.p, t->l2l_d.p, s));
+        t->ru = P.cheb ? P.Q : h.ru;
+        t->rd = P.cheb ? P.Q : h.rd;
+        if (P.cheb)
+            KF_TRY(build_cheb_ops(P, t->m2m_d.p, t->m2l_d.p, t->l2l_d.p, s));
+        else
+            KF_TRY(build_ops(P, h, t->m2m_d.p, t->m2l_d.p, t->l2l_d.p, s));
     } else {
         // translations between projections (see build_projected), two-term FP16
         t->ru = h.ru;
@@ -1503,33 +1752,35 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
 
 int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s) {
     Tree& T = P.tree->t;
-    const HostPinv& h = host_pinv(P.p, P.cutoff);
-    P.Q = h.Q;
-    P.Qp = (h.Q + 15) / 16 * 16;
+    // the Chebyshev engine has no pseudo-inverses (its order only picks the surface
+    // operators computed here, which it leaves unused)
+    const HostPinv& h = host_pinv(P.cheb ? 2 : P.p, P.cut_up, P.cut_dn);
+    P.Q = P.cheb ? P.p * P.p * P.p : h.Q;
+    P.Qp = (P.Q + 15) / 16 * 16;
     P.fp64 = P.prec == KIFMM_PREC_FP64;
-    P.cnear = P.prec == KIFMM_PREC_MIXED_CN && P.kernel != KIFMM_KERNEL_SL;
     KF_TRY(P.err.alloc(1));
     KF_CHECK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), s));
 
     // sorted normals
     if (P.kernel == KIFMM_KERNEL_DL) {
         KF_TRY(P.snrm.alloc(3 * T.ns));
-        k_gather_nrm<<<div_up(T.ns, 256), 256, 0, s>>>(src_nrm, T.sperm.p, T.ns, P.snrm.p, nullptr);
+        k_gather_nrm<<<div_up(T.ns, 256), 256, 0, s>>>(src_nrm, T.sperm.p, T.ns, P.snrm.p, nullptr, false);
         KF_CHECK_LAUNCH();
     }
     if (P.kernel == KIFMM_KERNEL_ADL) {
         const int64_t* tp = T.same ? T.sperm.p : T.tperm.p;
         KF_TRY(P.tnrm_d.alloc(3 * T.nt));
-        if (!P.fp64) KF_TRY(P.tnrm_f.alloc(3 * T.nt));
+        if (!P.fp64) KF_TRY(P.tnrm_f.alloc(6 * T.nt));
         k_gather_nrm<<<div_up(T.nt, 256), 256, 0, s>>>(trg_nrm, tp, T.nt, P.tnrm_d.p,
-                                                       P.fp64 ? nullptr : P.tnrm_f.p);
+                                                       P.fp64 ? nullptr : P.tnrm_f.p, true);
         KF_CHECK_LAUNCH();
     }
 
-    // surfaces
+    // surfaces (the Chebyshev engine: its box nodes)
     {
-        std::vector<float> sf(h.surf.begin(), h.surf.end());
-        KF_TRY(P.surf_d.upload(h.surf, s));
+        const std::vector<double> pts = P.cheb ? cheb_nodes(P.p) : h.surf;
+        std::vector<float> sf(pts.begin(), pts.end());
+        KF_TRY(P.surf_d.upload(pts, s));
         KF_TRY(P.surf_f.upload(sf, s));
     }
 
@@ -1550,6 +1801,11 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_TRY(P.sxf.alloc(6 * (size_t)T.ns));
         k_split_xyz<<<div_up(T.ns, 256), 256, 0, s>>>(T.sxyz.p, T.ns, P.sxf.p);
         KF_CHECK_LAUNCH();
+        if (!T.same && T.nt > 0) {
+            KF_TRY(P.txf.alloc(6 * (size_t)T.nt));
+            k_split_xyz<<<div_up(T.nt, 256), 256, 0, s>>>(T.txyz.p, T.nt, P.txf.p);
+            KF_CHECK_LAUNCH();
+        }
         KF_TRY(P.bcf.alloc(3 * (size_t)T.nbox));
         k_box_f<<<div_up(T.nbox, 256), 256, 0, s>>>(T.ctr.p, T.lvl.p, T.root_h, T.nbox, P.bcf.p);
         KF_CHECK_LAUNCH();
@@ -1601,7 +1857,12 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     KF_TRY(P.tleaf.upload(tleaf, s));
     KF_TRY(P.p2p_off.upload(p2p_off, s));
     KF_TRY(P.p2p_idx.upload(p2p_idx, s));
-    // mixed: near-field work units of at most kP2PUnitSrc sources, heaviest first
+    // mixed: near-field work units of at most kP2PUnitSrc sources, heaviest first.  Each
+    // range carries its offset exponent E (2^E above every coordinate offset of the leaf's
+    // targets and the range's sources, from the boxes' extents) and the flags of an FP64
+    // scan of its pairs; within a unit the ranges are ordered by E, so the targets are
+    // split anew only when it changes.  Ranges with close pairs are also dealt, one per
+    // unit, to the corrected-distance launch.
     if (!P.fp64) {
         struct Unit {
             int4 u;
@@ -1609,53 +1870,145 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         };
         std::vector<Unit> units;
         std::vector<longlong2> ranges;
+        std::vector<int> rleaf;
+        std::vector<double> rext;              // per range: largest coordinate offset of its pairs
+        auto half = [&](int box) { return std::ldexp(T.root_h, -T.h_lvl[box]); };
+        auto exp_of = [](double ext) { return std::max(-100, std::min(100, std::ilogb(ext * (1.0 + 1e-12)) + 1)); };
         for (size_t li = 0; li < tleaf.size(); ++li) {
             const int b = tleaf[li];
             const int64_t ntg = T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2];
+            const double hb = half(b);
             const size_t u0 = units.size();
             int r0 = (int)ranges.size();
             int64_t cnt = 0;
-            const int n_u = T.h_u_off[b + 1] - T.h_u_off[b];   // the U list comes first
+            auto close_unit = [&]() {
+                // order the unit's ranges by exponent
+                std::vector<int> ord(ranges.size() - r0);
+                std::iota(ord.begin(), ord.end(), r0);
+                std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+                    return range_exp(ranges[x].x) < range_exp(ranges[y].x);
+                });
+                std::vector<longlong2> rg;
+                std::vector<double> re;
+                for (int i : ord) {
+                    rg.push_back(ranges[i]);
+                    re.push_back(rext[i]);
+                }
+                std::copy(rg.begin(), rg.end(), ranges.begin() + r0);
+                std::copy(re.begin(), re.end(), rext.begin() + r0);
+                units.push_back({make_int4((int)li, r0, (int)ranges.size(), 0), ntg * cnt});
+                r0 = (int)ranges.size();
+                cnt = 0;
+            };
             for (int k = p2p_off[li]; k < p2p_off[li + 1]; ++k) {
                 const int a = p2p_idx[k];
-                // W- and X-list boxes are not adjacent to the leaf; flagged when their
-                // max-norm gap also exceeds twice the tolerance radius
-                long long far = 0;
-                if (k - p2p_off[li] >= n_u) {
-                    const double ha = std::ldexp(T.root_h, -T.h_lvl[a]), hb = std::ldexp(T.root_h, -T.h_lvl[b]);
-                    double dc = 0.0;
-                    for (int d = 0; d < 3; ++d) {
-                        const double ca = (2 * T.h_coord[3 * a + d] + 1) * ha, cb = (2 * T.h_coord[3 * b + d] + 1) * hb;
-                        dc = std::max(dc, std::fabs(ca - cb));
-                    }
-                    if (dc - ha - hb > 2.0 * kDelta) far = kFarRange;
+                const double ha = half(a);
+                double box_ext = hb;
+                for (int d = 0; d < 3; ++d) {
+                    const double ca = (2 * T.h_coord[3 * a + d] + 1) * ha, cb = (2 * T.h_coord[3 * b + d] + 1) * hb;
+                    box_ext = std::max(box_ext, std::fabs(ca - cb) + ha);
                 }
+                const long long ebits = (long long)(exp_of(box_ext) + 128) << 48;
                 int64_t j0 = T.h_rng[4 * a], j1 = T.h_rng[4 * a + 1];
                 while (j0 < j1) {
                     const int64_t take = std::min<int64_t>(j1 - j0, kP2PUnitSrc - cnt);
-                    ranges.push_back(make_longlong2(j0 | far, j0 + take));
+                    ranges.push_back(make_longlong2(j0 | ebits, j0 + take));
+                    rleaf.push_back((int)li);
+                    rext.push_back(box_ext);
                     cnt += take;
                     j0 += take;
-                    if (cnt == kP2PUnitSrc) {
-                        units.push_back({make_int4((int)li, r0, (int)ranges.size(), 0), ntg * cnt});
-                        r0 = (int)ranges.size();
-                        cnt = 0;
-                    }
+                    if (cnt == kP2PUnitSrc) close_unit();
                 }
             }
-            if (cnt > 0 || units.size() == u0)
-                units.push_back({make_int4((int)li, r0, (int)ranges.size(), 0), ntg * cnt});
+            if (cnt > 0 || units.size() == u0) close_unit();
             const bool split = units.size() - u0 > 1;
             P.p2p_multi = P.p2p_multi || split;
             P.n_p2p_split += split ? 1 : 0;
-            for (size_t i = u0; i < units.size(); ++i) units[i].u.w = (i == u0 ? 1 : 0) | (split ? 2 : 0);
+            for (size_t i = u0; i < units.size(); ++i)
+                units[i].u.w = (i == u0 ? kUnitFirst : 0) | (split ? kUnitSplit : 0);
         }
-        std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.work > y.work; });
+        // FP64 scan: the closest pair of each range
+        const int nr = (int)ranges.size();
+        std::vector<int4> hcu;
+        std::vector<longlong2> hcr;
+        if (nr > 0) {
+            DBuf<longlong2> dr;
+            DBuf<int> drl;
+            DBuf<double> dmin;
+            KF_TRY(dr.upload(ranges, s));
+            KF_TRY(drl.upload(rleaf, s));
+            KF_TRY(dmin.alloc(2 * (size_t)nr));
+            const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
+            k_range_min_r2<<<div_up((int64_t)nr * 32, 256), 256, 0, s>>>(nr, dr.p, drl.p, P.tleaf.p, T.rng.p, T.sxyz.p,
+                                                                       T.ns, txyz, T.nt, dmin.p);
+            KF_CHECK_LAUNCH();
+            std::vector<double> minr2;
+            KF_TRY(download(minr2, dmin.p, 2 * (size_t)nr, s));
+            const double excl2 = (4.0 * kDelta) * (4.0 * kDelta);
+            for (int r = 0; r < nr; ++r) {
+                // FP32 offsets of this range's pairs are good to 2^-24 of 2^Er: a pair much
+                // closer than that takes the corrected distance, and so does a pair between
+                // delta/2 and 4 delta, whose exclusion it then decides to FP32 accuracy
+                const double close = std::ldexp(1.0, range_exp(ranges[r].x) - kCloseBits);
+                if (minr2[2 * r] < excl2) ranges[r].x |= kRangeExcl;
+                if (minr2[2 * r + 1] < std::max(close * close, excl2)) {
+                    ranges[r].x |= kRangeCorr;
+                    hcu.push_back(make_int4(rleaf[r], (int)hcr.size(), (int)hcr.size() + 1, kUnitSplit));
+                    hcr.push_back(ranges[r]);
+                }
+            }
+        }
+        P.near_pairs = 0;
+        for (const Unit& u : units) P.near_pairs += u.work;
+        // double layer: units whose sources' dipoles all lie along one coordinate axis take
+        // the one-term kernel (KIND 4), dealt after the others
+        std::vector<char> is_axis(units.size(), 0);
+        if (P.kernel == KIFMM_KERNEL_DL && T.ns > 0) {
+            std::vector<double> hn;
+            KF_TRY(download(hn, P.snrm.p, 3 * (size_t)T.ns, s));
+            std::vector<signed char> ax(T.ns);
+            for (int64_t j = 0; j < T.ns; ++j) {
+                const double c[3] = {hn[j], hn[T.ns + j], hn[2 * T.ns + j]};
+                ax[j] = -1;
+                for (int k = 0; k < 3; ++k)
+                    if (c[(k + 1) % 3] == 0.0 && c[(k + 2) % 3] == 0.0 && c[k] != 0.0) ax[j] = (signed char)k;
+            }
+            // run[j]: end of the run of equal axis codes from j
+            std::vector<int64_t> run(T.ns);
+            for (int64_t j = T.ns - 1; j >= 0; --j)
+                run[j] = (j + 1 < T.ns && ax[j + 1] == ax[j]) ? run[j + 1] : j + 1;
+            for (size_t i = 0; i < units.size(); ++i) {
+                int k = -2;
+                for (int r = units[i].u.y; r < units[i].u.z && k != -1; ++r) {
+                    const int64_t j0 = ranges[r].x & kRangeIdx, j1 = ranges[r].y;
+                    const int kr = (run[j0] >= j1) ? ax[j0] : -1;
+                    k = (k == -2 || k == kr) ? kr : -1;
+                }
+                if (k >= 0) {
+                    is_axis[i] = 1;
+                    units[i].u.w |= k << 8;
+                }
+            }
+        }
+        std::vector<size_t> ord(units.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {
+            if (is_axis[x] != is_axis[y]) return is_axis[x] < is_axis[y];
+            return units[x].work > units[y].work;
+        });
         std::vector<int4> hu(units.size());
-        for (size_t i = 0; i < units.size(); ++i) hu[i] = units[i].u;
+        P.n_p2p_axis = 0;
+        for (size_t i = 0; i < units.size(); ++i) {
+            hu[i] = units[ord[i]].u;
+            P.n_p2p_axis += is_axis[ord[i]];
+        }
         KF_TRY(P.p2p_units.upload(hu, s));
         KF_TRY(P.p2p_ranges.upload(ranges, s));
+        KF_TRY(P.p2p_cunits.upload(hcu, s));
+        KF_TRY(P.p2p_cranges.upload(hcr, s));
         P.n_p2p_units = (int)hu.size();
+        P.n_p2p_corr = (int)hcu.size();
+        for (int k = 0; k < 5; ++k) KF_TRY(set_p2p_smem(k));
     }
 
     // U2U: per parent level, (child -> parent) grouped by the child's octant
@@ -1751,19 +2104,31 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     // per-target evaluation rows and buffers
     size_t nbq = (size_t)T.nbox * P.Qp;
     if (P.fp64) {
-        KF_TRY(P.d2t_d.alloc((size_t)T.nt * P.Qp));
-        KF_TRY(build_d2t<double>(P, h, false, 0, tleaf_of, P.d2t_d.p, s));
+        KF_TRY(P.d2t_d.alloc((size_t)P.nc * T.nt * P.Qp));
+        if (P.cheb) {
+            DBuf<int> dleaf;
+            KF_TRY(dleaf.upload(tleaf_of, s));
+            for (int c = 0; c < P.nc; ++c)
+                KF_TRY(cheb_rows(P, T, dleaf.p, P.kernel == KIFMM_KERNEL_ADL ? P.tnrm_d.p : nullptr, c,
+                                 gradient_kernel(P.kernel), P.d2t_d.p + (size_t)c * T.nt * P.Qp, s));
+            KF_CHECK_CUDA(cudaStreamSynchronize(s));
+        } else {
+            for (int c = 0; c < P.nc; ++c)
+                KF_TRY(build_d2t<double>(P, h, false, 0, tleaf_of, c, P.d2t_d.p + (size_t)c * T.nt * P.Qp, s));
+        }
         KF_TRY(P.u_d.alloc(nbq));
         KF_TRY(P.d_d.alloc(nbq));
-        KF_TRY(P.res_d.alloc(T.nt));
+        KF_TRY(P.res_d.alloc((size_t)P.nc * T.nt));
         KF_TRY(P.q_d.alloc(3 * T.ns));
     } else {
         // rows G W_d, reading the projected down-check potentials
-        KF_TRY(P.d2t_f.alloc((size_t)T.nt * P.ops->Kd));
-        KF_TRY(build_d2t<float>(P, h, true, P.ops->Kd, tleaf_of, P.d2t_f.p, s));
+        KF_TRY(P.d2t_f.alloc((size_t)P.nc * T.nt * P.ops->Kd));
+        for (int c = 0; c < P.nc; ++c)
+            KF_TRY(build_d2t<float>(P, h, true, P.ops->Kd, tleaf_of, c, P.d2t_f.p + (size_t)c * T.nt * P.ops->Kd, s));
         // (no FP32 check potentials: S2U and X write the projections' split inputs)
-        KF_TRY(P.res_f.alloc(T.nt));
-        KF_TRY(P.q_f.alloc((P.cnear ? 6 : 3) * T.ns));
+        KF_TRY(P.res_f.alloc((size_t)P.nc * T.nt));
+        // DL: the dipoles q n_j as FP32 and their FP32 remainders (6 rows); else 3 rows
+        KF_TRY(P.q_f.alloc((P.kernel == KIFMM_KERNEL_DL ? 6 : 3) * T.ns));
     }
     KF_CHECK_CUDA(cudaStreamSynchronize(s));
 
@@ -1772,7 +2137,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                      P.res_d.bytes(), P.q_d.bytes(), P.u_f.bytes(), P.d_f.bytes(), P.res_f.bytes(),
                      P.q_f.bytes(), P.snrm.bytes(), P.tnrm_d.bytes(), P.tnrm_f.bytes(),
                      P.bexp.bytes(), P.vin_h.bytes(), P.vin_l.bytes(), P.sexp.bytes(), P.sin_h.bytes(),
-                     P.sin_l.bytes(), P.sxf.bytes(), P.bcf.bytes(), P.zu.bytes(),
+                     P.sin_l.bytes(), P.sxf.bytes(), P.txf.bytes(), P.bcf.bytes(), P.zu.bytes(),
                      P.zd.bytes()})
         P.device_bytes += (int64_t)b;
     return KIFMM_OK;
@@ -1877,28 +2242,43 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     auto near_field = [&](cudaStream_t ns, const Real* res) -> int {
         const double* txyz = T.same ? T.sxyz.p : T.txyz.p;
         const int64_t* tperm = T.same ? T.sperm.p : T.tperm.p;
-        // FP32 with leaves of up to 64 targets: a warp per leaf; larger leaves (and FP64):
-        // a block per leaf, whose staged sources serve all of the leaf's targets at once
+        // FP32: the warp kernel over the near-field units (the single layer's leaves above
+        // kP2PWarpMaxLeaf targets, and FP64: a block per leaf, whose staged sources serve
+        // all of the leaf's targets at once)
         bool done = false;
         if constexpr (std::is_same<Real, float>::value) {
-          if (P.max_trg_leaf <= kP2PWarpMaxLeaf) {
-            const unsigned grid = (unsigned)((P.n_p2p_units + kP2PWarps - 1) / kP2PWarps);
+          if (warp_near(P)) {
             if (P.p2p_multi) {
-                KF_CHECK_CUDA(cudaMemsetAsync(out, 0, (size_t)T.nt * sizeof(double), ns));
+                KF_CHECK_CUDA(cudaMemsetAsync(out, 0, (size_t)P.nc * T.nt * sizeof(double), ns));
                 ++launches;
             }
-#define KF_P2PW(KIND, CN)                                                                                    \
-    k_p2p_warp<KIND, CN><<<grid, 32 * kP2PWarps, 0, ns>>>(P.tleaf.p, P.n_p2p_units, P.p2p_units.p,           \
-                                                          P.p2p_ranges.p, T.rng.p, T.ctr.p, P.sxf.p, T.ns, txyz, \
-                                                          T.nt, B.q, B.tnrm, P.tnrm_d.p, P.bcf.p, res, tperm, out)
-            if (P.kernel == KIFMM_KERNEL_SL) KF_P2PW(0, false);
-            else if (P.kernel == KIFMM_KERNEL_DL) {
-                if (P.cnear) KF_P2PW(1, true);
-                else KF_P2PW(1, false);
-            } else {
-                if (P.cnear) KF_P2PW(2, true);
-                else KF_P2PW(2, false);
+#define KF_P2PW(KIND, CORR, NU, UNITS, RANGES)                                                                 \
+    k_p2p_warp<KIND, CORR><<<(unsigned)div_up(NU, kP2PWarps), 32 * kP2PWarps, p2p_warp_smem<KIND>(), ns>>>(      \
+        P.tleaf.p, NU, UNITS, RANGES, T.rng.p, P.bcf.p, P.sxf.p, T.ns, T.same ? P.sxf.p : P.txf.p, T.nt, B.q,     \
+        P.tnrm_f.p, res, tperm, out)
+#define KF_P2PK(CORR, NU, UNITS, RANGES)                                                                        \
+    if (P.kernel == KIFMM_KERNEL_SL) KF_P2PW(0, CORR, NU, UNITS, RANGES);                                       \
+    else if (P.kernel == KIFMM_KERNEL_DL) KF_P2PW(1, CORR, NU, UNITS, RANGES);                                  \
+    else if (P.kernel == KIFMM_KERNEL_ADL) KF_P2PW(2, CORR, NU, UNITS, RANGES);                                 \
+    else KF_P2PW(3, CORR, NU, UNITS, RANGES);
+            {
+                const int ngen = P.n_p2p_units - P.n_p2p_axis;
+                if (ngen > 0 || P.n_p2p_axis == 0) KF_P2PK(false, ngen, P.p2p_units.p, P.p2p_ranges.p)
+                if (P.n_p2p_axis) {
+                    if (ngen > 0) {
+                        KF_CHECK_LAUNCH();
+                        ++launches;
+                    }
+                    KF_P2PW(4, false, P.n_p2p_axis, P.p2p_units.p + ngen, P.p2p_ranges.p);
+                }
             }
+            // the ranges with close pairs, added after the plain launch (same stream)
+            if (P.n_p2p_corr) {
+                KF_CHECK_LAUNCH();
+                ++launches;
+                KF_P2PK(true, P.n_p2p_corr, P.p2p_cunits.p, P.p2p_cranges.p)
+            }
+#undef KF_P2PK
 #undef KF_P2PW
             done = true;
           }
@@ -1912,7 +2292,8 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
                                                         res, tperm, out)
         if (P.kernel == KIFMM_KERNEL_SL) KF_P2P(0);
         else if (P.kernel == KIFMM_KERNEL_DL) KF_P2P(1);
-        else KF_P2P(2);
+        else if (P.kernel == KIFMM_KERNEL_ADL) KF_P2P(2);
+        else KF_P2P(3);
 #undef KF_P2P
         }
         KF_CHECK_LAUNCH();
@@ -1921,16 +2302,18 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     };
     // mixed, warp near field: it runs on its own stream beside the far field (forked
     // after the gather) and the far field is added once both are done
-    const bool near_overlap = std::is_same<Real, float>::value && P.n_tleaf && P.near_stream &&
-                              P.max_trg_leaf <= kP2PWarpMaxLeaf;
+    const bool near_overlap = std::is_same<Real, float>::value && P.n_tleaf && P.near_stream && warp_near(P) &&
+                              !P.serial;
     const bool dl = P.kernel == KIFMM_KERNEL_DL;
+    // mixed DL: the FP32 remainders of the dipoles too (the near field's exact products)
+    const bool dl_lo = dl && std::is_same<Real, float>::value;
     KF_TRY(mark(0));
     if (P.io_in)
         k_scatter_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, P.isperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q,
-                                                            P.cnear && dl);
+                                                            dl_lo);
     else
         k_gather_q<Real><<<div_up(T.ns, 256), 256, 0, s>>>(q, T.sperm.p, T.ns, dl ? P.snrm.p : nullptr, B.q,
-                                                           P.cnear && dl);
+                                                           dl_lo);
     KF_CHECK_LAUNCH();
     ++launches;
     const cudaStream_t s_in = s;                  // the caller's stream
@@ -1973,8 +2356,16 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_TRY(mark(1));
     // S2U
     if (P.n_s2u) {
-        KF_TRY(launch_surf<Real>(P, T, dl, P.n_s2u, P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, kUpCheck, B.q, B.surf,
-                                 B.u, s));
+        if constexpr (std::is_same<Real, double>::value) {
+            if (P.cheb)
+                KF_TRY(cheb_s2m(P, T, dl, P.n_s2u, P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, B.q, B.u, s));
+            else
+                KF_TRY(launch_surf<Real>(P, T, dl, P.n_s2u, P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, kUpCheck, B.q,
+                                         B.surf, B.u, s));
+        } else {
+            KF_TRY(launch_surf<Real>(P, T, dl, P.n_s2u, P.s2u_box.p, P.s2u_off.p, P.s2u_idx.p, kUpCheck, B.q, B.surf,
+                                     B.u, s));
+        }
         ++launches;
     }
     if (near_overlap) KF_TRY(fork_near());
@@ -1988,8 +2379,9 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_TRY(mark(3));
     // X list (mixed: then the X boxes' projections), then V list
     if (P.n_p2l) {
-        KF_TRY(launch_surf<Real>(P, T, dl, P.n_p2l, P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, kDnCheck, B.q, B.surf,
-                                 B.d, s));
+        // (the Chebyshev engine: X sources straight onto the box's nodes)
+        KF_TRY(launch_surf<Real>(P, T, dl, P.n_p2l, P.p2l_box.p, P.p2l_off.p, P.p2l_idx.p, P.cheb ? 1.0 : kDnCheck,
+                                 B.q, B.surf, B.d, s));
         ++launches;
         if constexpr (mixed) KF_TRY(project(P, 4, P.proj_x, dn, s, launches));
     }
@@ -2000,7 +2392,7 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     KF_TRY(mark(5));
     // L2L, coarsest children first (ADL in FP64: each level's potentials shifted to zero
     // mean first; the mixed tables carry that centring)
-    const bool center = !mixed && P.kernel == KIFMM_KERNEL_ADL;
+    const bool center = !mixed && gradient_kernel(P.kernel);
     for (int l = 2; l < T.nlev; ++l) {
         if (l >= 3)
             KF_TRY(run_pairs<Real>(P, kL2L, P.l2l, P.l2l.level_tile[l], P.l2l.level_tile[l + 1], B.l2l, dn, dn,
@@ -2014,9 +2406,12 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     }
     KF_TRY(mark(6));
     if (P.n_tleaf) {
-        k_d2t<Real><<<P.n_tleaf, 128, dw * sizeof(Real), s>>>(P.tleaf.p, T.rng.p, B.d2t, dn, dw, B.res);
-        KF_CHECK_LAUNCH();
-        ++launches;
+        for (int c = 0; c < P.nc; ++c) {
+            k_d2t<Real><<<P.n_tleaf, 128, dw * sizeof(Real), s>>>(P.tleaf.p, T.rng.p, B.d2t + (size_t)c * T.nt * dw,
+                                                                  dn, dw, B.res + (size_t)c * T.nt);
+            KF_CHECK_LAUNCH();
+            ++launches;
+        }
     }
     KF_TRY(mark(7));
     if (!near_overlap) {
@@ -2032,14 +2427,15 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         KF_CHECK_CUDA(cudaStreamWaitEvent(s, P.ev_join, 0));
         if (P.io_out)
             k_add_far_io<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(P.itperm.p, reinterpret_cast<const float*>(B.res),
-                                                                     out, T.nt, P.io_out);
+                                                                     out, T.nt, P.nc, P.io_out);
         else
             k_add_far<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(T.same ? T.sperm.p : T.tperm.p,
-                                                                  reinterpret_cast<const float*>(B.res), T.nt, out);
+                                                                  reinterpret_cast<const float*>(B.res), T.nt, P.nc,
+                                                                  out);
         KF_CHECK_LAUNCH();
         ++launches;
     } else if (P.io_out) {
-        k_add_far_io<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(P.itperm.p, nullptr, out, T.nt, P.io_out);
+        k_add_far_io<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(P.itperm.p, nullptr, out, T.nt, P.nc, P.io_out);
         KF_CHECK_LAUNCH();
         ++launches;
     }
@@ -2071,10 +2467,13 @@ extern "C" int kifmm_fmm_setup(kifmm_tree tree, int kernel, int p, int precision
     KF_ARG(out != nullptr, "out is NULL");
     *out = nullptr;
     KF_ARG(tree != nullptr, "tree is NULL");
-    KF_ARG(kernel >= KIFMM_KERNEL_SL && kernel <= KIFMM_KERNEL_ADL, "unknown kernel");
+    KF_ARG(kernel >= KIFMM_KERNEL_SL && kernel <= KIFMM_KERNEL_FIELD, "unknown kernel");
     KF_ARG(p >= 2 && p <= 16, "p must be in [2, 16]");
-    KF_ARG(precision == KIFMM_PREC_FP64 || precision == KIFMM_PREC_MIXED || precision == KIFMM_PREC_MIXED_CN,
-           "unknown precision");
+    const bool cheb = (precision & KIFMM_ENGINE_CHEB) != 0;
+    precision &= ~KIFMM_ENGINE_CHEB;
+    KF_ARG(precision == KIFMM_PREC_FP64 || precision == KIFMM_PREC_MIXED, "unknown precision");
+    KF_ARG(!cheb || precision == KIFMM_PREC_FP64, "the Chebyshev engine runs in FP64 only");
+    KF_ARG(!cheb || (p >= 2 && p <= kChebMaxN), "Chebyshev order must be in [2, 8]");
     KF_ARG(pinv_cutoff == 0.0 || (pinv_cutoff > 0.0 && pinv_cutoff < 1.0), "pinv_cutoff must be 0 or in (0,1)");
     KF_ARG(kernel != KIFMM_KERNEL_DL || src_nrm != nullptr, "DL needs src_nrm");
     KF_ARG(kernel != KIFMM_KERNEL_ADL || trg_nrm != nullptr, "ADL needs trg_nrm");
@@ -2089,9 +2488,20 @@ extern "C" int kifmm_fmm_setup(kifmm_tree tree, int kernel, int p, int precision
     Plan& P = pl->P;
     P.tree = tree;
     P.kernel = kernel;
+    P.cheb = cheb;
+    P.nc = kernel == KIFMM_KERNEL_FIELD ? 3 : 1;
     P.p = p;
     P.prec = precision;
-    P.cutoff = pinv_cutoff > 0 ? pinv_cutoff : (precision == KIFMM_PREC_FP64 ? 1e-9 : 1e-8);
+    // default truncations: FP64 1e-9; mixed 1e-8, except the double layer's Pu at 1e-9
+    // (dipole sources need the smaller singular directions of the upward surface)
+    if (pinv_cutoff > 0) {
+        P.cut_up = P.cut_dn = pinv_cutoff;
+    } else if (precision == KIFMM_PREC_FP64) {
+        P.cut_up = P.cut_dn = 1e-9;
+    } else {
+        P.cut_dn = 1e-8;
+        P.cut_up = kernel == KIFMM_KERNEL_DL ? 1e-9 : 1e-8;
+    }
     int rc = setup(P, src_nrm, trg_nrm, (cudaStream_t)stream);
     if (rc != KIFMM_OK) {
         delete pl;
@@ -2173,7 +2583,7 @@ int ensure_host_io(Plan& P, cudaStream_t s) {
     if (P.isperm.p || (T.ns == 0 && T.nt == 0)) return KIFMM_OK;
     KF_TRY(P.isperm.alloc(std::max<int64_t>(T.ns, 1)));
     KF_TRY(P.itperm.alloc(std::max<int64_t>(T.nt, 1)));
-    KF_TRY(P.out_stage.alloc(std::max<int64_t>(T.nt, 1)));
+    KF_TRY(P.out_stage.alloc(std::max<int64_t>((int64_t)P.nc * T.nt, 1)));
     if (T.ns) k_invert_perm<<<(unsigned)div_up(T.ns, 256), 256, 0, s>>>(T.sperm.p, T.ns, P.isperm.p);
     if (T.nt)
         k_invert_perm<<<(unsigned)div_up(T.nt, 256), 256, 0, s>>>(T.same ? T.sperm.p : T.tperm.p, T.nt,
@@ -2256,7 +2666,8 @@ extern "C" int kifmm_fmm_matvec_host(kifmm_plan plan, const double* q, double* o
     P.io_out = nullptr;
     if (rc != KIFMM_OK) return rc;
     if (ko == 0 && T.nt)
-        KF_CHECK_CUDA(cudaMemcpyAsync(out, P.out_stage.p, T.nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+        KF_CHECK_CUDA(cudaMemcpyAsync(out, P.out_stage.p, (size_t)P.nc * T.nt * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
     return KIFMM_OK;
 }
 
@@ -2267,8 +2678,9 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->kernel = P.kernel;
     st->p = P.p;
     st->q_points = P.Q;
-    st->precision = P.prec;
-    st->pinv_cutoff = P.cutoff;
+    st->precision = P.prec | (P.cheb ? KIFMM_ENGINE_CHEB : 0);
+    st->pinv_cutoff = P.cut_dn;
+    st->pinv_cutoff_up = P.cut_up;
     st->device_bytes = P.device_bytes;
     st->m2l_pairs = P.m2l.npairs;
     st->u2u_pairs = P.u2u.npairs;
@@ -2282,7 +2694,10 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->m2l_rows = P.fp64 ? P.Q : st->rank_down;
     st->near_units = P.n_p2p_units;
     st->near_split_leaves = P.n_p2p_split;
-    st->near_overlap = (!P.fp64 && P.near_stream && P.n_tleaf && P.max_trg_leaf <= kP2PWarpMaxLeaf) ? 1 : 0;
+    st->near_overlap = (!P.fp64 && P.near_stream && P.n_tleaf && warp_near(P)) ? 1 : 0;
+    st->near_corr_ranges = P.n_p2p_corr;
+    st->near_axis_units = P.n_p2p_axis;
+    st->near_pairs = P.near_pairs;
     st->s2u_points = (P.fp64 || !P.ops) ? P.Q : P.ops->ks;
     st->m2l_chain_pairs = P.m2l_chain_pairs;
     return KIFMM_OK;
@@ -2335,6 +2750,7 @@ extern "C" int kifmm_plan_profile(kifmm_plan plan, int enable, double* phases) {
         P.slots_used = 0;
     }
     P.profile = enable != 0;
+    P.serial = enable == 2;
     return KIFMM_OK;
 }
 

@@ -148,19 +148,19 @@ static std::vector<double> kernel_matrix(const std::vector<double>& x, double sx
     return K;
 }
 
-const HostPinv& host_pinv(int p, double cutoff) {
+const HostPinv& host_pinv(int p, double cut_up, double cut_dn) {
     static std::mutex mu;
-    static std::map<std::pair<int, double>, HostPinv> cache;
+    static std::map<std::tuple<int, double, double>, HostPinv> cache;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_pair(p, cutoff);
+    auto key = std::make_tuple(p, cut_up, cut_dn);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     HostPinv h;
     h.p = p;
     h.surf = surface_points(p);
     h.Q = (int)h.surf.size() / 3;
-    h.Pu = pinv_jacobi(kernel_matrix(h.surf, kUpCheck, h.surf, kUpEquiv), h.Q, cutoff, &h.Uu, &h.Wu, &h.ru);
-    h.Pd = pinv_jacobi(kernel_matrix(h.surf, kDnCheck, h.surf, kDnEquiv), h.Q, cutoff, &h.Ud, &h.Wd, &h.rd);
+    h.Pu = pinv_jacobi(kernel_matrix(h.surf, kUpCheck, h.surf, kUpEquiv), h.Q, cut_up, &h.Uu, &h.Wu, &h.ru);
+    h.Pd = pinv_jacobi(kernel_matrix(h.surf, kDnCheck, h.surf, kDnEquiv), h.Q, cut_dn, &h.Ud, &h.Wd, &h.rd);
     return cache.emplace(key, std::move(h)).first->second;
 }
 

@@ -29,7 +29,8 @@ std::vector<double> surface_points(int p);
 std::vector<double> pinv_jacobi(const std::vector<double>& A_rm, int n, double cutoff,
                                 std::vector<double>* U = nullptr, std::vector<double>* W = nullptr,
                                 int* rank = nullptr);
-const HostPinv& host_pinv(int p, double cutoff);
+// Pu truncated at cut_up * sigma_max, Pd at cut_dn * sigma_max; cached per (p, cuts).
+const HostPinv& host_pinv(int p, double cut_up, double cut_dn);
 
 // Column-pivoted Householder QR of A = K(2.95 s_i, 1.05 s_j)^T, the transposed map from
 // the upward equivalent surface to the upward check surface (both Q points of the unit

@@ -31,7 +31,7 @@ struct BieScratch {
     DBuf<double> q, krylov, w, r;
 };
 
-// Translation tables of one (device, order, cutoff, precision, ADL centring): shared by
+// Translation tables of one (device, order, cutoffs, precision, ADL centring): shared by
 // every plan with that key, freed with the last of them.  FP64 form: m2m/m2l/l2l in
 // FP64, Qp x Qp each.  Mixed form: every translation acts between projections onto
 // the ranges of the pseudo-inverses (P = W U^T, U orthonormal): families 0 M2M''
@@ -42,8 +42,9 @@ struct BieScratch {
 constexpr int kFamilies = 5;
 struct OpTables {
     int device = 0, p = 0;
-    double cutoff = 0;
+    double cut_up = 0, cut_dn = 0;  // truncation of Pu and Pd, relative to sigma_max
     bool fp64 = true, centered = false;
+    bool cheb = false;              // the Chebyshev engine's tables
     int ru = 0, rd = 0, Ku = 0, Kd = 0;
     int ks = 0;                     // mixed: S2U points (skeleton of the up-check surface)
     DBuf<float> surf_up;            // mixed: those points on the unit surface, ks x 3
@@ -61,7 +62,9 @@ struct OpTables {
 struct Plan {
     kifmm_tree_s* tree = nullptr;
     int kernel = 0, p = 0, Q = 0, Qp = 0, prec = 0;
-    double cutoff = 0;
+    int nc = 1;                     // output components per target (the field: 3)
+    bool cheb = false;              // far field by Chebyshev interpolation (p = nodes per dimension)
+    double cut_up = 0, cut_dn = 0;  // pseudo-inverse truncations (up: Pu, down: Pd)
     bool fp64 = true;
 
     // translation tables (shared, see OpTables), each Qp x Qp row-major; D2T rows in
@@ -80,8 +83,9 @@ struct Plan {
 
     DBuf<double> snrm, tnrm_d;      // sorted normals (DL: sources; ADL: targets)
     DBuf<float> sxf;                // mixed: sorted source coordinates as FP32 hi/lo pairs, 6 x ns SoA
+    DBuf<float> txf;                // mixed, targets apart from the sources: the same for them
     DBuf<float4> bcf;               // mixed: per box {centre hi, h}, {centre lo, 0}, {r_upcheck, r_dncheck}
-    DBuf<float> tnrm_f;
+    DBuf<float> tnrm_f;             // mixed ADL: sorted target normals, FP32 hi (3 rows) and lo (3 rows)
 
     // work lists
     DBuf<int> s2u_box, s2u_off, s2u_idx;  // S2U: leaf boxes, CSR of source boxes (itself)
@@ -91,7 +95,11 @@ struct Plan {
                                           // end range, flags: 1 first of its leaf, 2 leaf split)
     DBuf<longlong2> p2p_ranges;           // mixed: source index ranges of the units
     int n_p2p_units = 0, n_p2p_split = 0;
-    bool cnear = false;                   // mixed: compensated DL/ADL near field
+    int64_t near_pairs = 0;               // mixed: (target, source) pairs the near field evaluates
+    DBuf<int4> p2p_cunits;                // mixed: one unit per range with close pairs (the
+    DBuf<longlong2> p2p_cranges;          //   corrected-distance launch) and those ranges
+    int n_p2p_corr = 0;
+    int n_p2p_axis = 0;                   // DL: the last units of p2p_units, dipoles along one axis
     bool p2p_multi = false;               // some leaf spans several units
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
@@ -112,6 +120,7 @@ struct Plan {
 
     // profiling: per-matvec slots of 8 events, reduced when read
     bool profile = false;
+    bool serial = false;            // profiling: the near field after the far field, on one stream
     std::vector<std::vector<cudaEvent_t>> ev_slots;
     int slots_used = 0;
     int launches = 0;

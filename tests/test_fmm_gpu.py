@@ -1,11 +1,11 @@
 """GPU KIFMM through the C ABI vs the FP64 oracle (direct O(N^2) sums).
 
 Relative L2 error over all targets; full-size cases compare a seeded sample of
-targets, each computed exactly by the oracle.  Tolerances are the accuracy each
-form reaches at its order: the mixed form at p = 10 reaches 1e-6 on the benchmark
-geometry (cube, double layer) and for the single layer, 1-3e-6 for the double and
-adjoint double layer on curved or adaptive geometries (FP32 near-field cancellation
-in n.(x - y) and gradient evaluation of the far field); FP64 at p = 12 reaches 1e-8.
+targets, each computed exactly by the oracle.  The mixed form is held to rel-L2 <= 1e-6
+everywhere: the single and double layer at expansion order p = 10, the adjoint double
+layer at p = 11 (its far-field gradient rows, evaluated in FP32, sit at 0.7-1e-6 at
+p = 10 on curved surfaces; p = 11 is the lowest order that meets the target with a
+margin).  Orders below 8 are held to their truncation error (test_mixed_orders).
 """
 import math
 
@@ -63,7 +63,8 @@ def test_quadrature_points_match_oracle():
 
 
 # (kernel, precision, p, tolerance)
-MIXED = [("sl", "mixed", 10, 1e-6), ("dl", "mixed", 10, 3e-6), ("adl", "mixed", 10, 4e-6)]
+MIXED = [("sl", "mixed", 10, 1e-6), ("dl", "mixed", 10, 1e-6), ("adl", "mixed", 11, 1e-6)]
+P_MIXED = {"sl": 10, "dl": 10, "adl": 11}
 FP64 = [("sl", "fp64", 12, 1e-8), ("dl", "fp64", 12, 1e-7), ("adl", "fp64", 12, 1e-7)]
 
 
@@ -82,28 +83,34 @@ def test_fmm_matches_oracle(geom, kernel, prec, p, tol):
     assert err < tol
 
 
-@pytest.mark.parametrize("geom", ["sphere", "pack", "cube"])
-@pytest.mark.parametrize("kernel", ["dl", "adl"])
-def test_compensated_near_field(geom, kernel):
-    """mixed_cn: the double-layer near field with error-free n.(x - y) products.  DL
-    then meets 1e-6 on curved and adaptive geometries too; ADL improves by at least a
-    third, to about 1e-6, the rest being its far-field gradient rows."""
+def test_near_field_alone_at_single_layer_accuracy():
+    """A curved patch of 64 points that fits one leaf: the whole sum is near field, so
+    the result shows the FP32 near field's own accuracy.  On a sphere of radius 1
+    n.(x - y) between neighbours 0.02 apart is about 2e-4 of |x - y|^2 / |x - y|, and
+    plain FP32 offsets and products lose a factor 2R/|x - y| ~ 100 of it to
+    cancellation.  With the exact hi products the double layers stay at the single
+    layer's accuracy: within 3x of its error on the same points, and below 1e-6."""
     from paper_1605_01715_gb300 import Plan, Tree
-    m, h, (xyz, w, nrm), sig, refs = case(geom)
-    q = torch.from_numpy(sig).to(DEV) * w
+    rng = np.random.default_rng(31)
+    gx, gy = np.meshgrid(np.arange(8) * 0.02 - 0.07, np.arange(8) * 0.02 - 0.07)
+    v = np.stack([gx.ravel(), gy.ravel(), np.ones(64)]) + rng.uniform(-0.003, 0.003, (3, 64))
+    v /= np.linalg.norm(v, axis=0)                  # points on the unit sphere near the pole
+    xyz, nrm = v + 0.3, v.copy()
+    q = rng.uniform(-1.0, 1.0, 64) * 1e-3
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    tree = Tree(t(xyz), max_leaf=64)
+    assert tree.stats()["n_leaves"] == 1
     errs = {}
-    for prec in ("mixed", "mixed_cn"):
-        plan = Plan(Tree(xyz, max_leaf=40), kernel=kernel, p=10, precision=prec, src_nrm=nrm, trg_nrm=nrm)
-        out = plan.matvec(q).cpu().numpy()
-        plan.check()
-        errs[prec] = rel(out, refs[kernel])
-    print("%s %s mixed %.3e mixed_cn %.3e" % (geom, kernel, errs["mixed"], errs["mixed_cn"]))
-    if kernel == "dl":
-        assert errs["mixed_cn"] < 1e-6
-    else:
-        assert errs["mixed_cn"] < 1.1e-6
-    if geom != "cube":                              # flat faces: n.(x - y) = 0 exactly
-        assert errs["mixed_cn"] < 0.7 * errs["mixed"]
+    for kernel in ("sl", "dl", "adl"):
+        ref = oracle.direct(kernel, xyz, xyz, q, src_nrm=nrm if kernel == "dl" else None,
+                            trg_nrm=nrm if kernel == "adl" else None)
+        plan = Plan(tree, kernel=kernel, p=6, precision="mixed", src_nrm=t(nrm), trg_nrm=t(nrm))
+        assert plan.stats()["near_corr_ranges"] == 0      # the plain path, not the corrected one
+        errs[kernel] = rel(plan.matvec(t(q)).cpu().numpy(), ref)
+    print("single-leaf curved patch rel-L2", errs)
+    for kernel in ("sl", "dl", "adl"):
+        assert errs[kernel] < 1e-6
+    assert errs["dl"] < max(3 * errs["sl"], 2e-7) and errs["adl"] < max(3 * errs["sl"], 2e-7)
 
 
 def test_benchmark_geometry_meets_1e6():
@@ -116,9 +123,11 @@ def test_benchmark_geometry_meets_1e6():
     assert rel(plan.matvec(q).cpu().numpy(), refs["dl"]) <= 1e-6
 
 
-@pytest.mark.parametrize("p,tol", [(4, 3e-3), (6, 3e-5), (8, 2e-6), (12, 1e-6)])
+@pytest.mark.parametrize("p,tol", [(4, 3e-3), (6, 3e-5), (8, 1e-6), (12, 1e-6)])
 def test_mixed_orders(p, tol):
-    """Every order in the mixed form (odd and even K-chunk counts of the tensor-core GEMM)."""
+    """Every order in the mixed form (odd and even K-chunk counts of the tensor-core GEMM).
+    Orders 4 and 6 are held to their truncation error, which decays with p (about 1.6e-4
+    and 1.9e-6 on this sphere), not to 1e-6."""
     from paper_1605_01715_gb300 import Plan, Tree
     m, h, (xyz, w, nrm), sig, refs = case("sphere")
     plan = Plan(Tree(xyz, max_leaf=40), kernel="sl", p=p, precision="mixed")
@@ -150,15 +159,13 @@ def test_factored_m2l_widths():
         assert mx["s2u_points"] == {6: Q, 8: Q, 10: 384}[p]
 
 
-@pytest.mark.parametrize("prec", ["mixed", "mixed_cn"])
-@pytest.mark.parametrize("kernel,tol", [("sl", 1e-6), ("dl", 3e-6), ("adl", 4e-6)])
-def test_near_field_units_split_heavy_leaves(kernel, tol, prec):
+@pytest.mark.parametrize("kernel", ["sl", "dl", "adl"])
+def test_near_field_units_split_heavy_leaves(kernel):
     """A 5,120-point sphere of radius 0.03 beside a unit sphere of the same point count:
     leaves of the large sphere next to the small one take thousands of W- and X-list
     sources, so the FP32 near field splits them over several work units whose sums
-    meet by atomics.  The result still matches the oracle, also in the compensated form
-    and replayed from a captured graph (the zeroing of the outputs and the units'
-    atomics run inside it)."""
+    meet by atomics.  The result still matches the oracle, also replayed from a captured
+    graph (the zeroing of the outputs and the units' atomics run inside it)."""
     from paper_1605_01715_gb300 import Plan, Tree
     m = synth.pack_mesh(np.array([[0.0, 0.0, 0.0], [1.04, 0.0, 0.0]]), np.array([1.0, 0.03]), 16)
     h = quadrature_points(m.tri, m.sph)
@@ -166,7 +173,8 @@ def test_near_field_units_split_heavy_leaves(kernel, tol, prec):
     sig = synth.uniform_density(m.n, 23)
     ref = oracle.direct(kernel, h[0], h[0], sig * h[1], src_nrm=h[2] if kernel == "dl" else None,
                         trg_nrm=h[2] if kernel == "adl" else None)
-    plan = Plan(Tree(xyz, max_leaf=32), kernel=kernel, p=10, precision=prec, src_nrm=nrm, trg_nrm=nrm)
+    plan = Plan(Tree(xyz, max_leaf=32), kernel=kernel, p=P_MIXED[kernel], precision="mixed", src_nrm=nrm,
+                trg_nrm=nrm)
     st = plan.stats()
     assert st["near_split_leaves"] > 0 and st["near_units"] > st["near_split_leaves"]
     q = torch.from_numpy(sig).to(DEV) * w
@@ -177,9 +185,9 @@ def test_near_field_units_split_heavy_leaves(kernel, tol, prec):
     torch.cuda.synchronize()
     plan.check()
     err = rel(out, ref)
-    print("heavy-leaf pair %s %s p=10 rel-L2 %.3e, %d units, %d split leaves"
-          % (kernel, prec, err, st["near_units"], st["near_split_leaves"]))
-    assert err < tol
+    print("heavy-leaf pair %s rel-L2 %.3e, %d units, %d split leaves"
+          % (kernel, err, st["near_units"], st["near_split_leaves"]))
+    assert err < 1e-6
     assert rel(graph.cpu().numpy(), out) < 1e-6
 
 
@@ -189,11 +197,11 @@ def test_leaf_sizes_and_repeat(max_leaf):
     from paper_1605_01715_gb300 import Plan, Tree
     m, h, (xyz, w, nrm), sig, refs = case("sphere")
     tree = Tree(xyz, max_leaf=max_leaf)
-    plan = Plan(tree, kernel="sl", p=8, precision="mixed")
+    plan = Plan(tree, kernel="sl", p=10, precision="mixed")
     q = torch.from_numpy(sig).to(DEV) * w
     a = plan.matvec(q).cpu().numpy()
     b = plan.matvec(q).cpu().numpy()
-    assert rel(a, refs["sl"]) < 2e-6
+    assert rel(a, refs["sl"]) < 1e-6
     assert rel(a, b) < 1e-6
 
 
@@ -208,13 +216,15 @@ def test_target_source_model():
     ttrg = torch.from_numpy(trg).to(DEV)
     tree = Tree(xyz, ttrg, max_leaf=48)
     q = torch.from_numpy(sig).to(DEV) * w
-    # volume targets: measured 1e-7 (SL), 7.7e-6 (DL), < 6e-6 (ADL) in the mixed form
-    for kernel, tol in (("sl", 1e-6), ("dl", 1e-5), ("adl", 1e-5)):
-        plan = Plan(tree, kernel=kernel, p=10, precision="mixed", src_nrm=nrm,
+    # volume targets, some within 1e-3 of the surface, where n.(x - y) is small
+    for kernel in ("sl", "dl", "adl"):
+        plan = Plan(tree, kernel=kernel, p=P_MIXED[kernel], precision="mixed", src_nrm=nrm,
                     trg_nrm=torch.from_numpy(tnrm).to(DEV))
         ref = oracle.direct(kernel, trg, h[0], sig * h[1], src_nrm=h[2] if kernel == "dl" else None,
                             trg_nrm=tnrm if kernel == "adl" else None)
-        assert rel(plan.matvec(q).cpu().numpy(), ref) < tol
+        err = rel(plan.matvec(q).cpu().numpy(), ref)
+        print("volume targets %s rel-L2 %.3e" % (kernel, err))
+        assert err < 1e-6
 
 
 def test_m2l_chains_on_flat_faces():
@@ -288,7 +298,7 @@ def test_matvec_host_buffers(prec):
                     assert diff <= tol, (kernel, pinned, graph, diff, int(oh.isnan().sum()))
                     oh.fill_(float("nan"))
         if kernel == "dl" and prec == "mixed":
-            assert rel(ref.numpy(), refs["dl"]) < 2e-6
+            assert rel(ref.numpy(), refs["dl"]) < 1e-6
 
 
 def test_tolerance_radius_and_tiny_inputs():
@@ -305,9 +315,12 @@ def test_tolerance_radius_and_tiny_inputs():
     for prec in ("fp64", "mixed"):
         plan = Plan(Tree(torch.from_numpy(pts).to(DEV), max_leaf=4), kernel="sl", p=4, precision=prec)
         out = plan.matvec(torch.from_numpy(q).to(DEV)).cpu().numpy()
-        # mixed: pairs 1e-4 apart inside a leaf of half-width 0.25 keep ~3e-8/1e-4 of
-        # relative separation in FP32 leaf-centred coordinates
-        assert rel(out, ref) < (1e-12 if prec == "fp64" else 1e-4)
+        # mixed: a pair 1e-4 apart in a leaf of half-width 0.25 would keep only ~3e-4 of
+        # its separation in FP32 leaf-centred offsets; the set-up scan flags that range
+        # and the near field evaluates it in FP64
+        assert rel(out, ref) < (1e-12 if prec == "fp64" else 1e-6)
+        if prec == "mixed":
+            assert plan.stats()["near_corr_ranges"] >= 1
 
 
 def test_invalid_arguments_raise():
@@ -361,7 +374,7 @@ def test_polarization_operator_and_rhs():
     x = synth.uniform_density(m.n, 5)
     A = obie.polarization_operator(hx, hn, hw, eps, 1.0, curv)
     ref = A(x)
-    plan = Plan(Tree(xyz, max_leaf=32), kernel="adl", p=10, precision="mixed", trg_nrm=nrm)
+    plan = Plan(Tree(xyz, max_leaf=32), kernel="adl", p=P_MIXED["adl"], precision="mixed", trg_nrm=nrm)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
     y = plan.bie_apply(w, t(eps), 1.0, t(curv), t(x)).cpu().numpy()
     assert rel(y, ref) < 1e-6
@@ -369,10 +382,16 @@ def test_polarization_operator_and_rhs():
     assert rel(b, obie.polarization_rhs_uniform_field(hn, eps, 1.0, (0, 0, 1))) < 1e-14
 
 
-@pytest.mark.parametrize("prec,tol_x", [("fp64", 1e-7), ("mixed", 1e-5)])
-def test_polarization_gmres_matches_oracle_solve(prec, tol_x):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_polarization_gmres_matches_oracle_solve(prec):
+    """GPU GMRES on the two-sphere polarization system against the oracle's GMRES (to
+    1e-10).  The GPU solution's residual under the oracle's own operator must be below
+    1e-6 (mixed: the matvec's 1e-6 accuracy plus the solve tolerance), and its distance
+    to the oracle's solution within what that residual allows:
+    |x - x*| / |x*| <= cond(A) |b - A x| / |b|, with cond(A) from the oracle's dense
+    operator."""
     from paper_1605_01715_gb300 import Plan, Tree, kifmm_polarization_rhs
-    m, eps, curv = _two_spheres()
+    m, eps, curv = _two_spheres(6)
     hx, hw, hn = quadrature_points(m.tri, m.sph)
     xyz, w, nrm = gpu_points(m)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
@@ -380,16 +399,21 @@ def test_polarization_gmres_matches_oracle_solve(prec, tol_x):
     b_h = obie.polarization_rhs_uniform_field(hn, eps, 1.0, (0, 0, 1))
     x_ref, it_ref, _, ok = gmres(A, b_h, tol=1e-10, restart=50)
     assert ok
-    plan = Plan(Tree(xyz, max_leaf=32), kernel="adl", p=12 if prec == "fp64" else 10, precision=prec,
+    dense = np.stack([A(e) for e in np.eye(m.n)], axis=1)
+    kappa = np.linalg.cond(dense)
+    plan = Plan(Tree(xyz, max_leaf=32), kernel="adl", p=12 if prec == "fp64" else P_MIXED["adl"], precision=prec,
                 trg_nrm=nrm)
     b = kifmm_polarization_rhs(nrm, t(eps), 1.0, (0.0, 0.0, 1.0))
     x, it, rr, rc = plan.bie_solve(w, t(eps), 1.0, t(curv), b, tol=1e-10 if prec == "fp64" else 1e-7,
                                    restart=30)
     x = x.cpu().numpy()
     assert rc == 0 and it > 0
-    assert rel(x, x_ref) < tol_x
-    # the true residual of the GPU solution under the oracle's operator
-    assert np.linalg.norm(b_h - A(x)) / np.linalg.norm(b_h) < 10 * tol_x
+    res_or = np.linalg.norm(b_h - A(x)) / np.linalg.norm(b_h)
+    err_x = rel(x, x_ref)
+    print("%s solve: %d its, oracle residual %.2e, |x - x*|/|x*| %.2e, cond(A) %.1f" % (prec, it, res_or, err_x,
+                                                                                      kappa))
+    assert res_or < (1e-8 if prec == "fp64" else 1e-6)
+    assert err_x <= kappa * (res_or + 1e-10) * 1.01
 
 
 def test_dielectric_sphere_closed_form_on_gpu():
@@ -401,12 +425,12 @@ def test_dielectric_sphere_closed_form_on_gpu():
     n = m.n
     eps = torch.full((n,), ei, dtype=torch.float64, device=DEV)
     curv = torch.full((n,), 1.0 / R, dtype=torch.float64, device=DEV)
-    plan = Plan(Tree(xyz, max_leaf=48), kernel="adl", p=10, precision="mixed", trg_nrm=nrm)
+    plan = Plan(Tree(xyz, max_leaf=48), kernel="adl", p=P_MIXED["adl"], precision="mixed", trg_nrm=nrm)
     b = kifmm_polarization_rhs(nrm, eps, 1.0, (0.0, 0.0, 1.0))
     x, it, rr, rc = plan.bie_solve(w, eps, 1.0, curv, b, tol=1e-7)
     exact = 3 * (ei - 1.0) / (ei + 2.0) * nrm[2]
-    # the true residual bottoms out near the FP32 operator's own rounding (~1e-6)
-    assert rc == 0 and rr < 1e-5
+    # rr: the true residual under the library's own operator, after a solve to 1e-7
+    assert rc == 0 and rr < 1e-6
     assert rel(x.cpu().numpy(), exact.cpu().numpy()) < 1e-3
 
 

@@ -82,8 +82,8 @@ def test_forest_lists_stay_inside_instances():
                 assert np.all(owner[srcs] == owner[b]), ("list %s joins instances" % which)
 
 
-@pytest.mark.parametrize("kernel,prec,p,tol", [("sl", "mixed", 10, 1e-6), ("dl", "mixed", 10, 3e-6),
-                                               ("adl", "mixed", 10, 4e-6), ("sl", "fp64", 12, 1e-8),
+@pytest.mark.parametrize("kernel,prec,p,tol", [("sl", "mixed", 10, 1e-6), ("dl", "mixed", 10, 1e-6),
+                                               ("adl", "mixed", 11, 1e-6), ("sl", "fp64", 12, 1e-8),
                                                ("dl", "fp64", 12, 1e-7), ("adl", "fp64", 12, 1e-7)])
 def test_forest_matches_oracle_per_instance(kernel, prec, p, tol):
     from paper_1605_01715_gb300 import Plan, Tree
@@ -112,7 +112,7 @@ def test_single_instance_forest_matches_oracle():
     assert tree.stats()["forest_level"] == 0
     plan = Plan(tree, kernel="dl", p=10, precision="mixed", src_nrm=d[2], trg_nrm=d[2])
     out = plan.matvec(torch.from_numpy(sig).to(DEV) * d[1]).cpu().numpy()
-    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 3e-6
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-6
 
 
 def test_graph_matvec_matches_direct_launches():

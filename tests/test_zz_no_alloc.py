@@ -56,6 +56,27 @@ def test_noalloc_matches_allocating_entry_point_twice():
     assert _rel(outs[1], -2.5 * outs[0]) < 1e-6
 
 
+def test_noalloc_on_a_fresh_plan_takes_no_device_memory():
+    """On a plan that has never run an allocating call: after one warm-up call (which may
+    load the library's module and so place the static array), further calls leave the
+    device's free memory unchanged, and each result matches kifmm_demag_phi2, which runs
+    only after all the no-alloc calls."""
+    plan, xyz, w = _plan_and_inputs(14)
+    omega = torch.full_like(w, 2 * math.pi)
+    phis = [(4 * math.pi * s * (xyz[2] - 0.2 * xyz[1])).contiguous() for s in (1.0, 0.5, -3.0)]
+    outs = [torch.full_like(p, float("nan")) for p in phis]
+    plan.demag_phi2_noalloc(phis[0], w, omega, outs[0])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (1, 2):
+        plan.demag_phi2_noalloc(phis[k], w, omega, outs[k])
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    for k in range(3):
+        assert torch.isfinite(outs[k]).all()
+        assert _rel(outs[k], plan.demag_phi2(phis[k], w, omega)) < 1e-6
+
+
 def test_noalloc_rejects_oversized_plans():
     from paper_1605_01715_gb300 import KifmmError
     plan, xyz, w = _plan_and_inputs(296)           # 1,051,392 points > 2^20
