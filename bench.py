@@ -207,7 +207,7 @@ def run_kifmm(args):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     from paper_1605_01715_gb300 import Plan, Tree
-    peaks = measure_peaks(local)
+    peaks = None if args.lean else measure_peaks(local)
     wl, m, xyz, w, nrm, q = make_inputs(args.workload, device)
     inst = wl.get("instances")
     p = args.p or wl["p"]
@@ -269,6 +269,11 @@ def run_kifmm(args):
     ms = float(ms_t.item())
     value = n * ws / (ms * 1e-3)
 
+    if args.lean:                                  # the timed matvecs only (profiling runs)
+        print(json.dumps({"metric": METRIC, "value": n * ws / (ms * 1e-3), "unit": "targets/s", "n_gpus": ws,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "config": {"workload": args.workload, "lean": True}}), flush=True)
+        return 0
     # end to end through the C ABI with host buffers (kifmm_fmm_matvec_host): q and f in
     # pinned host memory, read and written in input order by the matvec's first and last
     # kernels every step (over NVLink-C2C on the Grace host), graph-replayed like the
@@ -347,9 +352,10 @@ def run_kifmm(args):
 
 def run_serve(args):
     """Serving stream (Poisson arrivals, mixed polarization solves and demag
-    evaluations, 2k-500k unknowns): p50/p99 latency and throughput of the
-    continuous-batching server at each arrival rate, against serial FP64 solves of
-    the same requests.  One JSON line; value = throughput at the highest rate."""
+    evaluations, 2k-500k unknowns): p50/p99 latency and throughput of the batching
+    server (requests admitted together share a forest and its launches) at each
+    arrival rate, against serial FP64 solves of the same requests.  One JSON line;
+    value = throughput at the highest rate."""
     import torch
 
     from paper_1605_01715_gb300.serve import Request, Server, percentiles, serial_baseline
@@ -361,7 +367,8 @@ def run_serve(args):
     with ClockSampler(0) as clk:
         for k, rate in enumerate(rates):
             reqs = [Request(rid=i, **d) for i, d in enumerate(synth.serve_requests(n_req, rate, 5000 + k))]
-            server = Server(mem_budget=args.serve_mem_gb * (1 << 30), p=args.serve_p, precision=args.precision)
+            server = Server(mem_budget=args.serve_mem_gb * (1 << 30), p=args.serve_p, precision=args.precision,
+                            max_batch=args.serve_max_batch)
             recs, tot = server.run(reqs)
             lat = [r["latency"] for r in recs]
             p50, p99 = percentiles(lat)
@@ -370,7 +377,8 @@ def run_serve(args):
             sweep.append({"rate_req_s": rate, "requests": len(recs), "p50_ms": p50 * 1e3, "p99_ms": p99 * 1e3,
                           "throughput_req_s": len(recs) / tot["makespan_s"],
                           "unknowns_per_s": unknowns / tot["makespan_s"], "makespan_s": tot["makespan_s"],
-                          "peak_live": tot["peak_live"], "rounds": tot["rounds"],
+                          "peak_live": tot["peak_live"], "rounds": tot["rounds"], "batches": tot["batches"],
+                          "peak_batch": tot["peak_batch"], "setup_s": tot["setup_s"],
                           "polar_max_true_rel_residual": max((r["rel_res"] for r in polar), default=None),
                           "polar_failed": sum(1 for r in polar if r["status"] != 0)})
             print("serve rate %g: p50 %.1f ms p99 %.1f ms, %.1f req/s" % (rate, p50 * 1e3, p99 * 1e3,
@@ -386,7 +394,9 @@ def run_serve(args):
             "unit": "requests/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
             "ms_per_step": 1e3 / max(top["throughput_req_s"], 1e-9), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": "serve_stream", "sizes": "log-uniform 2k-500k", "p": args.serve_p,
+            "config": {"workload": "serve_stream", "sizes": "log-uniform 2k-500k",
+                       "p": args.serve_p if args.serve_p else {"polar": 11, "demag": 10},
+                       "max_batch": args.serve_max_batch,
                        "precision": args.precision, "mem_budget_gb": args.serve_mem_gb,
                        "kinds": "half polarization GMRES(50) tol 1e-6, half demag phi2"},
             "serve": sweep, "serial_fp64": serial, "clocks": clk.summary(),
@@ -621,8 +631,10 @@ def _kernel_sha():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _m2l_traffic(pairs):
-    """DRAM bytes per M2L launch from the committed ncu record, if it is for this kernel source."""
+def _m2l_traffic(pairs, ku, kd):
+    """DRAM bytes per M2L launch: the operator tables (343 offsets x Kd x Ku, FP16 hi
+    and lo, read once) plus the per-pair bytes of the committed ncu record, if that
+    record is for this kernel source."""
     path = os.path.join(ROOT, "profiles", "m2l_tc_traffic.json")
     try:
         with open(path) as f:
@@ -631,7 +643,7 @@ def _m2l_traffic(pairs):
         return None
     if rec.get("kernel_sha") != _kernel_sha():
         return None
-    return rec["dram_bytes_per_pair"] * pairs + rec["dram_bytes_fixed"]
+    return rec["dram_bytes_per_pair"] * pairs + 343 * kd * ku * 2 * 2
 
 
 def rooflines(phases, st, tst, args, kernel, peaks):
@@ -658,7 +670,8 @@ def rooflines(phases, st, tst, args, kernel, peaks):
                       "peak_source": "measured FP64 FMA rate (kifmm_peak_rate)"}
     out["m2l"].update({"achieved": flops / t / 1e12 if t > 0 else None, "peak": peak, "unit": "TFLOP/s",
                        "frac": flops / t / 1e12 / peak if t > 0 else None,
-                       "traffic": _m2l_traffic(pairs) if mixed else None, "ms": phases["m2l"],
+                       "traffic": _m2l_traffic(pairs, (ru + 15) // 16 * 16, (rd + 15) // 16 * 16) if mixed else None,
+                       "ms": phases["m2l"],
                        "work": "2*R*W flops x %d pairs, R=%d, W=%d" % (pairs, rd, ru)})
     # near field
     t = phases["p2p"] * 1e-3
@@ -711,13 +724,17 @@ def main():
     ap.add_argument("--serve-rates", default="10,100,1000")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-serial", type=int, default=8)
-    ap.add_argument("--serve-p", type=int, default=10)
+    ap.add_argument("--serve-p", type=int, default=None,
+                    help="one order for both kinds (default: ADL p = 11, DL p = 10)")
+    ap.add_argument("--serve-max-batch", type=int, default=64, help="requests per batch (1: no shared launches)")
     ap.add_argument("--serve-mem-gb", type=float, default=96.0)
     ap.add_argument("--solves", type=int, default=5, help="timed polarization solves (0: skip)")
     ap.add_argument("--no-fp64-plain", dest="fp64_plain", action="store_false",
                     help="skip timing the FP64 plain form of the same matvec")
     ap.add_argument("--no-field-check", dest="field_check", action="store_false",
                     help="skip the interior demagnetizing field of the 1M sphere")
+    ap.add_argument("--lean", action="store_true",
+                    help="set-up, warm-up and the timed matvecs only, then a short line (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -344,9 +344,16 @@ int kifmm_polarization_rhs(const double* nrm, const double* eps_in, double eps_o
  * Gram-Schmidt applied twice) and residuals are FP64 on the device; x0 is the
  * content of x on entry.  Stops when the GMRES residual estimate falls to
  * tol * ||b|| and returns the true relative residual ||b - A x||/||b|| in *rel_res.
+ * On a forest (kifmm_forest_build) every instance is solved by its own GMRES -- its
+ * own Krylov coefficients, residual and stopping test on its segment of the vectors --
+ * and all instances share each step's matvec (one launch per phase for all of
+ * them); an instance that has stopped takes zero basis vectors until the others
+ * stop.  *iters is then the number of shared steps and *rel_res the largest
+ * instance's true residual; kifmm_solver_instances gives them per instance.
  *   area, eps_in, curv, b: device, n FP64 (input order);  x device n (in/out).
  *   iters, rel_res: host (may be NULL).
- * Errors: INVALID_ARG, OOM, CUDA, NOT_CONVERGED (x = last iterate), BREAKDOWN.
+ * Errors: INVALID_ARG, OOM, CUDA, NOT_CONVERGED (x = last iterate), BREAKDOWN (on a
+ * forest: the first failing instance's status).
  */
 int kifmm_bie_solve(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
                     const double* curv, const double* b, double* x,
@@ -380,6 +387,18 @@ int kifmm_solver_create(kifmm_plan plan, const double* area, const double* eps_i
 int kifmm_solver_launch(kifmm_solver solver, void* stream);
 int kifmm_solver_finish(kifmm_solver solver, int* done, int* iters, double* rel_res);
 int kifmm_solver_destroy(kifmm_solver solver);
+
+/*
+ * Per-instance state of a solver on a forest (on one tree: n_inst = 1).
+ *   n_inst  the tree's instance count (kifmm_tree_get_stats n_instances).
+ *   iters   host, n_inst: the shared step at which each instance last advanced.
+ *   rel_res host, n_inst: the GMRES residual estimate, or after the end the true
+ *           relative residual ||b_i - A_i x_i|| / ||b_i||.
+ *   status  host, n_inst: OK while running; after the end OK, NOT_CONVERGED or BREAKDOWN.
+ * Any array may be NULL.  Errors: INVALID_ARG (NULL solver, n_inst mismatch).
+ */
+int kifmm_solver_instances(kifmm_solver solver, int n_inst, int32_t* iters, double* rel_res,
+                           int32_t* status);
 
 /*
  * The polarization operator itself, y = A x (same definition as kifmm_bie_solve).

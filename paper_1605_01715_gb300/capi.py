@@ -98,6 +98,7 @@ _SIGS = {
     "kifmm_solver_finish": ([_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "kifmm_solver_destroy": ([_P], ctypes.c_int),
+    "kifmm_solver_instances": ([_P, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "kifmm_bie_solve": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_double, ctypes.c_int,
                          ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "kifmm_bie_apply": ([_P, _P, _P, ctypes.c_double, _P, _P, _P, _P], ctypes.c_int),
@@ -450,7 +451,17 @@ class Solver:
                                          ctypes.byref(h)))
         self.handle = h
         self._lib = lib()
+        self.n_inst = plan.tree.stats()["n_instances"]
         self.done, self.iters, self.rel_res, self.status = False, 0, float("inf"), 0
+
+    def instances(self):
+        """Per-instance (iters, rel_res, status) arrays (kifmm_solver_instances)."""
+        it = np.zeros(self.n_inst, np.int32)
+        rr = np.zeros(self.n_inst, np.float64)
+        stt = np.zeros(self.n_inst, np.int32)
+        _check(lib().kifmm_solver_instances(self.handle, self.n_inst, it.ctypes.data, rr.ctypes.data,
+                                            stt.ctypes.data))
+        return it, rr, stt
 
     def launch(self, stream=None):
         _check(lib().kifmm_solver_launch(self.handle, _stream(stream)))

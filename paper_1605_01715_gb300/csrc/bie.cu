@@ -120,16 +120,23 @@ __global__ void k_rhs(const double* __restrict__ nrm, const double* __restrict__
     b[i] = -(eps_out - eps_in[i]) * (ex * nrm[i] + ey * nrm[n + i] + ez * nrm[2 * n + i]);
 }
 
-// partial[blk * nv + i] = sum over this block's stride of V[i] . w  (i < nv)
-constexpr int kDotBlocks = 304;
+// Reductions and updates of the GMRES vectors, per instance.  A forest's vectors hold
+// its instances back to back (input order); every instance runs its own GMRES, so every
+// dot product, combination and scaling acts on one instance's segment with that
+// instance's coefficients.  A plan on one tree is the case of one instance.
+//
+// Dot products: block b sums V_j . w over the range [lo_b, hi_b) of one instance
+// (ranges never straddle two instances) into partial[b nv + j]; the final pass adds the
+// blocks of instance i into h[i hld + j].
 __global__ void k_dots(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w,
-                       int64_t n, double* __restrict__ partial) {
+                       const int64_t* __restrict__ blo, const int64_t* __restrict__ bhi,
+                       double* __restrict__ partial) {
     __shared__ double red[256];
+    const int64_t lo = blo[blockIdx.x], hi = bhi[blockIdx.x];
     for (int i = 0; i < nv; ++i) {
         const double* v = V + (size_t)i * ld;
         double s = 0;
-        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-            s += v[t] * w[t];
+        for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) s += v[t] * w[t];
         red[threadIdx.x] = s;
         __syncthreads();
         for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -141,34 +148,57 @@ __global__ void k_dots(const double* __restrict__ V, int64_t ld, int nv, const d
     }
 }
 
-__global__ void k_dots_final(const double* __restrict__ partial, int nblk, int nv, double* __restrict__ h) {
-    int i = blockIdx.x;
-    __shared__ double red[256];
+// grid (nv, n_inst): h[i hld + j] = sum of partial[b nv + j] over the blocks of instance i
+__global__ void k_dots_final(const double* __restrict__ partial, const int* __restrict__ inst_blk, int nv,
+                             int hld, double* __restrict__ h) {
+    const int j = blockIdx.x, i = blockIdx.y;
+    __shared__ double red[128];
     double s = 0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(size_t)b * nv + i];
+    for (int b = inst_blk[i] + threadIdx.x; b < inst_blk[i + 1]; b += blockDim.x) s += partial[(size_t)b * nv + j];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) h[i] = red[0];
+    if (threadIdx.x == 0) h[(size_t)i * hld + j] = red[0];
 }
 
-// w -= sum_i h[i] V[i]   (sign = -1)   or   x += sum_i h[i] V[i]   (sign = +1)
-__global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ h,
-                          double sign, int64_t n, double* __restrict__ w) {
+// w += sign sum_j h[inst(t) hld + j] V_j   (inst = 0 without a point-to-instance map)
+__global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ h, int hld,
+                          double sign, int64_t n, const int* __restrict__ inst, double* __restrict__ w) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
+    const double* hi = h + (size_t)(inst ? inst[t] : 0) * hld;
     double s = 0;
-    for (int i = 0; i < nv; ++i) s += h[i] * V[(size_t)i * ld + t];
+    for (int i = 0; i < nv; ++i) s += hi[i] * V[(size_t)i * ld + t];
     w[t] += sign * s;
+}
+
+// out = a[inst(t)] x   (out may be x)
+__global__ void k_scale(const double* __restrict__ a, const double* x, int64_t n, const int* __restrict__ inst,
+                        double* out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) out[t] = a[inst ? inst[t] : 0] * x[t];
 }
 
 __global__ void k_axpby(double a, const double* __restrict__ x, double b, const double* __restrict__ y, int64_t n,
                         double* __restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+// inst[t] = i for off[i] <= t < off[i + 1]
+__global__ void k_point_instance(const int64_t* __restrict__ off, int ninst, int64_t n, int* __restrict__ inst) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int lo = 0, hi = ninst;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (off[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    inst[t] = lo;
 }
 
 struct Gmres {
@@ -178,21 +208,12 @@ struct Gmres {
     int64_t n;
     cudaStream_t s;
     double* qbuf;
-    DBuf<double> partial, hdev;
 
     int apply(const double* x, double* y) {
         k_mul<<<div_up(n, 256), 256, 0, s>>>(x, area, n, qbuf);
         KF_CHECK_LAUNCH();
         KF_TRY(plan_matvec(P, qbuf, y, s));
         k_polar_combine<<<div_up(n, 256), 256, 0, s>>>(x, area, eps_in, eps_out, curv, n, y);
-        KF_CHECK_LAUNCH();
-        return KIFMM_OK;
-    }
-    // h (device, nv) = V[0..nv)^T w
-    int dots(const double* V, int64_t ld, int nv, const double* w, double* h) {
-        k_dots<<<kDotBlocks, 256, 0, s>>>(V, ld, nv, w, n, partial.p);
-        KF_CHECK_LAUNCH();
-        k_dots_final<<<nv, 256, 0, s>>>(partial.p, kDotBlocks, nv, h);
         KF_CHECK_LAUNCH();
         return KIFMM_OK;
     }
@@ -326,43 +347,78 @@ extern "C" int kifmm_demag_phi2_noalloc(kifmm_plan plan, const double* phi1, con
 // Arnoldi step (A v_k, CGS2, ||w||); the final true residual.  Device work that needs a
 // host result (v_0 = r / beta, v_{k+1} = w / h_{k+1,k}, x += V y) is carried into the
 // next launch.
+//
+// On a forest every instance runs its own GMRES: its own Hessenberg matrix, rotations,
+// residual and convergence test, on its own segment of the vectors.  All instances
+// share the steps (one matvec of the forest per step).  An instance leaves the cycle
+// when it has converged, when its Krylov space is exhausted (h_{k+1,k} = 0: it waits
+// for the next restart) or on breakdown; its new basis vectors are then zero, so the
+// matvec, the dots and the updates leave it unchanged.  A cycle ends when no instance
+// is left in it or after m steps.
 namespace kifmm {
 
 struct Solver {
+    enum Inst { kRun, kWait, kConv, kFail };
     Plan& P;
     const double *area, *eps_in, *curv, *b;
     double* x;
     double eps_out, tol;
     int m, max_iter;
     int64_t n;
-    // device: Krylov basis (m+1) x n, w, r, the area-weighted operand, dot partials, h
+    int ni;                                 // instances (1 unless the tree is a forest)
+    int hld;                                // leading dimension of the per-instance h rows: m + 2
+    // device: Krylov basis (m+1) x n, w, r, the area-weighted operand, dot partials and
+    // block ranges, per-instance h rows, the point-to-instance map (forests only)
     double *V = nullptr, *w = nullptr, *r = nullptr, *q = nullptr;
     DBuf<double> own_V, own_w, own_r, own_q;
+    DBuf<double> partial, hdev;
+    DBuf<int64_t> blo, bhi;
+    DBuf<int> inst_blk, pinst;
+    int nblk = 0;
     Gmres g;
-    double* hpin = nullptr;                 // pinned host copies: ha (m+2), hb (m+2), scalar
+    double* hpin = nullptr;                 // pinned: ha, hb, y (ni hld each), scales (ni)
     enum Step { kNormB, kRestart, kArnoldi, kFinal, kDone } step = kNormB;
     // pending device work for the next launch
-    double scale_v0 = 0, scale_next = 0;
+    int pend_scale = 0;                     // 1: V_0 *= scal, 2: V_k = scal w, 3: x *= scal
     int pend_x = 0;                         // x += V[0..pend_x) y
     bool zero_x = false;
-    // host state
-    std::vector<double> H, cs, sn, gv, y;
-    double bnorm = 0, rel = INFINITY, true_rel = 0;
+    // host state, per instance
+    std::vector<double> H, cs, sn, gv, bnorm, rel, true_rel;
+    std::vector<int> state, iters, status;
+    double rel_max = INFINITY, true_max = 0;
     int it = 0, k = 0;
-    int status = KIFMM_OK;                  // final status once step == kDone
+    int status_all = KIFMM_OK;              // first failing instance's status once step == kDone
     cudaStream_t last = nullptr;
 
     Solver(Plan& P_, const double* area_, const double* eps_in_, const double* curv_, double eps_out_,
            const double* b_, double* x_, double tol_, int m_, int max_iter_)
         : P(P_), area(area_), eps_in(eps_in_), curv(curv_), b(b_), x(x_), eps_out(eps_out_), tol(tol_),
-          m(m_), max_iter(max_iter_), n(P_.tree->t.nt), g{P_, area_, eps_in_, curv_, eps_out_, P_.tree->t.nt,
-                                                            nullptr, nullptr, {}, {}} {}
+          m(m_), max_iter(max_iter_), n(P_.tree->t.nt), ni(1), hld(m_ + 2),
+          g{P_, area_, eps_in_, curv_, eps_out_, P_.tree->t.nt, nullptr, nullptr} {
+        const Tree& T = P_.tree->t;
+        if (T.forest_level >= 0 && T.inst_off.size() >= 2) ni = (int)T.inst_off.size() - 1;
+    }
     ~Solver() {
         if (hpin) cudaFreeHost(hpin);
     }
 
+    double* ha() { return hpin; }
+    double* hb() { return hpin + (size_t)ni * hld; }
+    double* hyv() { return hpin + 2 * (size_t)ni * hld; }
+    double* hscal() { return hpin + 3 * (size_t)ni * hld; }
+    double* dA() { return hdev.p; }
+    double* dB() { return hdev.p + (size_t)ni * hld; }
+    double* dY() { return hdev.p + 2 * (size_t)ni * hld; }
+    double* dS() { return hdev.p + 3 * (size_t)ni * hld; }
+    double& Hx(int i, int row, int col) { return H[((size_t)i * (m + 1) + row) * m + col]; }
+
     // own = false: use the plan's resident scratch (one solve at a time on that plan)
     int init(bool own) {
+        const size_t state_doubles = (size_t)ni * ((size_t)(m + 1) * m + 3 * (size_t)m + 8);
+        if (state_doubles > ((size_t)1 << 27)) {
+            set_error("invalid argument: GMRES(%d) state of %d instances exceeds 1 GiB of host memory", m, ni);
+            return KIFMM_ERR_INVALID_ARG;
+        }
         if (own) {
             KF_TRY(own_V.alloc((size_t)(m + 1) * n));
             KF_TRY(own_w.alloc(n));
@@ -378,20 +434,66 @@ struct Solver {
             V = S.krylov.p, w = S.w.p, r = S.r.p, q = S.q.p;
         }
         g.qbuf = q;
-        KF_TRY(g.partial.alloc((size_t)kDotBlocks * (m + 1)));
-        KF_TRY(g.hdev.alloc(3 * (size_t)(m + 2)));
-        KF_CHECK_CUDA(cudaMallocHost(&hpin, (2 * (size_t)(m + 2) + 1) * sizeof(double)));
-        H.assign((size_t)(m + 1) * m, 0.0);
-        cs.assign(m, 0.0);
-        sn.assign(m, 0.0);
-        gv.assign(m + 1, 0.0);
-        y.assign(m, 0.0);
+        // dot-product blocks: chunks of at least 2048 points (about 600 blocks on large
+        // vectors), never across an instance boundary
+        std::vector<int64_t> off(ni + 1);
+        if (ni > 1) off = P.tree->t.inst_off;
+        else off[0] = 0, off[1] = n;
+        const int64_t chunk = std::max<int64_t>(2048, div_up(n, 600));
+        std::vector<int64_t> lo, hi;
+        std::vector<int> ib(ni + 1, 0);
+        for (int i = 0; i < ni; ++i) {
+            ib[i] = (int)lo.size();
+            for (int64_t a = off[i]; a < off[i + 1]; a += chunk) {
+                lo.push_back(a);
+                hi.push_back(std::min(off[i + 1], a + chunk));
+            }
+            if (off[i + 1] == off[i]) lo.push_back(off[i]), hi.push_back(off[i]);   // an empty plan
+        }
+        ib[ni] = (int)lo.size();
+        nblk = (int)lo.size();
+        KF_TRY(blo.alloc(nblk));
+        KF_TRY(bhi.alloc(nblk));
+        KF_TRY(inst_blk.alloc(ni + 1));
+        KF_CHECK_CUDA(cudaMemcpy(blo.p, lo.data(), nblk * sizeof(int64_t), cudaMemcpyHostToDevice));
+        KF_CHECK_CUDA(cudaMemcpy(bhi.p, hi.data(), nblk * sizeof(int64_t), cudaMemcpyHostToDevice));
+        KF_CHECK_CUDA(cudaMemcpy(inst_blk.p, ib.data(), (ni + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        if (ni > 1) {
+            DBuf<int64_t> doff;
+            KF_TRY(doff.alloc(ni + 1));
+            KF_CHECK_CUDA(cudaMemcpy(doff.p, off.data(), (ni + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+            KF_TRY(pinst.alloc(n));
+            k_point_instance<<<div_up(n, 256), 256>>>(doff.p, ni, n, pinst.p);
+            KF_CHECK_LAUNCH();
+            KF_CHECK_CUDA(cudaDeviceSynchronize());
+        }
+        KF_TRY(partial.alloc((size_t)nblk * (m + 1)));
+        KF_TRY(hdev.alloc(3 * (size_t)ni * hld + ni));
+        KF_CHECK_CUDA(cudaMallocHost(&hpin, (3 * (size_t)ni * hld + ni) * sizeof(double)));
+        std::fill(hpin, hpin + 3 * (size_t)ni * hld + ni, 0.0);
+        H.assign((size_t)ni * (m + 1) * m, 0.0);
+        cs.assign((size_t)ni * m, 0.0);
+        sn.assign((size_t)ni * m, 0.0);
+        gv.assign((size_t)ni * (m + 1), 0.0);
+        bnorm.assign(ni, 0.0);
+        rel.assign(ni, INFINITY);
+        true_rel.assign(ni, 0.0);
+        state.assign(ni, kRun);
+        iters.assign(ni, 0);
+        status.assign(ni, KIFMM_OK);
         return KIFMM_OK;
     }
 
-    double* hA() { return g.hdev.p; }
-    double* hB() { return g.hdev.p + (m + 2); }
-    double* hy() { return g.hdev.p + 2 * (m + 2); }
+    const int* inst() const { return ni > 1 ? pinst.p : nullptr; }
+
+    // h (device, row i at i hld_h) = V[0..nv)^T w per instance
+    int dots(const double* Vp, int64_t ld, int nv, const double* wp, double* h, int hld_h, cudaStream_t s) {
+        k_dots<<<nblk, 256, 0, s>>>(Vp, ld, nv, wp, blo.p, bhi.p, partial.p);
+        KF_CHECK_LAUNCH();
+        k_dots_final<<<dim3(nv, ni), 128, 0, s>>>(partial.p, inst_blk.p, nv, hld_h, h);
+        KF_CHECK_LAUNCH();
+        return KIFMM_OK;
+    }
 
     int flush_pending(cudaStream_t s) {
         if (zero_x) {
@@ -399,21 +501,20 @@ struct Solver {
             zero_x = false;
         }
         if (pend_x > 0) {
-            // y was written to the pinned buffer by finish(); copy and update x
-            KF_CHECK_CUDA(cudaMemcpyAsync(hy(), hpin, pend_x * sizeof(double), cudaMemcpyHostToDevice, s));
-            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, pend_x, hy(), 1.0, n, x);
+            // y rows were written to the pinned buffer by finish(); copy and update x
+            KF_CHECK_CUDA(cudaMemcpyAsync(dY(), hyv(), (size_t)ni * hld * sizeof(double), cudaMemcpyHostToDevice,
+                                          s));
+            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, pend_x, dY(), hld, 1.0, n, inst(), x);
             KF_CHECK_LAUNCH();
             pend_x = 0;
         }
-        if (scale_v0 != 0) {
-            k_axpby<<<div_up(n, 256), 256, 0, s>>>(scale_v0, V, 0.0, V, n, V);
+        if (pend_scale) {
+            KF_CHECK_CUDA(cudaMemcpyAsync(dS(), hscal(), ni * sizeof(double), cudaMemcpyHostToDevice, s));
+            if (pend_scale == 1) k_scale<<<div_up(n, 256), 256, 0, s>>>(dS(), V, n, inst(), V);
+            else if (pend_scale == 2) k_scale<<<div_up(n, 256), 256, 0, s>>>(dS(), w, n, inst(), V + (size_t)k * n);
+            else k_scale<<<div_up(n, 256), 256, 0, s>>>(dS(), x, n, inst(), x);
             KF_CHECK_LAUNCH();
-            scale_v0 = 0;
-        }
-        if (scale_next != 0) {
-            k_axpby<<<div_up(n, 256), 256, 0, s>>>(scale_next, w, 0.0, w, n, V + (size_t)k * n);
-            KF_CHECK_LAUNCH();
-            scale_next = 0;
+            pend_scale = 0;
         }
         return KIFMM_OK;
     }
@@ -424,120 +525,201 @@ struct Solver {
         last = s;
         KF_TRY(flush_pending(s));
         if (step == kNormB) {
-            KF_TRY(g.dots(b, 0, 1, b, hA()));
-            KF_CHECK_CUDA(cudaMemcpyAsync(hpin, hA(), sizeof(double), cudaMemcpyDeviceToHost, s));
+            KF_TRY(dots(b, 0, 1, b, dA(), 1, s));
+            KF_CHECK_CUDA(cudaMemcpyAsync(ha(), dA(), ni * sizeof(double), cudaMemcpyDeviceToHost, s));
         } else if (step == kRestart || step == kFinal) {
             // r = b - A x (restart: into v_0)
             KF_TRY(g.apply(x, r));
             double* dst = step == kRestart ? V : r;
             k_axpby<<<div_up(n, 256), 256, 0, s>>>(1.0, b, -1.0, r, n, dst);
             KF_CHECK_LAUNCH();
-            KF_TRY(g.dots(dst, 0, 1, dst, hA()));
-            KF_CHECK_CUDA(cudaMemcpyAsync(hpin, hA(), sizeof(double), cudaMemcpyDeviceToHost, s));
+            KF_TRY(dots(dst, 0, 1, dst, dA(), 1, s));
+            KF_CHECK_CUDA(cudaMemcpyAsync(ha(), dA(), ni * sizeof(double), cudaMemcpyDeviceToHost, s));
         } else {  // kArnoldi: w = A v_k, two Gram-Schmidt passes against v_0..v_k, ||w||^2
             KF_TRY(g.apply(V + (size_t)k * n, w));
-            KF_TRY(g.dots(V, n, k + 1, w, hA()));
-            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, k + 1, hA(), -1.0, n, w);
+            KF_TRY(dots(V, n, k + 1, w, dA(), hld, s));
+            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, k + 1, dA(), hld, -1.0, n, inst(), w);
             KF_CHECK_LAUNCH();
-            KF_TRY(g.dots(V, n, k + 1, w, hB()));
-            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, k + 1, hB(), -1.0, n, w);
+            KF_TRY(dots(V, n, k + 1, w, dB(), hld, s));
+            k_combine<<<div_up(n, 256), 256, 0, s>>>(V, n, k + 1, dB(), hld, -1.0, n, inst(), w);
             KF_CHECK_LAUNCH();
-            KF_TRY(g.dots(w, 0, 1, w, hB() + (m + 1)));
-            KF_CHECK_CUDA(cudaMemcpyAsync(hpin, hA(), (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            KF_CHECK_CUDA(cudaMemcpyAsync(hpin + (m + 2), hB(), (m + 2) * sizeof(double),
-                                          cudaMemcpyDeviceToHost, s));
+            KF_TRY(dots(w, 0, 1, w, dB() + (m + 1), hld, s));
+            KF_CHECK_CUDA(cudaMemcpyAsync(ha(), dA(), 2 * (size_t)ni * hld * sizeof(double), cudaMemcpyDeviceToHost,
+                                          s));
         }
         return KIFMM_OK;
     }
 
-    // End of a cycle: back substitution, then x += V y at the next launch.
-    void end_cycle(int kdone) {
-        for (int i = kdone - 1; i >= 0; --i) {
-            double acc = gv[i];
-            for (int j = i + 1; j < kdone; ++j) acc -= H[(size_t)i * m + j] * y[j];
-            y[i] = acc / H[(size_t)i * m + i];
+    // Instance i leaves the cycle after kdone steps: back substitution into its y row;
+    // x += V y runs at the next launch.
+    void end_cycle(int i, int kdone) {
+        double* y = hyv() + (size_t)i * hld;
+        const double* g_i = &gv[(size_t)i * (m + 1)];
+        for (int a = kdone - 1; a >= 0; --a) {
+            double acc = g_i[a];
+            for (int c = a + 1; c < kdone; ++c) acc -= Hx(i, a, c) * y[c];
+            y[a] = acc / Hx(i, a, a);
         }
-        for (int i = 0; i < kdone; ++i) hpin[i] = y[i];   // read by the next launch's copy
-        pend_x = kdone;
+        pend_x = std::max(pend_x, kdone);
+    }
+
+    void update_rel_max() {
+        rel_max = 0;
+        for (int i = 0; i < ni; ++i)
+            if (state[i] == kRun || state[i] == kWait) rel_max = std::max(rel_max, rel[i]);
+    }
+
+    void fail(int i, int code) {
+        state[i] = kFail;
+        status[i] = code;
     }
 
     int finish() {
         if (step == kDone) return KIFMM_OK;
         KF_CHECK_CUDA(cudaStreamSynchronize(last));
+        const double* h0 = ha();
         if (step == kNormB) {
-            bnorm = std::sqrt(hpin[0]);
-            if (!(bnorm > 0)) {
+            bool any = false;
+            for (int i = 0; i < ni; ++i) {
+                bnorm[i] = std::sqrt(h0[i]);
+                if (bnorm[i] > 0) any = true;
+                else state[i] = kConv, rel[i] = 0;    // x_i = 0 is exact
+            }
+            if (!any) {
                 zero_x = true;
-                rel = true_rel = 0;
+                rel_max = 0;
                 step = kFinal;              // x = 0; the final residual is then exactly 0
                 return KIFMM_OK;
             }
+            if (ni > 1) {
+                // x_i = 0 for the instances with b_i = 0 (their exact solution), by a
+                // scaling of x with 0 there and 1 elsewhere
+                bool zero_any = false;
+                for (int i = 0; i < ni; ++i) {
+                    hscal()[i] = bnorm[i] > 0 ? 1.0 : 0.0;
+                    zero_any |= !(bnorm[i] > 0);
+                }
+                if (zero_any) pend_scale = 3;
+            }
             step = kRestart;
+            update_rel_max();
             return KIFMM_OK;
         }
         if (step == kFinal) {
-            true_rel = bnorm > 0 ? std::sqrt(hpin[0]) / bnorm : 0.0;
-            if (status == KIFMM_OK && !(rel <= tol)) {
-                set_error("GMRES did not converge in %d iterations (residual estimate %.3e)", it, rel);
-                status = KIFMM_ERR_NOT_CONVERGED;
+            true_max = 0;
+            status_all = KIFMM_OK;
+            for (int i = 0; i < ni; ++i) {
+                true_rel[i] = bnorm[i] > 0 ? std::sqrt(h0[i]) / bnorm[i] : 0.0;
+                true_max = std::max(true_max, true_rel[i]);
+                if (status[i] == KIFMM_OK && !(rel[i] <= tol)) status[i] = KIFMM_ERR_NOT_CONVERGED;
+                if (status_all == KIFMM_OK && status[i] != KIFMM_OK) status_all = status[i];
             }
+            if (status_all == KIFMM_ERR_NOT_CONVERGED)
+                set_error("GMRES did not converge in %d iterations (residual estimate %.3e)", it, rel_max);
+            else if (status_all == KIFMM_ERR_BREAKDOWN)
+                set_error("GMRES breakdown after %d iterations", it);
             step = kDone;
             return KIFMM_OK;
         }
         if (step == kRestart) {
-            const double beta = std::sqrt(hpin[0]);
-            rel = beta / bnorm;
-            if (!std::isfinite(beta)) return breakdown();
-            if (rel <= tol || it >= max_iter) {
+            bool any = false;
+            for (int i = 0; i < ni; ++i) {
+                double* sc = hscal() + i;
+                *sc = 0.0;
+                if (state[i] != kRun && state[i] != kWait) continue;
+                const double beta = std::sqrt(h0[i]);
+                rel[i] = beta / bnorm[i];
+                if (!std::isfinite(beta)) {
+                    fail(i, KIFMM_ERR_BREAKDOWN);
+                    continue;
+                }
+                if (rel[i] <= tol) {
+                    state[i] = kConv;
+                    continue;
+                }
+                state[i] = kRun;
+                *sc = 1.0 / beta;
+                double* g_i = &gv[(size_t)i * (m + 1)];
+                std::fill(g_i, g_i + m + 1, 0.0);
+                g_i[0] = beta;
+                any = true;
+            }
+            update_rel_max();
+            if (!any || it >= max_iter) {
                 step = kFinal;
                 return KIFMM_OK;
             }
-            scale_v0 = 1.0 / beta;
-            std::fill(gv.begin(), gv.end(), 0.0);
-            gv[0] = beta;
+            pend_scale = 1;
             k = 0;
             step = kArnoldi;
             return KIFMM_OK;
         }
-        // kArnoldi: column k of H, the previous rotations, a new rotation
-        const double* ha = hpin;
-        const double* hb = hpin + (m + 2);
-        for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = ha[i] + hb[i];
-        const double hk1 = std::sqrt(hb[m + 1]);
-        H[(size_t)(k + 1) * m + k] = hk1;
-        if (!std::isfinite(hk1)) return breakdown();
-        for (int i = 0; i < k; ++i) {
-            const double a0 = H[(size_t)i * m + k], a1 = H[(size_t)(i + 1) * m + k];
-            H[(size_t)i * m + k] = cs[i] * a0 + sn[i] * a1;
-            H[(size_t)(i + 1) * m + k] = -sn[i] * a0 + cs[i] * a1;
-        }
-        const double a0 = H[(size_t)k * m + k], a1 = H[(size_t)(k + 1) * m + k];
-        const double den = std::hypot(a0, a1);
-        if (!(den > 0)) return breakdown();
-        cs[k] = a0 / den;
-        sn[k] = a1 / den;
-        H[(size_t)k * m + k] = den;
-        H[(size_t)(k + 1) * m + k] = 0;
-        gv[k + 1] = -sn[k] * gv[k];
-        gv[k] = cs[k] * gv[k];
+        // kArnoldi: per instance in the cycle, column k of H, the previous rotations, a
+        // new rotation
+        const double* hA_ = ha();
+        const double* hB_ = hb();
         ++it;
-        rel = std::fabs(gv[k + 1]) / bnorm;
-        if (rel <= tol || hk1 == 0 || k + 1 == m || it >= max_iter) {
-            end_cycle(k + 1);
-            step = (rel <= tol || it >= max_iter) ? kFinal : kRestart;
+        std::fill(hyv(), hyv() + (size_t)ni * hld, 0.0);
+        bool left = false;
+        const bool last_step = k + 1 == m || it >= max_iter;
+        for (int i = 0; i < ni; ++i) {
+            double* sc = hscal() + i;
+            *sc = 0.0;
+            if (state[i] != kRun) continue;
+            const double* a_ = hA_ + (size_t)i * hld;
+            const double* b_ = hB_ + (size_t)i * hld;
+            for (int a = 0; a <= k; ++a) Hx(i, a, k) = a_[a] + b_[a];
+            const double hk1 = std::sqrt(b_[m + 1]);
+            Hx(i, k + 1, k) = hk1;
+            if (!std::isfinite(hk1)) {
+                fail(i, KIFMM_ERR_BREAKDOWN);
+                continue;
+            }
+            double* cs_i = &cs[(size_t)i * m];
+            double* sn_i = &sn[(size_t)i * m];
+            double* g_i = &gv[(size_t)i * (m + 1)];
+            for (int a = 0; a < k; ++a) {
+                const double a0 = Hx(i, a, k), a1 = Hx(i, a + 1, k);
+                Hx(i, a, k) = cs_i[a] * a0 + sn_i[a] * a1;
+                Hx(i, a + 1, k) = -sn_i[a] * a0 + cs_i[a] * a1;
+            }
+            const double a0 = Hx(i, k, k), a1 = Hx(i, k + 1, k);
+            const double den = std::hypot(a0, a1);
+            if (!(den > 0)) {
+                fail(i, KIFMM_ERR_BREAKDOWN);
+                continue;
+            }
+            cs_i[k] = a0 / den;
+            sn_i[k] = a1 / den;
+            Hx(i, k, k) = den;
+            Hx(i, k + 1, k) = 0;
+            g_i[k + 1] = -sn_i[k] * g_i[k];
+            g_i[k] = cs_i[k] * g_i[k];
+            iters[i] = it;
+            rel[i] = std::fabs(g_i[k + 1]) / bnorm[i];
+            if (rel[i] <= tol) {
+                end_cycle(i, k + 1);
+                state[i] = kConv;
+            } else if (hk1 == 0 || last_step) {
+                end_cycle(i, k + 1);
+                state[i] = kWait;           // Krylov space exhausted or cycle over: restart
+            } else {
+                *sc = 1.0 / hk1;            // v_{k+1} = w / h_{k+1,k}
+                left = true;
+            }
+        }
+        update_rel_max();
+        if (left) {
+            pend_scale = 2;
+            ++k;
             return KIFMM_OK;
         }
-        if (hk1 > 0) scale_next = 1.0 / hk1;   // v_{k+1} = w / h_{k+1,k}
-        ++k;
+        bool waiting = false;
+        for (int i = 0; i < ni; ++i) waiting |= state[i] == kWait;
+        step = waiting && it < max_iter ? kRestart : kFinal;
         return KIFMM_OK;
     }
 
-    int breakdown() {
-        set_error("GMRES breakdown after %d iterations", it);
-        status = KIFMM_ERR_BREAKDOWN;
-        step = kFinal;
-        return KIFMM_OK;
-    }
 };
 
 }  // namespace kifmm
@@ -571,8 +753,8 @@ extern "C" int kifmm_bie_solve(kifmm_plan plan, const double* area, const double
         KF_TRY(S.finish());
     }
     if (iters) *iters = S.it;
-    if (rel_res) *rel_res = S.true_rel;
-    return S.status;
+    if (rel_res) *rel_res = S.true_max;
+    return S.status_all;
 }
 
 extern "C" int kifmm_solver_create(kifmm_plan plan, const double* area, const double* eps_in, double eps_out,
@@ -610,8 +792,23 @@ extern "C" int kifmm_solver_finish(kifmm_solver solver, int* done, int* iters, d
     const Solver& S = solver->S;
     if (done) *done = S.step == Solver::kDone;
     if (iters) *iters = S.it;
-    if (rel_res) *rel_res = S.step == Solver::kDone ? S.true_rel : S.rel;
-    return S.step == Solver::kDone ? S.status : KIFMM_OK;
+    if (rel_res) *rel_res = S.step == Solver::kDone ? S.true_max : S.rel_max;
+    return S.step == Solver::kDone ? S.status_all : KIFMM_OK;
+}
+
+extern "C" int kifmm_solver_instances(kifmm_solver solver, int n_inst, int32_t* iters, double* rel_res,
+                                      int32_t* status) {
+    clear_error();
+    KF_ARG(solver != nullptr, "NULL solver");
+    const Solver& S = solver->S;
+    KF_ARG(n_inst == S.ni, "n_inst must be the tree's instance count");
+    const bool done = S.step == Solver::kDone;
+    for (int i = 0; i < S.ni; ++i) {
+        if (iters) iters[i] = S.iters[i];
+        if (rel_res) rel_res[i] = done ? S.true_rel[i] : S.rel[i];
+        if (status) status[i] = done ? S.status[i] : KIFMM_OK;
+    }
+    return KIFMM_OK;
 }
 
 extern "C" int kifmm_solver_destroy(kifmm_solver solver) {

@@ -1,19 +1,27 @@
-"""Serving loop: a stream of solve requests on one GPU with continuous batching.
+"""Serving loop: a stream of solve requests on one GPU, batched into shared launches.
 
 Host scheduler over the C ABI (no arithmetic of the method here).  Requests arrive on
 a wall clock; each is
 
-* ``polar`` -- a dielectric polarization solve (Sec. II.C): GMRES on the ADL operator
-  (``kifmm_solver_*``), one matvec per step; or
+* ``polar`` -- a dielectric polarization solve (Sec. II.C): GMRES on the ADL operator,
+  one matvec per step; or
 * ``demag`` -- the demagnetizing boundary potential phi2 of the Fredkin-Koehler split
   (Sec. II.B, Eq. fk_integral_discrete), one DL matvec.
 
-A request is admitted when the device-memory estimate of its tree, plan and Krylov
-basis fits the budget; its tree, plan and solver state then stay on the device until
-it completes.  Every round launches the next step of every live request, each on its
-own CUDA stream, and only then waits for them, so the matvecs of all live solves
-overlap on the GPU; completed requests leave and waiting ones are admitted between
-rounds.  Latency = completion - arrival (queueing, set-up and solve).
+Batches.  At every admission point the waiting requests of one kind (and, for
+polarization, one exterior permittivity and applied field) are admitted together, as
+far as the device-memory budget and the batch limits allow, into one forest
+(``kifmm_forest_build``): one tree, one plan and -- for polarization -- one solver
+whose instances each run their own GMRES while sharing every matvec.  Every FMM phase
+of a step is then one launch for the whole batch.  A request that arrives while a
+batch runs waits for the next admission point and joins a new batch; batches run
+concurrently, each on its own CUDA stream: every round launches the next step of
+every live batch before it waits on any.  A batch releases its requests when its last
+instance has finished.  Latency = completion - arrival (queueing, set-up and solve).
+
+Orders.  The adjoint double layer of the polarization operator runs at p = 11 and the
+double layer of the demag potential at p = 10: the lowest orders at which the mixed
+form's matvec meets rel-L2 1e-6 on curved surfaces.
 """
 from __future__ import annotations
 
@@ -27,6 +35,7 @@ import torch
 from .capi import Plan, Solver, Tree, kifmm_polarization_rhs, kifmm_quadrature_points
 
 PI4 = 4.0 * math.pi
+DEFAULT_P = {"polar": 11, "demag": 10}
 
 
 @dataclass
@@ -46,6 +55,12 @@ class Request:
     def __post_init__(self):
         self.n = int(self.tri.shape[0])
 
+    def key(self):
+        """Requests with equal keys can share a batch."""
+        if self.kind == "polar":
+            return ("polar", float(self.eps_out), tuple(float(v) for v in self.e0))
+        return ("demag",)
+
 
 def device_bytes(n, p, restart=50, kind="polar"):
     """Upper estimate of a request's resident device memory: per-point D2T rows,
@@ -59,38 +74,53 @@ def device_bytes(n, p, restart=50, kind="polar"):
     return n * per_pt + boxes * Qp * 16 + tables
 
 
-class _Live:
-    """One admitted request: its device data, plan and step state."""
+class _Batch:
+    """Admitted requests of one key: their forest (or tree, for one request), plan,
+    solver or demag inputs, and their stream."""
 
-    def __init__(self, req, dev, p, max_leaf, precision, tol, restart, max_iter):
-        self.req = req
-        tri = torch.from_numpy(np.ascontiguousarray(req.tri.reshape(-1, 9))).to(dev)
-        sph = torch.from_numpy(np.ascontiguousarray(req.sph)).to(dev)
-        xyz, w, nrm = kifmm_quadrature_points(tri, sph)
+    def __init__(self, reqs, dev, p, max_leaf, precision, tol, restart, max_iter):
+        t0 = time.perf_counter()
+        self.reqs = reqs
+        self.kind = reqs[0].kind
+        sizes = [r.n for r in reqs]
+        self.off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        tri = np.concatenate([r.tri.reshape(-1, 9) for r in reqs])
+        sph = np.concatenate([r.sph for r in reqs])
         self.stream = torch.cuda.Stream(device=dev)
-        self.tree = Tree(xyz, max_leaf=max_leaf)
-        if req.kind == "polar":
-            self.plan = Plan(self.tree, kernel="adl", p=p, precision=precision, src_nrm=nrm, trg_nrm=nrm)
-            eps = torch.from_numpy(np.ascontiguousarray(req.eps_in)).to(dev)
-            curv = torch.from_numpy(np.ascontiguousarray(req.curv)).to(dev)
-            b = kifmm_polarization_rhs(nrm, eps, req.eps_out, req.e0)
-            self.solver = Solver(self.plan, w, eps, req.eps_out, curv, b, tol=tol, restart=restart,
-                                 max_iter=max_iter)
-            self.result = self.solver.x
-        else:
-            self.plan = Plan(self.tree, kernel="dl", p=p, precision=precision, src_nrm=nrm, trg_nrm=nrm)
-            M = req.magnetization
-            # phi1 = 4 pi M.r: the Fredkin-Koehler interior potential of uniform M
-            self.phi1 = PI4 * (M[0] * xyz[0] + M[1] * xyz[1] + M[2] * xyz[2])
-            self.w = w
-            self.omega = torch.full_like(w, 2.0 * math.pi)   # face centroids: Omega = 2 pi
-            self.result = torch.empty_like(w)
-            self.solver = None
-        torch.cuda.synchronize()
+        with torch.cuda.stream(self.stream):
+            tri_d = torch.from_numpy(np.ascontiguousarray(tri)).to(dev)
+            sph_d = torch.from_numpy(np.ascontiguousarray(sph)).to(dev)
+            xyz, w, nrm = kifmm_quadrature_points(tri_d, sph_d, stream=self.stream)
+            self.stream.synchronize()
+            if len(reqs) == 1:
+                self.tree = Tree(xyz, max_leaf=max_leaf, stream=self.stream)
+            else:
+                self.tree = Tree(xyz, max_leaf=max_leaf, stream=self.stream, instances=self.off)
+            if self.kind == "polar":
+                r0 = reqs[0]
+                self.plan = Plan(self.tree, kernel="adl", p=p, precision=precision, src_nrm=nrm, trg_nrm=nrm,
+                                 stream=self.stream)
+                eps = torch.from_numpy(np.concatenate([r.eps_in for r in reqs])).to(dev)
+                curv = torch.from_numpy(np.concatenate([r.curv for r in reqs])).to(dev)
+                b = kifmm_polarization_rhs(nrm, eps, r0.eps_out, r0.e0, stream=self.stream)
+                self.stream.synchronize()
+                self.solver = Solver(self.plan, w, eps, r0.eps_out, curv, b, tol=tol, restart=restart,
+                                     max_iter=max_iter)
+                self.result = self.solver.x
+            else:
+                self.plan = Plan(self.tree, kernel="dl", p=p, precision=precision, src_nrm=nrm, trg_nrm=nrm,
+                                 stream=self.stream)
+                # phi1 = 4 pi M.r per request: the Fredkin-Koehler interior potential of uniform M
+                M = torch.from_numpy(np.repeat(np.array([r.magnetization for r in reqs], np.float64).T,
+                                               sizes, axis=1)).to(dev)
+                self.phi1 = PI4 * (M * xyz).sum(0)
+                self.w = w
+                self.omega = torch.full_like(w, 2.0 * math.pi)   # face centroids: Omega = 2 pi
+                self.result = torch.empty_like(w)
+                self.solver = None
+        self.stream.synchronize()
+        self.setup_s = time.perf_counter() - t0
         self.done = False
-        self.iters = 0
-        self.rel_res = None
-        self.status = 0
 
     def launch(self):
         if self.solver is not None:
@@ -101,11 +131,17 @@ class _Live:
     def finish(self):
         if self.solver is not None:
             self.done = self.solver.finish()
-            self.iters, self.rel_res, self.status = self.solver.iters, self.solver.rel_res, self.solver.status
         else:
             self.stream.synchronize()
             self.done = True
         return self.done
+
+    def outcome(self, i):
+        """(iters, rel_res, status) of request i of the batch."""
+        if self.solver is None:
+            return 1, None, 0
+        it, rr, st = self.solver.instances()
+        return int(it[i]), float(rr[i]), int(st[i])
 
     def close(self):
         if self.solver is not None:
@@ -115,86 +151,121 @@ class _Live:
 
 
 class Server:
-    """Continuous-batching server for polarization solves and demag evaluations."""
+    """Batching server for polarization solves and demag evaluations."""
 
-    def __init__(self, mem_budget=64 << 30, p=10, max_leaf=64, precision="mixed", tol=1e-6, restart=50,
-                 max_iter=500, max_live=256, device="cuda:0"):
+    def __init__(self, mem_budget=64 << 30, p=None, max_leaf=64, precision="mixed", tol=1e-6, restart=50,
+                 max_iter=500, max_live=64, max_batch=64, max_batch_points=4 << 20, device="cuda:0"):
         self.mem_budget = int(mem_budget)
-        self.p, self.max_leaf, self.precision = p, max_leaf, precision
+        self.p = dict(DEFAULT_P)
+        if isinstance(p, dict):
+            self.p.update(p)
+        elif p is not None:
+            self.p = {"polar": int(p), "demag": int(p)}
+        self.max_leaf, self.precision = max_leaf, precision
         self.tol, self.restart, self.max_iter = tol, restart, max_iter
-        self.max_live = max_live
+        self.max_live, self.max_batch, self.max_batch_points = max_live, max_batch, max_batch_points
         self.dev = torch.device(device)
+
+    def _need(self, r):
+        return device_bytes(r.n, self.p[r.kind], self.restart, r.kind)
+
+    def _take_batch(self, waiting, mem_free, first_fits):
+        """Requests of the head's key, in arrival order, while the memory budget and the
+        batch limits allow (the head always, if nothing else is live)."""
+        key = waiting[0].key()
+        group, need, pts = [], 0, 0
+        for r in waiting:
+            if r.key() != key:
+                continue
+            nr = self._need(r)
+            if group and (len(group) >= self.max_batch or pts + r.n > self.max_batch_points):
+                break
+            if need + nr > mem_free and not (first_fits and not group):
+                break
+            group.append(r)
+            need += nr
+            pts += r.n
+        return group, need
 
     def run(self, requests, keep_results=False):
         """Serve ``requests`` (sorted by arrival) in real time; returns per-request
         records (rid, kind, n, arrival, admitted, completed, latency, iters, rel_res,
-        status) and run totals."""
+        status, batch, setup_s) and run totals."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         i_next, waiting, live, mem_used, out = 0, [], [], 0, []
-        peak_live = 0
-        rounds = 0
+        peak_live = peak_batch = rounds = n_batches = 0
+        setup_total = 0.0
         t0 = time.perf_counter()
         while i_next < len(reqs) or waiting or live:
             now = time.perf_counter() - t0
             while i_next < len(reqs) and reqs[i_next].arrival <= now:
                 waiting.append(reqs[i_next])
                 i_next += 1
-            # admission: first come, first served, within the memory budget
+            # admission: batches of the head's key, first come first served, within the budget
             while waiting and len(live) < self.max_live:
-                r = waiting[0]
-                need = device_bytes(r.n, self.p, self.restart, r.kind)
-                if live and mem_used + need > self.mem_budget:
+                group, need = self._take_batch(waiting, self.mem_budget - mem_used, not live)
+                if not group:
                     break
-                waiting.pop(0)
+                ids = {id(r) for r in group}
+                waiting = [r for r in waiting if id(r) not in ids]
                 t_adm = time.perf_counter() - t0
-                lv = _Live(r, self.dev, self.p, self.max_leaf, self.precision, self.tol, self.restart,
-                           self.max_iter)
-                lv.admitted, lv.need = t_adm, need
+                bt = _Batch(group, self.dev, self.p[group[0].kind], self.max_leaf, self.precision, self.tol,
+                            self.restart, self.max_iter)
+                bt.admitted, bt.need = t_adm, need
+                setup_total += bt.setup_s
+                n_batches += 1
+                peak_batch = max(peak_batch, len(group))
                 mem_used += need
-                live.append(lv)
+                live.append(bt)
             if not live:
                 if i_next < len(reqs):
                     time.sleep(max(0.0, reqs[i_next].arrival - (time.perf_counter() - t0)))
                 continue
             peak_live = max(peak_live, len(live))
-            # one round: every live request's next step on its own stream, then the waits
-            for lv in live:
-                lv.launch()
+            # one round: every live batch's next step on its own stream, then the waits
+            for bt in live:
+                bt.launch()
             rounds += 1
             still = []
-            for lv in live:
-                if lv.finish():
+            for bt in live:
+                if bt.finish():
                     t_done = time.perf_counter() - t0
-                    rec = dict(rid=lv.req.rid, kind=lv.req.kind, n=lv.req.n, arrival=lv.req.arrival,
-                               admitted=lv.admitted, completed=t_done, latency=t_done - lv.req.arrival,
-                               iters=lv.iters, rel_res=lv.rel_res, status=lv.status)
-                    if keep_results:
-                        rec["result"] = lv.result.clone()
-                    out.append(rec)
-                    mem_used -= lv.need
-                    lv.close()
+                    for i, r in enumerate(bt.reqs):
+                        iters, rel_res, status = bt.outcome(i)
+                        rec = dict(rid=r.rid, kind=r.kind, n=r.n, arrival=r.arrival, admitted=bt.admitted,
+                                   completed=t_done, latency=t_done - r.arrival, iters=iters, rel_res=rel_res,
+                                   status=status, batch=len(bt.reqs), setup_s=bt.setup_s)
+                        if keep_results:
+                            rec["result"] = bt.result[int(bt.off[i]):int(bt.off[i + 1])].clone()
+                        out.append(rec)
+                    mem_used -= bt.need
+                    bt.close()
                 else:
-                    still.append(lv)
+                    still.append(bt)
             live = still
         span = time.perf_counter() - t0
-        return out, dict(makespan_s=span, rounds=rounds, peak_live=peak_live)
+        return out, dict(makespan_s=span, rounds=rounds, peak_live=peak_live, batches=n_batches,
+                         peak_batch=peak_batch, setup_s=setup_total)
 
 
-def serial_baseline(requests, p=10, max_leaf=64, precision="fp64", tol=1e-6, restart=50, max_iter=500,
+def serial_baseline(requests, p=None, max_leaf=64, precision="fp64", tol=1e-6, restart=50, max_iter=500,
                     device="cuda:0"):
     """The same requests one at a time -- set up, solved (or evaluated) to the end and
     released before the next starts, the plain FP64 form by default; returns each
     request's service time in seconds."""
     dev = torch.device(device)
+    pk = dict(DEFAULT_P)
+    if p is not None:
+        pk = {"polar": int(p), "demag": int(p)}
     times = []
     for r in requests:
         t0 = time.perf_counter()
-        lv = _Live(r, dev, p, max_leaf, precision, tol, restart, max_iter)
+        bt = _Batch([r], dev, pk[r.kind], max_leaf, precision, tol, restart, max_iter)
         done = False
         while not done:
-            lv.launch()
-            done = lv.finish()
-        lv.close()
+            bt.launch()
+            done = bt.finish()
+        bt.close()
         times.append(time.perf_counter() - t0)
     return times
 

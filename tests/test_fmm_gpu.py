@@ -83,6 +83,34 @@ def test_fmm_matches_oracle(geom, kernel, prec, p, tol):
     assert err < tol
 
 
+def test_fp64_accuracy_floor():
+    """The FP64 form's floor, and why it is a floor.  On the 5,120-point sphere the
+    single layer stops at about 4e-9 and the double layers at about 4e-8 (p = 12,
+    pseudo-inverse cut at 1e-9 of the largest singular value):
+    - the floor: p = 14 is no better than p = 12 (within 2x; measured 8.5e-9 vs 4.1e-9);
+    - its cause: a smaller cut makes the error larger (cut 1e-11: 5.5e-7), because the
+      truncated pseudo-inverse multiplies the rounding error of the FP64 check
+      potentials by up to 1/cut while the truncation error it removes is already
+      below the rounding floor.  1e-9 is therefore out of reach of the
+      equivalent-density form in FP64 at any order on this geometry."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    m, h, (xyz, w, nrm), sig, refs = case("sphere")
+    tree = Tree(xyz, max_leaf=40)
+    q = torch.from_numpy(sig).to(DEV) * w
+
+    def err(kernel, p, cut=0.0):
+        plan = Plan(tree, kernel=kernel, p=p, precision="fp64", src_nrm=nrm, trg_nrm=nrm, pinv_cutoff=cut)
+        return rel(plan.matvec(q).cpu().numpy(), refs[kernel])
+
+    e12 = {k: err(k, 12) for k in ("sl", "dl", "adl")}
+    e14 = err("sl", 14)
+    e12_fine = err("sl", 12, 1e-11)
+    print("FP64 floor: p=12 %s; SL p=14 %.3e; SL p=12 cut 1e-11 %.3e" % (e12, e14, e12_fine))
+    assert e12["sl"] < 1e-8 and e12["dl"] < 1e-7 and e12["adl"] < 1e-7
+    assert e14 > 0.5 * e12["sl"]
+    assert e12_fine > 10 * e12["sl"]
+
+
 def test_near_field_alone_at_single_layer_accuracy():
     """A curved patch of 64 points that fits one leaf: the whole sum is near field, so
     the result shows the FP32 near field's own accuracy.  On a sphere of radius 1
