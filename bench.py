@@ -368,8 +368,10 @@ def run_serve(args):
         for k, rate in enumerate(rates):
             reqs = [Request(rid=i, **d) for i, d in enumerate(synth.serve_requests(n_req, rate, 5000 + k))]
             server = Server(mem_budget=args.serve_mem_gb * (1 << 30), p=args.serve_p, precision=args.precision,
-                            max_batch=args.serve_max_batch)
+                            max_batch=args.serve_max_batch, max_batch_points=args.serve_max_batch_points,
+                            setup_workers=args.serve_setup_workers)
             recs, tot = server.run(reqs)
+            server.close()
             lat = [r["latency"] for r in recs]
             p50, p99 = percentiles(lat)
             polar = [r for r in recs if r["kind"] == "polar"]
@@ -379,16 +381,19 @@ def run_serve(args):
                           "unknowns_per_s": unknowns / tot["makespan_s"], "makespan_s": tot["makespan_s"],
                           "peak_live": tot["peak_live"], "rounds": tot["rounds"], "batches": tot["batches"],
                           "peak_batch": tot["peak_batch"], "setup_s": tot["setup_s"],
+                          "server_start_s": tot["start_s"],
                           "polar_max_true_rel_residual": max((r["rel_res"] for r in polar), default=None),
                           "polar_failed": sum(1 for r in polar if r["status"] != 0)})
             print("serve rate %g: p50 %.1f ms p99 %.1f ms, %.1f req/s" % (rate, p50 * 1e3, p99 * 1e3,
                                                                     sweep[-1]["throughput_req_s"]),
                   file=sys.stderr, flush=True)
-    base_reqs = [Request(rid=i, **d) for i, d in enumerate(synth.serve_requests(args.serve_serial, 1.0, 5999))]
-    st = serial_baseline(base_reqs, p=args.serve_p, precision="fp64")
-    serial = {"requests": len(st), "precision": "fp64", "mean_service_ms": float(np.mean(st)) * 1e3,
-              "throughput_req_s": len(st) / float(np.sum(st)),
-              "unknowns_per_s": sum(r.n for r in base_reqs) / float(np.sum(st))}
+    serial = None
+    if args.serve_serial > 0:
+        base_reqs = [Request(rid=i, **d) for i, d in enumerate(synth.serve_requests(args.serve_serial, 1.0, 5999))]
+        st = serial_baseline(base_reqs, p=args.serve_p, precision="fp64")
+        serial = {"requests": len(st), "precision": "fp64", "mean_service_ms": float(np.mean(st)) * 1e3,
+                  "throughput_req_s": len(st) / float(np.sum(st)),
+                  "unknowns_per_s": sum(r.n for r in base_reqs) / float(np.sum(st))}
     top = sweep[-1]
     line = {"metric": "serving throughput (solve requests/s) with p50/p99 latency", "value": top["throughput_req_s"],
             "unit": "requests/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
@@ -396,7 +401,8 @@ def run_serve(args):
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": "serve_stream", "sizes": "log-uniform 2k-500k",
                        "p": args.serve_p if args.serve_p else {"polar": 11, "demag": 10},
-                       "max_batch": args.serve_max_batch,
+                       "max_batch": args.serve_max_batch, "max_batch_points": args.serve_max_batch_points,
+                       "setup_workers": args.serve_setup_workers,
                        "precision": args.precision, "mem_budget_gb": args.serve_mem_gb,
                        "kinds": "half polarization GMRES(50) tol 1e-6, half demag phi2"},
             "serve": sweep, "serial_fp64": serial, "clocks": clk.summary(),
@@ -682,7 +688,8 @@ def rooflines(phases, st, tst, args, kernel, peaks):
         out["p2p"] = {"kernel": "k_p2p_warp<%d> (FP32x2)" % {"sl": 0, "dl": 1, "adl": 2, "field": 3}[kernel],
                       "bound": "alu", "achieved": fpp * npairs / t / 1e12, "peak": peak, "unit": "TFLOP/s",
                       "frac": fpp * npairs / t / 1e12 / peak, "traffic": None, "ms": phases["p2p"],
-                      "pairs": npairs, "flops_per_pair": fpp, "pairs_per_s": npairs / t,
+                      "pairs": npairs, "axis_pairs": st.get("near_axis_pairs", 0), "flops_per_pair": fpp,
+                      "pairs_per_s": npairs / t,
                       "mufu_frac": npairs / t / peaks["rsqrt_per_s"],
                       "peak_source": "measured FP32 FMA rate (kifmm_peak_rate) at %.0f MHz" % (peaks["sm_mhz"] or 0)}
     else:
@@ -727,6 +734,8 @@ def main():
     ap.add_argument("--serve-p", type=int, default=None,
                     help="one order for both kinds (default: ADL p = 11, DL p = 10)")
     ap.add_argument("--serve-max-batch", type=int, default=64, help="requests per batch (1: no shared launches)")
+    ap.add_argument("--serve-max-batch-points", type=int, default=4 << 20, help="unknowns per batch")
+    ap.add_argument("--serve-setup-workers", type=int, default=2, help="threads setting batches up")
     ap.add_argument("--serve-mem-gb", type=float, default=96.0)
     ap.add_argument("--solves", type=int, default=5, help="timed polarization solves (0: skip)")
     ap.add_argument("--no-fp64-plain", dest="fp64_plain", action="store_false",

@@ -274,6 +274,12 @@ typedef struct {
                                          all lie along one coordinate axis (flat faces
                                          normal to an axis), evaluated with the one-term
                                          n.(x - y) of those normals                      */
+    double  setup_ms[5];              /* wall-clock set-up time (ms), device work included:
+                                         [0] operator tables (0 when shared with a live
+                                         plan of the same key), [1] work lists and the
+                                         near-field units, [2] translation tiles, [3]
+                                         evaluation rows, [4] the total                    */
+    int64_t near_axis_pairs;          /* mixed DL: the pairs of those axis units         */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);

@@ -52,7 +52,7 @@ def _time_graph(plan, q, out, reps):
 
 
 def autotune(xyz, q, kernel, instances, nrm=None, target=1e-6, safety=0.7,
-             orders=(4, 6, 8, 10), leaf_sizes=(32, 48, 64, 96, 128, 192, 256), p_ref=12,
+             orders=(4, 6, 8, 10, 11, 12), leaf_sizes=(32, 48, 64, 96, 128, 192, 256), p_ref=12,
              ref_leaf=64, stride=8, reps=5, log=None):
     """Returns dict(p, max_leaf, est_err, errors, times_ms, tune_s) for the batch.
 

@@ -463,9 +463,17 @@ struct Solver {
             KF_TRY(doff.alloc(ni + 1));
             KF_CHECK_CUDA(cudaMemcpy(doff.p, off.data(), (ni + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
             KF_TRY(pinst.alloc(n));
-            k_point_instance<<<div_up(n, 256), 256>>>(doff.p, ni, n, pinst.p);
-            KF_CHECK_LAUNCH();
-            KF_CHECK_CUDA(cudaDeviceSynchronize());
+            // on a private stream, so that other solves' work in flight is not waited for
+            cudaStream_t ps = nullptr;
+            KF_CHECK_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+            k_point_instance<<<div_up(n, 256), 256, 0, ps>>>(doff.p, ni, n, pinst.p);
+            cudaError_t le = cudaGetLastError();
+            cudaError_t se = cudaStreamSynchronize(ps);
+            cudaStreamDestroy(ps);
+            if (le != cudaSuccess || se != cudaSuccess) {
+                set_error("point-to-instance map: %s", cudaGetErrorString(le != cudaSuccess ? le : se));
+                return KIFMM_ERR_CUDA;
+            }
         }
         KF_TRY(partial.alloc((size_t)nblk * (m + 1)));
         KF_TRY(hdev.alloc(3 * (size_t)ni * hld + ni));
@@ -566,7 +574,7 @@ struct Solver {
     void update_rel_max() {
         rel_max = 0;
         for (int i = 0; i < ni; ++i)
-            if (state[i] == kRun || state[i] == kWait) rel_max = std::max(rel_max, rel[i]);
+            if (state[i] != kFail) rel_max = std::max(rel_max, rel[i]);
     }
 
     void fail(int i, int code) {

@@ -14,6 +14,7 @@
 //           input order
 // Near-singular pairs (|r_i - r_j| < 1e-5) contribute nothing (Sec. III.A.1).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <map>
 #include <memory>
@@ -1752,6 +1753,16 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
 
 int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s) {
     Tree& T = P.tree->t;
+    // wall-clock time of each set-up phase, the device work of the phase included
+    const auto t_start = std::chrono::steady_clock::now();
+    auto t_last = t_start;
+    auto stamp = [&](int k) -> int {
+        KF_CHECK_CUDA(cudaStreamSynchronize(s));
+        const auto now = std::chrono::steady_clock::now();
+        P.setup_ms[k] = std::chrono::duration<double, std::milli>(now - t_last).count();
+        t_last = now;
+        return KIFMM_OK;
+    };
     // the Chebyshev engine has no pseudo-inverses (its order only picks the surface
     // operators computed here, which it leaves unused)
     const HostPinv& h = host_pinv(P.cheb ? 2 : P.p, P.cut_up, P.cut_dn);
@@ -1786,6 +1797,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
 
     // operators: shared tables of this key, built once
     KF_TRY(get_tables(P, h, s));
+    KF_TRY(stamp(0));
     // mixed: tiles sized for the tensor-core GEMM of each family's row count; FP64:
     // CUDA-core blocks of kPairTile
     const int cap_up = P.fp64 ? kPairTile : tc_tile_pairs(P.ops->Ku);
@@ -1998,9 +2010,11 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         });
         std::vector<int4> hu(units.size());
         P.n_p2p_axis = 0;
+        P.near_axis_pairs = 0;
         for (size_t i = 0; i < units.size(); ++i) {
             hu[i] = units[ord[i]].u;
             P.n_p2p_axis += is_axis[ord[i]];
+            if (is_axis[ord[i]]) P.near_axis_pairs += units[ord[i]].work;
         }
         KF_TRY(P.p2p_units.upload(hu, s));
         KF_TRY(P.p2p_ranges.upload(ranges, s));
@@ -2010,6 +2024,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         P.n_p2p_corr = (int)hcu.size();
         for (int k = 0; k < 5; ++k) KF_TRY(set_p2p_smem(k));
     }
+    KF_TRY(stamp(1));
 
     // U2U: per parent level, (child -> parent) grouped by the child's octant
     {
@@ -2101,6 +2116,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_CHECK_CUDA(cudaEventCreateWithFlags(&P.ev_far, cudaEventDisableTiming));
     }
 
+    KF_TRY(stamp(2));
     // per-target evaluation rows and buffers
     size_t nbq = (size_t)T.nbox * P.Qp;
     if (P.fp64) {
@@ -2130,7 +2146,8 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         // DL: the dipoles q n_j as FP32 and their FP32 remainders (6 rows); else 3 rows
         KF_TRY(P.q_f.alloc((P.kernel == KIFMM_KERNEL_DL ? 6 : 3) * T.ns));
     }
-    KF_CHECK_CUDA(cudaStreamSynchronize(s));
+    KF_TRY(stamp(3));
+    P.setup_ms[4] = std::chrono::duration<double, std::milli>(t_last - t_start).count();
 
     P.device_bytes = 0;
     for (size_t b : {(size_t)P.ops->bytes(), P.d2t_d.bytes(), P.d2t_f.bytes(), P.u_d.bytes(), P.d_d.bytes(),
@@ -2700,6 +2717,8 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->near_pairs = P.near_pairs;
     st->s2u_points = (P.fp64 || !P.ops) ? P.Q : P.ops->ks;
     st->m2l_chain_pairs = P.m2l_chain_pairs;
+    for (int k = 0; k < 5; ++k) st->setup_ms[k] = P.setup_ms[k];
+    st->near_axis_pairs = P.near_axis_pairs;
     return KIFMM_OK;
 }
 

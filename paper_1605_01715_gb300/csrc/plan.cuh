@@ -100,6 +100,7 @@ struct Plan {
     DBuf<longlong2> p2p_cranges;          //   corrected-distance launch) and those ranges
     int n_p2p_corr = 0;
     int n_p2p_axis = 0;                   // DL: the last units of p2p_units, dipoles along one axis
+    int64_t near_axis_pairs = 0;          // their (target, source) pairs
     bool p2p_multi = false;               // some leaf spans several units
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
@@ -121,6 +122,7 @@ struct Plan {
     // profiling: per-matvec slots of 8 events, reduced when read
     bool profile = false;
     bool serial = false;            // profiling: the near field after the far field, on one stream
+    double setup_ms[5] = {};        // set-up phases (ms): tables, work lists, tiles, rows, total
     std::vector<std::vector<cudaEvent_t>> ev_slots;
     int slots_used = 0;
     int launches = 0;

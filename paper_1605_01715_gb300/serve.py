@@ -16,8 +16,13 @@ whose instances each run their own GMRES while sharing every matvec.  Every FMM 
 of a step is then one launch for the whole batch.  A request that arrives while a
 batch runs waits for the next admission point and joins a new batch; batches run
 concurrently, each on its own CUDA stream: every round launches the next step of
-every live batch before it waits on any.  A batch releases its requests when its last
-instance has finished.  Latency = completion - arrival (queueing, set-up and solve).
+every live batch before it waits on any.  A batch's set-up (tree, plan, evaluation
+rows) runs on one of two worker threads while the live batches keep stepping: the
+set-up is host work (work lists, tiles) and FP64 device work (the evaluation rows),
+and two set-ups overlap one's host part with the other's device part.  A batch releases
+its requests when its last instance has finished.  Latency = completion - arrival
+(queueing, set-up and solve).  The operator tables are built once, at server start,
+and kept by one small anchor plan per kind.
 
 Orders.  The adjoint double layer of the polarization operator runs at p = 11 and the
 double layer of the demag potential at p = 10: the lowest orders at which the mixed
@@ -151,11 +156,19 @@ class _Batch:
 
 
 class Server:
-    """Batching server for polarization solves and demag evaluations."""
+    """Batching server for polarization solves and demag evaluations.
+
+    ``start()`` (called by ``run`` if needed) builds one small anchor plan per kind:
+    the operator tables depend only on the kernel, order, precision and cutoffs, and a
+    live plan of the same key keeps them resident, so batches never rebuild them.
+    Batches are set up on a worker thread (the library's calls release the GIL), so
+    the scheduler keeps stepping the live batches meanwhile."""
 
     def __init__(self, mem_budget=64 << 30, p=None, max_leaf=64, precision="mixed", tol=1e-6, restart=50,
-                 max_iter=500, max_live=64, max_batch=64, max_batch_points=4 << 20, device="cuda:0"):
+                 max_iter=500, max_live=64, max_batch=64, max_batch_points=4 << 20, setup_workers=2,
+                 device="cuda:0"):
         self.mem_budget = int(mem_budget)
+        self.setup_workers = max(1, int(setup_workers))
         self.p = dict(DEFAULT_P)
         if isinstance(p, dict):
             self.p.update(p)
@@ -165,6 +178,33 @@ class Server:
         self.tol, self.restart, self.max_iter = tol, restart, max_iter
         self.max_live, self.max_batch, self.max_batch_points = max_live, max_batch, max_batch_points
         self.dev = torch.device(device)
+        self._anchors = None
+        self.start_s = None
+
+    def start(self):
+        """Build the anchor plans (once); returns the seconds it took."""
+        if self._anchors is not None:
+            return 0.0
+        t0 = time.perf_counter()
+        # the 8 corners of a small cube with their diagonal normals: one leaf
+        c = np.array([[x, y, z] for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)]).T
+        xyz = torch.from_numpy(np.ascontiguousarray(0.1 * c)).to(self.dev)
+        nrm = torch.from_numpy(np.ascontiguousarray(c / math.sqrt(3.0))).to(self.dev)
+        tree = Tree(xyz, max_leaf=self.max_leaf)
+        plans = [Plan(tree, kernel=k, p=self.p[kind], precision=self.precision, src_nrm=nrm, trg_nrm=nrm)
+                 for kind, k in (("polar", "adl"), ("demag", "dl"))]
+        torch.cuda.synchronize(self.dev)
+        self._anchors = (tree, plans)
+        self.start_s = time.perf_counter() - t0
+        return self.start_s
+
+    def close(self):
+        if self._anchors is not None:
+            tree, plans = self._anchors
+            for pl in plans:
+                pl.close()
+            tree.close()
+            self._anchors = None
 
     def _need(self, r):
         return device_bytes(r.n, self.p[r.kind], self.restart, r.kind)
@@ -187,86 +227,109 @@ class Server:
             pts += r.n
         return group, need
 
+    def _new_batch(self, group):
+        return _Batch(group, self.dev, self.p[group[0].kind], self.max_leaf, self.precision, self.tol,
+                      self.restart, self.max_iter)
+
     def run(self, requests, keep_results=False):
         """Serve ``requests`` (sorted by arrival) in real time; returns per-request
         records (rid, kind, n, arrival, admitted, completed, latency, iters, rel_res,
         status, batch, setup_s) and run totals."""
+        from concurrent.futures import FIRST_COMPLETED, ThreadPoolExecutor, wait
+
+        self.start()
         reqs = sorted(requests, key=lambda r: r.arrival)
-        i_next, waiting, live, mem_used, out = 0, [], [], 0, []
+        i_next, waiting, live, pending, mem_used, out = 0, [], [], [], 0, []
         peak_live = peak_batch = rounds = n_batches = 0
         setup_total = 0.0
+        pool = ThreadPoolExecutor(max_workers=self.setup_workers)
         t0 = time.perf_counter()
-        while i_next < len(reqs) or waiting or live:
-            now = time.perf_counter() - t0
-            while i_next < len(reqs) and reqs[i_next].arrival <= now:
-                waiting.append(reqs[i_next])
-                i_next += 1
-            # admission: batches of the head's key, first come first served, within the budget
-            while waiting and len(live) < self.max_live:
-                group, need = self._take_batch(waiting, self.mem_budget - mem_used, not live)
-                if not group:
-                    break
-                ids = {id(r) for r in group}
-                waiting = [r for r in waiting if id(r) not in ids]
-                t_adm = time.perf_counter() - t0
-                bt = _Batch(group, self.dev, self.p[group[0].kind], self.max_leaf, self.precision, self.tol,
-                            self.restart, self.max_iter)
-                bt.admitted, bt.need = t_adm, need
-                setup_total += bt.setup_s
-                n_batches += 1
-                peak_batch = max(peak_batch, len(group))
-                mem_used += need
-                live.append(bt)
-            if not live:
-                if i_next < len(reqs):
-                    time.sleep(max(0.0, reqs[i_next].arrival - (time.perf_counter() - t0)))
-                continue
-            peak_live = max(peak_live, len(live))
-            # one round: every live batch's next step on its own stream, then the waits
-            for bt in live:
-                bt.launch()
-            rounds += 1
-            still = []
-            for bt in live:
-                if bt.finish():
-                    t_done = time.perf_counter() - t0
-                    for i, r in enumerate(bt.reqs):
-                        iters, rel_res, status = bt.outcome(i)
-                        rec = dict(rid=r.rid, kind=r.kind, n=r.n, arrival=r.arrival, admitted=bt.admitted,
-                                   completed=t_done, latency=t_done - r.arrival, iters=iters, rel_res=rel_res,
-                                   status=status, batch=len(bt.reqs), setup_s=bt.setup_s)
-                        if keep_results:
-                            rec["result"] = bt.result[int(bt.off[i]):int(bt.off[i + 1])].clone()
-                        out.append(rec)
-                    mem_used -= bt.need
-                    bt.close()
-                else:
-                    still.append(bt)
-            live = still
+        try:
+            while i_next < len(reqs) or waiting or live or pending:
+                now = time.perf_counter() - t0
+                while i_next < len(reqs) and reqs[i_next].arrival <= now:
+                    waiting.append(reqs[i_next])
+                    i_next += 1
+                # admission: a batch of the head's key, first come first served, within
+                # the budget, whenever a set-up worker is free (requests that arrive
+                # while the workers are busy gather into the next batch)
+                if waiting and len(pending) < self.setup_workers and len(live) + len(pending) < self.max_live:
+                    group, need = self._take_batch(waiting, self.mem_budget - mem_used, not (live or pending))
+                    if group:
+                        ids = {id(r) for r in group}
+                        waiting = [r for r in waiting if id(r) not in ids]
+                        pending.append((pool.submit(self._new_batch, group), time.perf_counter() - t0, need))
+                        mem_used += need
+                        n_batches += 1
+                        peak_batch = max(peak_batch, len(group))
+                # batches whose set-up has finished join the live set
+                still_pending = []
+                for fut, t_adm, need in pending:
+                    if fut.done():
+                        bt = fut.result()
+                        bt.admitted, bt.need = t_adm, need
+                        setup_total += bt.setup_s
+                        live.append(bt)
+                    else:
+                        still_pending.append((fut, t_adm, need))
+                pending = still_pending
+                if not live:
+                    if pending:                  # wait (briefly) for a set-up to finish
+                        wait([f for f, _, _ in pending], timeout=0.05, return_when=FIRST_COMPLETED)
+                    elif i_next < len(reqs):
+                        time.sleep(max(0.0, reqs[i_next].arrival - (time.perf_counter() - t0)))
+                    continue
+                peak_live = max(peak_live, len(live))
+                # one round: every live batch's next step on its own stream, then the waits
+                for bt in live:
+                    bt.launch()
+                rounds += 1
+                still = []
+                for bt in live:
+                    if bt.finish():
+                        t_done = time.perf_counter() - t0
+                        for i, r in enumerate(bt.reqs):
+                            iters, rel_res, status = bt.outcome(i)
+                            rec = dict(rid=r.rid, kind=r.kind, n=r.n, arrival=r.arrival, admitted=bt.admitted,
+                                       completed=t_done, latency=t_done - r.arrival, iters=iters, rel_res=rel_res,
+                                       status=status, batch=len(bt.reqs), setup_s=bt.setup_s)
+                            if keep_results:
+                                rec["result"] = bt.result[int(bt.off[i]):int(bt.off[i + 1])].clone()
+                            out.append(rec)
+                        mem_used -= bt.need
+                        bt.close()
+                    else:
+                        still.append(bt)
+                live = still
+        finally:
+            pool.shutdown(wait=True)
         span = time.perf_counter() - t0
         return out, dict(makespan_s=span, rounds=rounds, peak_live=peak_live, batches=n_batches,
-                         peak_batch=peak_batch, setup_s=setup_total)
+                         peak_batch=peak_batch, setup_s=setup_total, start_s=self.start_s)
 
 
 def serial_baseline(requests, p=None, max_leaf=64, precision="fp64", tol=1e-6, restart=50, max_iter=500,
                     device="cuda:0"):
     """The same requests one at a time -- set up, solved (or evaluated) to the end and
-    released before the next starts, the plain FP64 form by default; returns each
-    request's service time in seconds."""
-    dev = torch.device(device)
-    pk = dict(DEFAULT_P)
-    if p is not None:
-        pk = {"polar": int(p), "demag": int(p)}
+    released before the next starts, the plain FP64 form by default, with the operator
+    tables built once beforehand as for the server; returns each request's service
+    time in seconds."""
+    srv = Server(p=p, max_leaf=max_leaf, precision=precision, tol=tol, restart=restart, max_iter=max_iter,
+                 device=device)
+    srv.start()
     times = []
-    for r in requests:
-        t0 = time.perf_counter()
-        bt = _Batch([r], dev, pk[r.kind], max_leaf, precision, tol, restart, max_iter)
-        done = False
-        while not done:
-            bt.launch()
-            done = bt.finish()
-        bt.close()
-        times.append(time.perf_counter() - t0)
+    try:
+        for r in requests:
+            t0 = time.perf_counter()
+            bt = srv._new_batch([r])
+            done = False
+            while not done:
+                bt.launch()
+                done = bt.finish()
+            bt.close()
+            times.append(time.perf_counter() - t0)
+    finally:
+        srv.close()
     return times
 
 
