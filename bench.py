@@ -685,7 +685,10 @@ def rooflines(phases, st, tst, args, kernel, peaks):
     if mixed:
         fpp = P2P_FLOPS[kernel]
         peak = peaks["fp32_tflops"]
-        out["p2p"] = {"kernel": "k_p2p_warp<%d> (FP32x2)" % {"sl": 0, "dl": 1, "adl": 2, "field": 3}[kernel],
+        kinds = "<%d>" % {"sl": 0, "dl": 1, "adl": 2, "field": 3}[kernel]
+        if st.get("near_axis_pairs"):
+            kinds += " + <4> (axis-aligned dipoles)"
+        out["p2p"] = {"kernel": "k_p2p_warp%s (FP32x2)" % kinds,
                       "bound": "alu", "achieved": fpp * npairs / t / 1e12, "peak": peak, "unit": "TFLOP/s",
                       "frac": fpp * npairs / t / 1e12 / peak, "traffic": None, "ms": phases["p2p"],
                       "pairs": npairs, "axis_pairs": st.get("near_axis_pairs", 0), "flops_per_pair": fpp,
