@@ -184,7 +184,11 @@ int kifmm_tree_destroy(kifmm_tree tree);
  *               selects the Chebyshev-interpolation far field (p: nodes per dimension).
  *   pinv_cutoff > 0 and < 1: both pseudo-inverses truncated there; or 0 for the
  *               defaults: FP64 1e-9; mixed 1e-8, except Pu of the double layer at 1e-9
- *               (the dipole sources' upward densities need those directions).
+ *               (the dipole sources' upward densities need those directions).  The
+ *               mixed form also keeps at most 256 singular triplets of Pd, and of Pu
+ *               except for the double layer (from p = 11 on, 1e-8 would keep more):
+ *               the rows one tensor-core work item covers.  The ranks kept are in
+ *               kifmm_plan_get_stats (rank_up, rank_down).
  *   src_nrm     device 3*n_src SoA; required for DL, else ignored (may be NULL).
  *   trg_nrm     device 3*n_trg SoA; required for ADL, else ignored (may be NULL).
  * Errors: INVALID_ARG, OOM, CUDA.

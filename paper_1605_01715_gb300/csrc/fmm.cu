@@ -41,9 +41,23 @@ int launch_pair_tc(int which, const CUtensorMap& hi, const CUtensorMap& lo, int 
 
 namespace {
 
+// Largest pseudo-inverse rank of the mixed form: the operator rows one tensor-core work
+// item covers (two 128-row slabs).
+constexpr int kMixedMaxRank = 256;
+
+// 1/sqrt(x) by the hardware approximation with subnormal inputs and results flushed to
+// zero (PTX rsqrt.approx.ftz.f32), without the rescaling of subnormal inputs that
+// rsqrtf adds around it.  Every r^2 that reaches it is a normal float, or 0 for a pair
+// within the tolerance radius, whose term a select then drops.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <typename Real> struct RT;
 template <> struct RT<float> {
-    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float rsq(float x) { return rsqrt_ftz(x); }
 };
 template <> struct RT<double> {
     static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
@@ -204,7 +218,7 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
         for (int m = 0; m < NP; ++m) {
             const float2 dx = __fadd2_rn(px[m], nx), dy = __fadd2_rn(py[m], ny), dz = __fadd2_rn(pz[m], nz);
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 inv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
             float2 v;
             if (DIFF) {
                 // |y|^2 - |p - y|^2 = 2 p.y - |p|^2; |p - y| = r2 inv
@@ -859,9 +873,8 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
 
     // raw rows per source: hi x|y|z, lo x|y|z, then q (SL, ADL, field) or q n_j hi x|y|z
     // and lo x|y|z (DL)
-    auto issue = [&](int64_t jb, int64_t je, int buf) {
-        const int64_t j = jb + lane;
-        if (j < je) {
+    auto issue = [&](int64_t j, int buf) {
+        if (j >= 0) {
             float* rw = raw + buf * (S::kRaw * 32) + lane;
 #pragma unroll
             for (int d = 0; d < 6; ++d) cp_async4(rw + 32 * d, sxf + d * ns + j);
@@ -882,34 +895,54 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
             ge = e1;
         const float magic = 1.5f * exp2i(E + 13);        // rounds to the grid 2^(E-10)
         if (ACC) split_targets(magic);
+        // Chunks of 32 sources run across the group's ranges (a leaf's neighbour boxes hold
+        // a few dozen sources each), skipping the ranges of the other launch (the
+        // corrected-distance ranges are the CORR instance's, and only its).  take() walks
+        // the warp-uniform position (e, j0) past the next chunk; each lane gets its source
+        // j (-1: none) and whether its range needs the tolerance-radius select.
         int e = gb;
         int64_t j0 = ranges[e].x & kRangeIdx, se = ranges[e].y;
         long long fl = ranges[e].x & ~kRangeIdx;
-        issue(j0, se, 0);
-        int buf = 0;
-        while (e < ge) {
-            const int cnt = (int)(se - j0 < 32 ? se - j0 : 32);
-            const long long cfl = fl;
-            // the next chunk, whose copy overlaps this one's evaluation
-            j0 += 32;
-            while (j0 >= se && ++e < ge) {
-                j0 = ranges[e].x & kRangeIdx;
-                fl = ranges[e].x & ~kRangeIdx;
-                se = ranges[e].y;
+        auto take = [&](int64_t& j, bool& ex) -> int {
+            j = -1;
+            ex = false;
+            int got = 0;
+            while (e < ge && got < 32) {
+                const bool mine = ((fl & kRangeCorr) != 0) == CORR;
+                if (mine && j0 < se) {
+                    const int n = (int)(se - j0 < 32 - got ? se - j0 : 32 - got);
+                    if (lane >= got && lane < got + n) {
+                        j = j0 + (lane - got);
+                        ex = (fl & kRangeExcl) != 0;
+                    }
+                    got += n;
+                    j0 += n;
+                }
+                if ((!mine || j0 >= se) && ++e < ge) {
+                    j0 = ranges[e].x & kRangeIdx;
+                    se = ranges[e].y;
+                    fl = ranges[e].x & ~kRangeIdx;
+                }
             }
-            if (e < ge) {
-                issue(j0, se, buf ^ 1);
+            return got;
+        };
+        int64_t jn;
+        bool exn;
+        int cnt = take(jn, exn);
+        bool excl = __any_sync(0xffffffffu, exn);
+        if (cnt > 0) issue(jn, 0);
+        int buf = 0;
+        while (cnt > 0) {
+            // the next chunk, whose copy overlaps this one's evaluation
+            const int ncnt = take(jn, exn);
+            const bool nexcl = __any_sync(0xffffffffu, exn);
+            if (ncnt > 0) {
+                issue(jn, buf ^ 1);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
             __syncwarp();
-            // the corrected-distance ranges are this launch's in the CORR instance, and only there
-            if (((cfl & kRangeCorr) != 0) != CORR) {
-                __syncwarp();
-                buf ^= 1;
-                continue;
-            }
             // stage this lane's source of the chunk
             if (lane < cnt) {
                 const float* rw = raw + buf * (S::kRaw * 32) + lane;
@@ -972,7 +1005,6 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
                 }
             }
             __syncwarp();
-            const bool excl = (cfl & kRangeExcl) != 0;
     #pragma unroll 1
             for (int jj = g; jj < cnt; jj += 4) {
                 const float4 A = st[jj], B = st[32 + jj];
@@ -1011,7 +1043,7 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
                         dz = __fadd2_rn(dz, __fadd2_rn(tez[m], ez));
                     }
                     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-                    float2 w = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                    float2 w = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
                     float2 num;
                     if (KIND == 3) {
                         // q (t - s) / r^3, three components
@@ -1059,6 +1091,8 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
             }
             __syncwarp();
             buf ^= 1;
+            cnt = ncnt;
+            excl = nexcl;
         }
         gb = ge;
     }
@@ -1669,7 +1703,8 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
             it = cache.erase(it);
             continue;
         }
-        if (t->device == dev && t->p == P.p && t->cut_up == P.cut_up && t->cut_dn == P.cut_dn && t->fp64 == P.fp64 &&
+        if (t->device == dev && t->p == P.p && t->cut_up == P.cut_up && t->cut_dn == P.cut_dn &&
+            t->cap_up == P.cap_up && t->cap_dn == P.cap_dn && t->fp64 == P.fp64 &&
             t->cheb == P.cheb &&
             t->centered == centered) {
             P.ops = t;
@@ -1682,6 +1717,8 @@ int get_tables(Plan& P, const HostPinv& h, cudaStream_t s) {
     t->p = P.p;
     t->cut_up = P.cut_up;
     t->cut_dn = P.cut_dn;
+    t->cap_up = P.cap_up;
+    t->cap_dn = P.cap_dn;
     t->cheb = P.cheb;
     t->fp64 = P.fp64;
     t->centered = centered;
@@ -1763,12 +1800,17 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         t_last = now;
         return KIFMM_OK;
     };
-    // the Chebyshev engine has no pseudo-inverses (its order only picks the surface
-    // operators computed here, which it leaves unused)
-    const HostPinv& h = host_pinv(P.cheb ? 2 : P.p, P.cut_up, P.cut_dn);
+    // mixed form: ranks capped at 256, the rows one tensor-core work item covers, so that
+    // M2L'' and L2L'' (and for kernels other than DL M2M'') take one row group; the
+    // double layer keeps its larger upward rank (dipole sources need it).  The
+    // Chebyshev engine has no pseudo-inverses (its order only picks the surface
+    // operators computed here, which it leaves unused).
+    P.fp64 = P.prec == KIFMM_PREC_FP64;
+    P.cap_dn = P.fp64 || P.cheb ? 0 : kMixedMaxRank;
+    P.cap_up = P.fp64 || P.cheb || P.kernel == KIFMM_KERNEL_DL ? 0 : kMixedMaxRank;
+    const HostPinv& h = host_pinv(P.cheb ? 2 : P.p, P.cut_up, P.cut_dn, P.cap_up, P.cap_dn);
     P.Q = P.cheb ? P.p * P.p * P.p : h.Q;
     P.Qp = (P.Q + 15) / 16 * 16;
-    P.fp64 = P.prec == KIFMM_PREC_FP64;
     KF_TRY(P.err.alloc(1));
     KF_CHECK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), s));
 

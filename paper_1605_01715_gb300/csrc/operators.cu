@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -46,7 +47,7 @@ std::vector<double> surface_points(int p) {
 // (Hestenes): rotate column pairs of A until mutually orthogonal, A V = U S.
 // Pairs are visited in round-robin order so each round's rotations are disjoint.
 std::vector<double> pinv_jacobi(const std::vector<double>& A_rm, int n, double cutoff, std::vector<double>* U,
-                                std::vector<double>* W, int* rank) {
+                                std::vector<double>* W, int* rank, int max_rank) {
     std::vector<double> a((size_t)n * n), v((size_t)n * n, 0.0);  // column-major
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) a[(size_t)j * n + i] = A_rm[(size_t)i * n + j];
@@ -105,8 +106,15 @@ std::vector<double> pinv_jacobi(const std::vector<double>& A_rm, int n, double c
         smax = std::max(smax, sig[j]);
     }
     // pinv = V diag(1/s) U^T with u_j = a_j / s_j  =>  pinv[r][c] = sum_j v[r][j] a[c][j] / s_j^2
+    // kept: s_j > cutoff s_max, and at most max_rank of them (the largest) when max_rank > 0
+    double thresh = cutoff * smax;
+    if (max_rank > 0) {
+        std::vector<double> s(sig);
+        std::sort(s.begin(), s.end(), std::greater<double>());
+        if ((int)s.size() > max_rank && s[max_rank] > thresh) thresh = s[max_rank];
+    }
     std::vector<double> w(n);
-    for (int j = 0; j < n; ++j) w[j] = (sig[j] > cutoff * smax) ? 1.0 / (sig[j] * sig[j]) : 0.0;
+    for (int j = 0; j < n; ++j) w[j] = (sig[j] > thresh) ? 1.0 / (sig[j] * sig[j]) : 0.0;
     std::vector<double> P((size_t)n * n);
 #pragma omp parallel for schedule(static)
     for (int r = 0; r < n; ++r)
@@ -148,19 +156,19 @@ static std::vector<double> kernel_matrix(const std::vector<double>& x, double sx
     return K;
 }
 
-const HostPinv& host_pinv(int p, double cut_up, double cut_dn) {
+const HostPinv& host_pinv(int p, double cut_up, double cut_dn, int max_up, int max_dn) {
     static std::mutex mu;
-    static std::map<std::tuple<int, double, double>, HostPinv> cache;
+    static std::map<std::tuple<int, double, double, int, int>, HostPinv> cache;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_tuple(p, cut_up, cut_dn);
+    auto key = std::make_tuple(p, cut_up, cut_dn, max_up, max_dn);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     HostPinv h;
     h.p = p;
     h.surf = surface_points(p);
     h.Q = (int)h.surf.size() / 3;
-    h.Pu = pinv_jacobi(kernel_matrix(h.surf, kUpCheck, h.surf, kUpEquiv), h.Q, cut_up, &h.Uu, &h.Wu, &h.ru);
-    h.Pd = pinv_jacobi(kernel_matrix(h.surf, kDnCheck, h.surf, kDnEquiv), h.Q, cut_dn, &h.Ud, &h.Wd, &h.rd);
+    h.Pu = pinv_jacobi(kernel_matrix(h.surf, kUpCheck, h.surf, kUpEquiv), h.Q, cut_up, &h.Uu, &h.Wu, &h.ru, max_up);
+    h.Pd = pinv_jacobi(kernel_matrix(h.surf, kDnCheck, h.surf, kDnEquiv), h.Q, cut_dn, &h.Ud, &h.Wd, &h.rd, max_dn);
     return cache.emplace(key, std::move(h)).first->second;
 }
 

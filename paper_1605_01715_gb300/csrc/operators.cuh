@@ -26,11 +26,14 @@ struct HostPinv {
 std::vector<double> surface_points(int p);
 // Pseudo-inverse (n x n, row-major) by one-sided Jacobi SVD; U and W (n x rank,
 // row-major) of its factored form when requested.
+// Singular values above cutoff * sigma_max are kept, and at most max_rank of them (the
+// largest) when max_rank > 0.
 std::vector<double> pinv_jacobi(const std::vector<double>& A_rm, int n, double cutoff,
                                 std::vector<double>* U = nullptr, std::vector<double>* W = nullptr,
-                                int* rank = nullptr);
-// Pu truncated at cut_up * sigma_max, Pd at cut_dn * sigma_max; cached per (p, cuts).
-const HostPinv& host_pinv(int p, double cut_up, double cut_dn);
+                                int* rank = nullptr, int max_rank = 0);
+// Pu truncated at cut_up * sigma_max and to at most max_up singular triplets, Pd at
+// cut_dn * sigma_max and max_dn (0: no cap); cached per (p, cuts, caps).
+const HostPinv& host_pinv(int p, double cut_up, double cut_dn, int max_up = 0, int max_dn = 0);
 
 // Column-pivoted Householder QR of A = K(2.95 s_i, 1.05 s_j)^T, the transposed map from
 // the upward equivalent surface to the upward check surface (both Q points of the unit

@@ -7,7 +7,8 @@
 // clock it runs during the measurement.
 //   unit 0  FP32 FMA, scalar (fmaf)                     2 flops per lane-op
 //   unit 1  FP32 FMA, packed pairs (__ffma2_rn)         4 flops per lane-op
-//   unit 2  FP32 reciprocal square root (rsqrtf)        1 op per lane-op
+//   unit 2  FP32 reciprocal square root                 1 op per lane-op
+//           (rsqrt.approx.ftz.f32, the near field's instruction)
 //   unit 3  FP64 FMA (fma)                              2 flops per lane-op
 #include <cuda_runtime.h>
 
@@ -63,7 +64,8 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, float seed, fl
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
-                for (int k = 0; k < kChains; ++k) a[k] = rsqrtf(a[k]);   // x -> x^(-1/2): stays near 1
+                for (int k = 0; k < kChains; ++k)                        // x -> x^(-1/2): stays near 1
+                    asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(a[k]));
         }
         float t = 0.f;
 #pragma unroll

@@ -43,6 +43,7 @@ constexpr int kFamilies = 5;
 struct OpTables {
     int device = 0, p = 0;
     double cut_up = 0, cut_dn = 0;  // truncation of Pu and Pd, relative to sigma_max
+    int cap_up = 0, cap_dn = 0;     // and at most this many singular triplets (0: no cap)
     bool fp64 = true, centered = false;
     bool cheb = false;              // the Chebyshev engine's tables
     int ru = 0, rd = 0, Ku = 0, Kd = 0;
@@ -65,6 +66,7 @@ struct Plan {
     int nc = 1;                     // output components per target (the field: 3)
     bool cheb = false;              // far field by Chebyshev interpolation (p = nodes per dimension)
     double cut_up = 0, cut_dn = 0;  // pseudo-inverse truncations (up: Pu, down: Pd)
+    int cap_up = 0, cap_dn = 0;     // and rank caps (mixed form; 0: none)
     bool fp64 = true;
 
     // translation tables (shared, see OpTables), each Qp x Qp row-major; D2T rows in

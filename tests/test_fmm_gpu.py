@@ -187,6 +187,23 @@ def test_factored_m2l_widths():
         assert mx["s2u_points"] == {6: Q, 8: Q, 10: 384}[p]
 
 
+def test_mixed_ranks_are_capped_at_one_work_item():
+    """From p = 11 on, truncation at 1e-8 keeps more than 256 singular triplets (268 at
+    p = 11, 272 at p = 12).  The mixed form keeps the largest 256 of Pd, and of Pu for
+    every kernel but the double layer, so that one tensor-core work item covers an
+    operator's rows; the FP64 form keeps them all."""
+    from paper_1605_01715_gb300 import Plan, Tree
+    m, h, (xyz, w, nrm), sig, refs = case("sphere")
+    tree = Tree(xyz, max_leaf=40)
+    for p in (11, 12):
+        mx = Plan(tree, kernel="adl", p=p, precision="mixed", trg_nrm=nrm, pinv_cutoff=1e-8).stats()
+        fp = Plan(tree, kernel="adl", p=p, precision="fp64", trg_nrm=nrm, pinv_cutoff=1e-8).stats()
+        dl = Plan(tree, kernel="dl", p=p, precision="mixed", src_nrm=nrm, pinv_cutoff=1e-8).stats()
+        assert (mx["rank_up"], mx["rank_down"]) == (256, 256)
+        assert fp["rank_up"] > 256 and fp["rank_down"] > 256
+        assert dl["rank_up"] == fp["rank_up"] and dl["rank_down"] == 256
+
+
 @pytest.mark.parametrize("kernel", ["sl", "dl", "adl"])
 def test_near_field_units_split_heavy_leaves(kernel):
     """A 5,120-point sphere of radius 0.03 beside a unit sphere of the same point count:
