@@ -1005,7 +1005,8 @@ __device__ __forceinline__ void p2p_pass(int lane, int e0, int e1, const longlon
                 }
             }
             __syncwarp();
-    #pragma unroll 1
+            constexpr int kJJ = (KIND == 1 && CORR) ? 1 : 2;   // two sources in flight; the DL corrected launch would spill
+    #pragma unroll kJJ
             for (int jj = g; jj < cnt; jj += 4) {
                 const float4 A = st[jj], B = st[32 + jj];
                 float4 C, D, F, G, H;
