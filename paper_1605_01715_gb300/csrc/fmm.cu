@@ -1304,9 +1304,21 @@ struct Triple {
     int op, in, out;
 };
 
+// Stable order of tr by op: a counting sort (ops are small non-negative operator ids).
+void sort_by_op(std::vector<Triple>& tr) {
+    int nop = 0;
+    for (const Triple& x : tr) nop = std::max(nop, x.op + 1);
+    std::vector<size_t> at((size_t)nop + 1, 0);
+    for (const Triple& x : tr) ++at[(size_t)x.op + 1];
+    for (int o = 0; o < nop; ++o) at[(size_t)o + 1] += at[(size_t)o];
+    std::vector<Triple> out(tr.size());
+    for (const Triple& x : tr) out[at[(size_t)x.op]++] = x;
+    tr.swap(out);
+}
+
 void make_tiles(std::vector<Triple>& tr, std::vector<int4>& tiles, std::vector<int>& pin,
                 std::vector<int>& pout, int cap) {
-    std::stable_sort(tr.begin(), tr.end(), [](const Triple& a, const Triple& b) { return a.op < b.op; });
+    sort_by_op(tr);
     size_t base = pin.size();
     size_t i = 0;
     while (i < tr.size()) {
@@ -1340,8 +1352,21 @@ void m2l_schedule(std::vector<Triple>& tr, const std::vector<int>& level, int ca
                   std::vector<int>& kcount, int64_t* chain_pairs) {
     *chain_pairs = 0;
     kcount.clear();
-    std::stable_sort(tr.begin(), tr.end(),
-                     [](const Triple& a, const Triple& b) { return a.out != b.out ? a.out < b.out : a.op < b.op; });
+    // order by (target, offset): the V lists arrive target by target, so only each
+    // target's own list needs sorting
+    auto by_out_op = [](const Triple& a, const Triple& b) { return a.out != b.out ? a.out < b.out : a.op < b.op; };
+    bool grouped = true;
+    for (size_t i = 1; i < tr.size() && grouped; ++i) grouped = tr[i - 1].out <= tr[i].out;
+    if (grouped) {
+        for (size_t i = 0; i < tr.size();) {
+            size_t j = i;
+            while (j < tr.size() && tr[j].out == tr[i].out) ++j;
+            std::stable_sort(tr.begin() + i, tr.begin() + j, by_out_op);
+            i = j;
+        }
+    } else {
+        std::stable_sort(tr.begin(), tr.end(), by_out_op);
+    }
     // targets by (level, offsets of the V list), members in box order
     std::map<std::pair<int, std::vector<int>>, std::vector<std::pair<int, size_t>>> groups;
     for (size_t i = 0; i < tr.size();) {
