@@ -343,6 +343,9 @@ def run_kifmm(args):
         line["solve"] = solve_latency(args, device)
     if rank == 0 and args.field_check and inst is None:
         line["demag_sphere_interior"] = demag_interior_field(device)
+    if rank == 0 and ws == 1 and args.extras and inst is None:
+        line["batched"] = batched_summary(device)
+        line["serving"] = serving_summary(args)
     if ws > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -462,6 +465,67 @@ def fp64_plain(wl, tree, xyz, nrm, q, p, idx, ref, ms_mixed, peaks, steps=3):
         got = out.cpu().numpy()[idx]
         res["rel_err_sampled"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     return res
+
+
+def batched_summary(device, steps=20, n_sample=2048):
+    """The batched-instance workload (batch_256: 256 sphere-pack instances, 10.9M
+    points, SL) as one forest, at the order and leaf size the autotuner picks for it
+    (p = 8, leaf 64; `--workload batch_256` reruns the tuning): graph-replayed matvecs
+    and their sampled error against the per-instance oracle."""
+    import torch
+
+    from paper_1605_01715_gb300 import Plan, Tree
+    wl, m, xyz, w, nrm, q = make_inputs("batch_256", device)
+    t0 = time.perf_counter()
+    tree = Tree(xyz, max_leaf=64, instances=wl["instances"])
+    plan = Plan(tree, kernel="sl", p=8, precision="mixed")
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    out = torch.empty_like(q)
+    for _ in range(3):
+        plan.matvec_graph(q, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.matvec_graph(q, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    idx, ref, _, _ = oracle_sample(wl, m, q.cpu().numpy(), n_sample)
+    got = out.cpu().numpy()[idx]
+    st = plan.stats()
+    res = {"workload": "batch_256", "instances": int(len(wl["instances"]) - 1), "n_targets": m.n, "kernel": "sl",
+           "p": 8, "max_leaf": 64, "precision": "mixed", "ms_per_matvec": ms, "targets_per_s": m.n / (ms * 1e-3),
+           "setup_ms": t_setup * 1e3, "m2l_pairs": st["m2l_pairs"], "gpu_launches": st["launches_per_matvec"] * steps,
+           "rel_err_sampled": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), "sampled_targets": int(idx.size)}
+    plan.close()
+    tree.close()
+    return res
+
+
+def serving_summary(args, rate=100.0, n_req=32, n_serial=4):
+    """One point of the serving sweep (`--serve` runs the whole sweep): Poisson
+    arrivals at 100 requests/s of polarization and demag requests of 2k-500k unknowns,
+    served mixed with batching, against the same kind of requests served one at a
+    time in the plain FP64 form."""
+    from paper_1605_01715_gb300.serve import Request, Server, percentiles, serial_baseline
+    reqs = [Request(rid=i, **d) for i, d in enumerate(synth.serve_requests(n_req, rate, 5001))]
+    server = Server(mem_budget=96 << 30, precision="mixed")
+    recs, tot = server.run(reqs)
+    server.close()
+    p50, p99 = percentiles([r["latency"] for r in recs])
+    polar = [r for r in recs if r["kind"] == "polar"]
+    base = [Request(rid=i, **d) for i, d in enumerate(synth.serve_requests(n_serial, 1.0, 5999))]
+    st = serial_baseline(base, precision="fp64")
+    return {"workload": "serve_stream", "rate_req_s": rate, "requests": len(recs),
+            "throughput_req_s": len(recs) / tot["makespan_s"],
+            "unknowns_per_s": sum(r["n"] for r in recs) / tot["makespan_s"], "p50_ms": p50 * 1e3, "p99_ms": p99 * 1e3,
+            "batches": tot["batches"], "peak_batch": tot["peak_batch"], "server_start_s": tot["start_s"],
+            "polar_max_true_rel_residual": max((r["rel_res"] for r in polar), default=None),
+            "polar_failed": sum(1 for r in polar if r["status"] != 0),
+            "serial_fp64": {"requests": len(st), "throughput_req_s": len(st) / float(np.sum(st)),
+                            "mean_service_ms": float(np.mean(st)) * 1e3}}
 
 
 def demag_interior_field(device, n_trg=4096):
@@ -745,6 +809,8 @@ def main():
                     help="skip timing the FP64 plain form of the same matvec")
     ap.add_argument("--no-field-check", dest="field_check", action="store_false",
                     help="skip the interior demagnetizing field of the 1M sphere")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the batched-instance and serving summaries of the default run")
     ap.add_argument("--lean", action="store_true",
                     help="set-up, warm-up and the timed matvecs only, then a short line (for profiler runs)")
     args = ap.parse_args()

@@ -22,6 +22,7 @@
 #include <numeric>
 #include <queue>
 #include <type_traits>
+#include <unordered_map>
 
 #include "cheb.cuh"
 #include "common.cuh"
@@ -1367,19 +1368,33 @@ void m2l_schedule(std::vector<Triple>& tr, const std::vector<int>& level, int ca
     } else {
         std::stable_sort(tr.begin(), tr.end(), by_out_op);
     }
-    // targets by (level, offsets of the V list), members in box order
-    std::map<std::pair<int, std::vector<int>>, std::vector<std::pair<int, size_t>>> groups;
+    // targets by (level, offsets of the V list), members in box order; groups are
+    // visited in the order of their (level, offsets) keys
+    struct KeyHash {
+        size_t operator()(const std::pair<int, std::vector<int>>& k) const {
+            uint64_t h = 1469598103934665603ull ^ (uint64_t)(uint32_t)k.first;
+            for (int x : k.second) h = (h ^ (uint64_t)(uint32_t)x) * 1099511628211ull;
+            return (size_t)h;
+        }
+    };
+    std::unordered_map<std::pair<int, std::vector<int>>, std::vector<std::pair<int, size_t>>, KeyHash> hgroups;
     for (size_t i = 0; i < tr.size();) {
         size_t j = i;
         std::vector<int> sig;
         while (j < tr.size() && tr[j].out == tr[i].out) sig.push_back(tr[j++].op);
-        groups[{level[tr[i].out], sig}].push_back({tr[i].out, i});
+        hgroups[{level[tr[i].out], std::move(sig)}].push_back({tr[i].out, i});
         i = j;
     }
+    std::vector<const std::pair<const std::pair<int, std::vector<int>>, std::vector<std::pair<int, size_t>>>*> groups;
+    groups.reserve(hgroups.size());
+    for (const auto& kv : hgroups)
+        if (kv.second.size() * 4 >= (size_t)cap * 3 && kv.first.second.size() >= 2) groups.push_back(&kv);
+    std::sort(groups.begin(), groups.end(), [](const auto* a, const auto* b) { return a->first < b->first; });
     std::vector<std::vector<int4>> chains;
     std::vector<int> cpin, cpout;
     std::vector<char> chained(tr.size(), 0);
-    for (auto& kv : groups) {
+    for (const auto* kvp : groups) {
+        const auto& kv = *kvp;
         const std::vector<int>& sig = kv.first.second;
         const auto& mem = kv.second;
         for (size_t c0 = 0; c0 < mem.size(); c0 += (size_t)cap) {

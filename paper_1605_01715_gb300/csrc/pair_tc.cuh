@@ -436,7 +436,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
         const int fw = warp - kFoldWarp0, ft = tid - kFoldWarp0 * 32;
         const int quarter = warp & 3, half = fw >> 2;
         const int my_slab = (half * 128) / N, my_col0 = (half * 128) % N;
-        float acc[128];
+        float2 acc[64];                       // columns 2j and 2j+1 of this thread's row
         auto load_meta = [&](int k) {
             const int w = (int)blockIdx.x + k * G;
             const int4 t = tiles[w / mgroups];
@@ -460,7 +460,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
             const bool cont = mgroups == 1 && tiles[w / mgroups].w != 0;
             if (!cont_prev) {
 #pragma unroll
-                for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+                for (int j = 0; j < 64; ++j) acc[j] = make_float2(0.f, 0.f);
             }
             bool ok = true;
             for (int j = 0; j < nfg; ++j) {
@@ -477,11 +477,11 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
                     tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)j0, v);
 #pragma unroll
                     for (int jj = 0; jj < 16; jj += 4) {
+                        // packed FP32x2: the same roundings as two scalar FMAs
                         const float4 sc = osc4[(j0 + jj) >> 2];
-                        acc[j0 + jj] = fmaf(v[jj], sc.x, acc[j0 + jj]);
-                        acc[j0 + jj + 1] = fmaf(v[jj + 1], sc.y, acc[j0 + jj + 1]);
-                        acc[j0 + jj + 2] = fmaf(v[jj + 2], sc.z, acc[j0 + jj + 2]);
-                        acc[j0 + jj + 3] = fmaf(v[jj + 3], sc.w, acc[j0 + jj + 3]);
+                        const int a = (j0 + jj) >> 1;
+                        acc[a] = __ffma2_rn(make_float2(v[jj], v[jj + 1]), make_float2(sc.x, sc.y), acc[a]);
+                        acc[a + 1] = __ffma2_rn(make_float2(v[jj + 2], v[jj + 3]), make_float2(sc.z, sc.w), acc[a + 1]);
                     }
                 }
                 tc_fence_before();
@@ -493,7 +493,7 @@ __device__ __forceinline__ void pair_tc_body(const CUtensorMap& map_hi, const CU
 #pragma unroll
                 for (int j = 0; j < 128; ++j) {
                     const int ob = s_out[my_col0 + j];
-                    if (ob >= 0) atomicAdd(out + (size_t)ob * ostride + row, acc[j]);
+                    if (ob >= 0) atomicAdd(out + (size_t)ob * ostride + row, (j & 1) ? acc[j >> 1].y : acc[j >> 1].x);
                 }
             }
             cont_prev = cont;
