@@ -37,33 +37,27 @@ __global__ void k_split_table(const float* __restrict__ x, __half* __restrict__ 
     lo[i] = __float2half_rn(v - __half2float(h));
 }
 
-// Box b of [b0, b0 + gridDim.x): e[b] = kScaleTop - floor(log2 max_k |v[b][k]|), the
-// power of two bringing its vector into [2^14, 2^15) (0 for an all-zero vector), and
+// Box b of [b0, b1), one warp per box: e[b] = kScaleTop - floor(log2 max_k |v[b][k]|),
+// the power of two bringing its vector into [2^14, 2^15) (0 for an all-zero vector), and
 // hi[b][k] + lo[b][k] = v[b][k] * 2^e[b] as two nearest FP16 values; columns past Q zero.
-__global__ void k_box_split(const float* __restrict__ v, int Q, int Qp, int b0, __half* __restrict__ hi,
-                            __half* __restrict__ lo, int* __restrict__ e) {
-    __shared__ float red[128];
-    __shared__ float s_scale;
-    const int b = b0 + blockIdx.x;
+constexpr int kSplitWarps = 8;
+__global__ void __launch_bounds__(32 * kSplitWarps) k_box_split(const float* __restrict__ v, int Q, int Qp, int b0,
+                                                                int b1, __half* __restrict__ hi,
+                                                                __half* __restrict__ lo, int* __restrict__ e) {
+    const int lane = threadIdx.x & 31;
+    const int b = b0 + (int)blockIdx.x * kSplitWarps + (int)(threadIdx.x >> 5);
+    if (b >= b1) return;                      // whole warp; no block-wide barrier below
     const float* vb = v + (size_t)b * Qp;
     float m = 0.f;
-    for (int k = threadIdx.x; k < Q; k += blockDim.x) m = fmaxf(m, fabsf(vb[k]));
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int o = 64; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        int ex = 0;
-        if (red[0] > 0.f) ex = tc::kScaleTop - ilogbf(red[0]);
-        ex = max(-100, min(100, ex));
-        e[b] = ex;
-        s_scale = tc::pow2f(ex);
-    }
-    __syncthreads();
-    const float sc = s_scale;
-    for (int k = threadIdx.x; k < Qp; k += blockDim.x) {
+    for (int k = lane; k < Q; k += 32) m = fmaxf(m, fabsf(vb[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int ex = 0;
+    if (m > 0.f) ex = tc::kScaleTop - ilogbf(m);
+    ex = max(-100, min(100, ex));
+    if (lane == 0) e[b] = ex;
+    const float sc = tc::pow2f(ex);
+    for (int k = lane; k < Qp; k += 32) {
         const float x = k < Q ? vb[k] * sc : 0.f;
         const __half h = __float2half_rn(x);
         hi[(size_t)b * Qp + k] = h;
@@ -123,7 +117,7 @@ int tc_split_table(const float* table, __half* hi, __half* lo, size_t n, int* te
 // Per-box scales and FP16 hi/lo splits of boxes [b0, b1) of a check-potential buffer.
 int tc_box_split(const float* v, int Q, int Qp, int b0, int b1, __half* hi, __half* lo, int* e, cudaStream_t s) {
     if (b1 <= b0) return KIFMM_OK;
-    k_box_split<<<b1 - b0, 128, 0, s>>>(v, Q, Qp, b0, hi, lo, e);
+    k_box_split<<<(b1 - b0 + kSplitWarps - 1) / kSplitWarps, 32 * kSplitWarps, 0, s>>>(v, Q, Qp, b0, b1, hi, lo, e);
     KF_CHECK_LAUNCH();
     return KIFMM_OK;
 }
