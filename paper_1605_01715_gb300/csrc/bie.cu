@@ -28,6 +28,7 @@
 
 namespace kifmm {
 int plan_matvec(Plan& P, const double* q, double* out, cudaStream_t s);
+int plan_matvec_graph(Plan& P, const double* q, double* out, cudaStream_t s);
 }
 
 using namespace kifmm;
@@ -128,22 +129,39 @@ __global__ void k_rhs(const double* __restrict__ nrm, const double* __restrict__
 // Dot products: block b sums V_j . w over the range [lo_b, hi_b) of one instance
 // (ranges never straddle two instances) into partial[b nv + j]; the final pass adds the
 // blocks of instance i into h[i hld + j].
-__global__ void k_dots(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w,
-                       const int64_t* __restrict__ blo, const int64_t* __restrict__ bhi,
-                       double* __restrict__ partial) {
-    __shared__ double red[256];
+__global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, int64_t ld, int nv,
+                                              const double* __restrict__ w, const int64_t* __restrict__ blo,
+                                              const int64_t* __restrict__ bhi, double* __restrict__ partial) {
+    // eight vectors per pass over the block's range of w; per pass a warp-shuffle
+    // reduction of the eight sums, then one across the block's warps
+    constexpr int G = 8;
+    __shared__ double red[8][G];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t lo = blo[blockIdx.x], hi = bhi[blockIdx.x];
-    for (int i = 0; i < nv; ++i) {
-        const double* v = V + (size_t)i * ld;
-        double s = 0;
-        for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) s += v[t] * w[t];
-        red[threadIdx.x] = s;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
+    for (int i0 = 0; i0 < nv; i0 += G) {
+        const int m = nv - i0 < G ? nv - i0 : G;
+        double s[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) s[j] = 0.0;
+        for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+            const double wt = w[t];
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                if (j < m) s[j] += V[(size_t)(i0 + j) * ld + t] * wt;
         }
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * nv + i] = red[0];
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
+        if (lane == 0)
+#pragma unroll
+            for (int j = 0; j < G; ++j) red[warp][j] = s[j];
+        __syncthreads();
+        if (threadIdx.x < m) {
+            double a = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q][threadIdx.x];
+            partial[(size_t)blockIdx.x * nv + i0 + threadIdx.x] = a;
+        }
         __syncthreads();
     }
 }
@@ -208,11 +226,13 @@ struct Gmres {
     int64_t n;
     cudaStream_t s;
     double* qbuf;
+    bool graph = false;              // replay the plan's captured matvec (fixed qbuf and y)
 
     int apply(const double* x, double* y) {
         k_mul<<<div_up(n, 256), 256, 0, s>>>(x, area, n, qbuf);
         KF_CHECK_LAUNCH();
-        KF_TRY(plan_matvec(P, qbuf, y, s));
+        if (graph) KF_TRY(plan_matvec_graph(P, qbuf, y, s));
+        else KF_TRY(plan_matvec(P, qbuf, y, s));
         k_polar_combine<<<div_up(n, 256), 256, 0, s>>>(x, area, eps_in, eps_out, curv, n, y);
         KF_CHECK_LAUNCH();
         return KIFMM_OK;
@@ -394,7 +414,7 @@ struct Solver {
            const double* b_, double* x_, double tol_, int m_, int max_iter_)
         : P(P_), area(area_), eps_in(eps_in_), curv(curv_), b(b_), x(x_), eps_out(eps_out_), tol(tol_),
           m(m_), max_iter(max_iter_), n(P_.tree->t.nt), ni(1), hld(m_ + 2),
-          g{P_, area_, eps_in_, curv_, eps_out_, P_.tree->t.nt, nullptr, nullptr} {
+          g{P_, area_, eps_in_, curv_, eps_out_, P_.tree->t.nt, nullptr, nullptr, true} {
         const Tree& T = P_.tree->t;
         if (T.forest_level >= 0 && T.inst_off.size() >= 2) ni = (int)T.inst_off.size() - 1;
     }
@@ -536,10 +556,10 @@ struct Solver {
             KF_TRY(dots(b, 0, 1, b, dA(), 1, s));
             KF_CHECK_CUDA(cudaMemcpyAsync(ha(), dA(), ni * sizeof(double), cudaMemcpyDeviceToHost, s));
         } else if (step == kRestart || step == kFinal) {
-            // r = b - A x (restart: into v_0)
-            KF_TRY(g.apply(x, r));
+            // r = b - A x (restart: into v_0); A x into w, the matvec's one output buffer
+            KF_TRY(g.apply(x, w));
             double* dst = step == kRestart ? V : r;
-            k_axpby<<<div_up(n, 256), 256, 0, s>>>(1.0, b, -1.0, r, n, dst);
+            k_axpby<<<div_up(n, 256), 256, 0, s>>>(1.0, b, -1.0, w, n, dst);
             KF_CHECK_LAUNCH();
             KF_TRY(dots(dst, 0, 1, dst, dA(), 1, s));
             KF_CHECK_CUDA(cudaMemcpyAsync(ha(), dA(), ni * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -2695,17 +2695,23 @@ int ensure_host_io(Plan& P, cudaStream_t s) {
 }  // namespace
 }  // namespace kifmm
 
-extern "C" int kifmm_fmm_matvec_graph(kifmm_plan plan, const double* q, double* out, void* stream) {
-    clear_error();
-    KF_ARG(plan && q && out, "NULL plan, q or out");
-    Plan& P = plan->P;
+namespace kifmm {
+// The matvec as a replay of its captured launches (captured again when q or out change).
+int plan_matvec_graph(Plan& P, const double* q, double* out, cudaStream_t s) {
     if (!P.gexec || P.g_q != q || P.g_out != out) {
         KF_TRY(capture_matvec(P, q, out, &P.gexec));
         P.g_q = q;
         P.g_out = out;
     }
-    KF_CHECK_CUDA(cudaGraphLaunch(P.gexec, (cudaStream_t)stream));
+    KF_CHECK_CUDA(cudaGraphLaunch(P.gexec, s));
     return KIFMM_OK;
+}
+}  // namespace kifmm
+
+extern "C" int kifmm_fmm_matvec_graph(kifmm_plan plan, const double* q, double* out, void* stream) {
+    clear_error();
+    KF_ARG(plan && q && out, "NULL plan, q or out");
+    return plan_matvec_graph(plan->P, q, out, (cudaStream_t)stream);
 }
 
 extern "C" int kifmm_fmm_matvec_host(kifmm_plan plan, const double* q, double* out, int graph, void* stream) {
