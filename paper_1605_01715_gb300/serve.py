@@ -164,7 +164,7 @@ class Server:
     Batches are set up on a worker thread (the library's calls release the GIL), so
     the scheduler keeps stepping the live batches meanwhile."""
 
-    def __init__(self, mem_budget=64 << 30, p=None, max_leaf=64, precision="mixed", tol=1e-6, restart=50,
+    def __init__(self, mem_budget=64 << 30, p=None, max_leaf=96, precision="mixed", tol=1e-6, restart=50,
                  max_iter=500, max_live=64, max_batch=64, max_batch_points=4 << 20, setup_workers=2,
                  device="cuda:0"):
         self.mem_budget = int(mem_budget)
@@ -308,7 +308,7 @@ class Server:
                          peak_batch=peak_batch, setup_s=setup_total, start_s=self.start_s)
 
 
-def serial_baseline(requests, p=None, max_leaf=64, precision="fp64", tol=1e-6, restart=50, max_iter=500,
+def serial_baseline(requests, p=None, max_leaf=96, precision="fp64", tol=1e-6, restart=50, max_iter=500,
                     device="cuda:0"):
     """The same requests one at a time -- set up, solved (or evaluated) to the end and
     released before the next starts, the plain FP64 form by default, with the operator

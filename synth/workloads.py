@@ -7,12 +7,15 @@ Sizes follow the configurations the library is benchmarked and tested on:
                       densities U[-1,1], p=6, at most 64 points per leaf.
 * ``demag_cube_1m``   unit cube, n=296 per face (1,051,392 triangles), double
                       layer with density n.M, M = z-hat, p=10 (p=8 misses 1e-6),
-                      both pseudo-inverses truncated at 1e-8 (enough on flat faces).
-* ``demag_sphere_1m`` unit geodesic sphere f=229 (1,048,820 triangles), same.
+                      both pseudo-inverses truncated at 1e-8 (enough on flat faces),
+                      at most 128 points per leaf.
+* ``demag_sphere_1m`` unit geodesic sphere f=229 (1,048,820 triangles), same
+                      (default truncations).
 * ``polar_64``        64 spheres, radii U[0.5,1.5], centres in a 20^3 box with a
                       0.05 surface gap, f=23 (10,580 triangles each, 677,120
                       unknowns), contrast eps_in/eps_out U[2,20], E0 = z-hat; adjoint
-                      double layer at p=11 (p=10 reaches only about 1e-6).
+                      double layer at p=11 (p=10 reaches only about 1e-6), at most 96
+                      points per leaf.
 * ``batch_256``       256 independent instances of 1-64 spheres (radii U[0.5,1.5],
                       packed at the density of polar_64), each of a total size
                       log-uniform in 1k-200k triangles (about 10M in all),
@@ -42,24 +45,24 @@ def _sl_sphere_20k():
 
 def _demag_cube_1m():
     m = cube_surface(296)
-    return dict(mesh=m, kernel="dl", p=10, max_leaf=64, magnetization=(0.0, 0.0, 1.0), pinv_cutoff=1e-8)
+    return dict(mesh=m, kernel="dl", p=10, max_leaf=128, magnetization=(0.0, 0.0, 1.0), pinv_cutoff=1e-8)
 
 
 def _demag_cube_270k():
     m = cube_surface(150)
-    return dict(mesh=m, kernel="dl", p=10, max_leaf=64, magnetization=(0.0, 0.0, 1.0))
+    return dict(mesh=m, kernel="dl", p=10, max_leaf=128, magnetization=(0.0, 0.0, 1.0))
 
 
 def _demag_sphere_1m():
     m = geodesic_sphere(229)
-    return dict(mesh=m, kernel="dl", p=10, max_leaf=64, magnetization=(0.0, 0.0, 1.0))
+    return dict(mesh=m, kernel="dl", p=10, max_leaf=128, magnetization=(0.0, 0.0, 1.0))
 
 
 def _polar_64():
     c, r = sphere_pack(64, 0.5, 1.5, 20.0, 0.05, seed=3000)
     m = pack_mesh(c, r, 23)
     contrast = np.random.default_rng(3001).uniform(2.0, 20.0, size=64)
-    return dict(mesh=m, kernel="adl", p=11, max_leaf=64, centres=c, radii=r,
+    return dict(mesh=m, kernel="adl", p=11, max_leaf=96, centres=c, radii=r,
                 contrast=contrast, eps_out=1.0, e0=(0.0, 0.0, 1.0))
 
 
