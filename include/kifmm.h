@@ -284,6 +284,10 @@ typedef struct {
                                          near-field units, [2] translation tiles, [3]
                                          evaluation rows, [4] the total                    */
     int64_t near_axis_pairs;          /* mixed DL: the pairs of those axis units         */
+    int64_t near_zero_pairs;          /* mixed DL: pairs left out because they add exactly
+                                         zero -- a source range coplanar with its target
+                                         leaf along the dipoles' axis (n.(x - y) = 0);
+                                         not in near_pairs                               */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);

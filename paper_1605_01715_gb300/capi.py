@@ -59,7 +59,8 @@ class PlanStats(ctypes.Structure):
                 ("s2u_points", ctypes.c_int32), ("m2l_chain_pairs", ctypes.c_int64),
                 ("pinv_cutoff_up", ctypes.c_double), ("near_corr_ranges", ctypes.c_int64),
                 ("near_pairs", ctypes.c_int64), ("near_axis_units", ctypes.c_int32),
-                ("setup_ms", ctypes.c_double * 5), ("near_axis_pairs", ctypes.c_int64)]
+                ("setup_ms", ctypes.c_double * 5), ("near_axis_pairs", ctypes.c_int64),
+                ("near_zero_pairs", ctypes.c_int64)]
 
 
 def _as_dict(st):

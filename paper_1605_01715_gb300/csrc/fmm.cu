@@ -2026,6 +2026,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         const int nr = (int)ranges.size();
         std::vector<int4> hcu;
         std::vector<longlong2> hcr;
+        std::vector<int> hcr_of;                 // the range each corrected entry copies
         if (nr > 0) {
             DBuf<longlong2> dr;
             DBuf<int> drl;
@@ -2050,11 +2051,10 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                     ranges[r].x |= kRangeCorr;
                     hcu.push_back(make_int4(rleaf[r], (int)hcr.size(), (int)hcr.size() + 1, kUnitSplit));
                     hcr.push_back(ranges[r]);
+                    hcr_of.push_back(r);
                 }
             }
         }
-        P.near_pairs = 0;
-        for (const Unit& u : units) P.near_pairs += u.work;
         // double layer: units whose sources' dipoles all lie along one coordinate axis take
         // the one-term kernel (KIND 4), dealt after the others
         std::vector<char> is_axis(units.size(), 0);
@@ -2084,7 +2084,71 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                     units[i].u.w |= k << 8;
                 }
             }
+            // Coplanar ranges: in an axis unit whose leaf's targets all share one
+            // coordinate c along the dipoles' axis, a range whose sources have that
+            // coordinate too adds exactly zero (n.(x - y) = 0 for every pair, in any
+            // precision): the range is dropped.  (A flat face's interior leaves.)
+            std::vector<char> drop(ranges.size(), 0);
+            bool any_axis = false;
+            for (char a : is_axis) any_axis |= a != 0;
+            if (any_axis) {
+                std::vector<double> hs, ht;
+                KF_TRY(download(hs, T.sxyz.p, 3 * (size_t)T.ns, s));
+                if (!T.same) KF_TRY(download(ht, T.txyz.p, 3 * (size_t)T.nt, s));
+                const std::vector<double>& tc = T.same ? hs : ht;
+                const int64_t ntp = T.same ? T.ns : T.nt;
+                for (size_t i = 0; i < units.size(); ++i) {
+                    if (!is_axis[i]) continue;
+                    const int k = (units[i].u.w >> 8) & 3;
+                    const int b = tleaf[units[i].u.x];
+                    const int64_t t0 = T.h_rng[4 * b + 2], t1 = T.h_rng[4 * b + 3];
+                    if (t1 <= t0) continue;
+                    const double c = tc[(size_t)k * ntp + t0];
+                    bool flat = true;
+                    for (int64_t q = t0; q < t1 && flat; ++q) flat = tc[(size_t)k * ntp + q] == c;
+                    if (!flat) continue;
+                    for (int r = units[i].u.y; r < units[i].u.z; ++r) {
+                        const int64_t j0 = ranges[r].x & kRangeIdx, j1 = ranges[r].y;
+                        bool zero = true;
+                        for (int64_t j = j0; j < j1 && zero; ++j) zero = hs[(size_t)k * T.ns + j] == c;
+                        if (zero) drop[r] = 1;
+                    }
+                }
+            }
+            // compact: units keep their place (an emptied unit still writes its
+            // targets' zero near sums), their work drops with the ranges
+            std::vector<longlong2> kept;
+            kept.reserve(ranges.size());
+            P.near_zero_pairs = 0;
+            for (Unit& u : units) {
+                const int b = tleaf[u.u.x];
+                const int64_t ntg = T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2];
+                const int y = (int)kept.size();
+                for (int r = u.u.y; r < u.u.z; ++r) {
+                    if (drop[r]) {
+                        const int64_t pairs = ntg * (ranges[r].y - (ranges[r].x & kRangeIdx));
+                        u.work -= pairs;
+                        P.near_zero_pairs += pairs;
+                    } else {
+                        kept.push_back(ranges[r]);
+                    }
+                }
+                u.u.y = y;
+                u.u.z = (int)kept.size();
+            }
+            ranges.swap(kept);
+            std::vector<int4> cu;
+            std::vector<longlong2> cr;
+            for (size_t e = 0; e < hcr.size(); ++e) {
+                if (drop[hcr_of[e]]) continue;
+                cu.push_back(make_int4(hcu[e].x, (int)cr.size(), (int)cr.size() + 1, hcu[e].w));
+                cr.push_back(hcr[e]);
+            }
+            hcu.swap(cu);
+            hcr.swap(cr);
         }
+        P.near_pairs = 0;
+        for (const Unit& u : units) P.near_pairs += u.work;
         std::vector<size_t> ord(units.size());
         std::iota(ord.begin(), ord.end(), 0);
         std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {
@@ -2808,6 +2872,7 @@ extern "C" int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* st) {
     st->m2l_chain_pairs = P.m2l_chain_pairs;
     for (int k = 0; k < 5; ++k) st->setup_ms[k] = P.setup_ms[k];
     st->near_axis_pairs = P.near_axis_pairs;
+    st->near_zero_pairs = P.near_zero_pairs;
     return KIFMM_OK;
 }
 

@@ -103,6 +103,7 @@ struct Plan {
     int n_p2p_corr = 0;
     int n_p2p_axis = 0;                   // DL: the last units of p2p_units, dipoles along one axis
     int64_t near_axis_pairs = 0;          // their (target, source) pairs
+    int64_t near_zero_pairs = 0;          // DL: coplanar pairs dropped (exact zeros)
     bool p2p_multi = false;               // some leaf spans several units
     int n_s2u = 0, n_p2l = 0, n_tleaf = 0;
     int64_t n_xpairs = 0;
