@@ -272,8 +272,8 @@ typedef struct {
                                          than 1/32 of the range's extent or within 4x the
                                          tolerance radius, evaluated with the distance
                                          corrected for the FP32 offsets' rounding         */
-    int64_t near_pairs;               /* mixed: (target, source) pairs of the near field
-                                         (U, W and leaf X lists) per matvec              */
+    int64_t near_pairs;               /* (target, source) pairs of the near field (U, W
+                                         and leaf X lists) per matvec                    */
     int32_t near_axis_units;          /* mixed DL: near-field units whose source normals
                                          all lie along one coordinate axis (flat faces
                                          normal to an axis), evaluated with the one-term
@@ -284,10 +284,11 @@ typedef struct {
                                          near-field units, [2] translation tiles, [3]
                                          evaluation rows, [4] the total                    */
     int64_t near_axis_pairs;          /* mixed DL: the pairs of those axis units         */
-    int64_t near_zero_pairs;          /* mixed DL: pairs left out because they add exactly
-                                         zero -- a source range coplanar with its target
-                                         leaf along the dipoles' axis (n.(x - y) = 0);
-                                         not in near_pairs                               */
+    int64_t near_zero_pairs;          /* DL: pairs left out because they add exactly
+                                         zero -- a source box whose dipoles all lie along
+                                         one coordinate axis and whose points all share
+                                         the target leaf's coordinate along it
+                                         (n.(x - y) = 0); not in near_pairs            */
 } kifmm_plan_stats;
 
 int kifmm_plan_get_stats(kifmm_plan plan, kifmm_plan_stats* stats);

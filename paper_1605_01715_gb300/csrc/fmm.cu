@@ -1137,6 +1137,12 @@ k_p2p_warp(const int* __restrict__ leaves, int nunits, const int4* __restrict__ 
     const int b = leaves[u.x];
     const float4 cb0 = bcf[3 * b], cb1 = bcf[3 * b + 1];   // leaf centre, FP32 hi and lo
     const int64_t tb = rng[4 * b + 2], te = rng[4 * b + 3];
+    if (!CORR && u.y == u.z) {                    // no sources (all exact zeros): the far field alone
+        constexpr int NC = KIND == 3 ? 3 : 1;     // the leaf's only unit, so a plain store
+        for (int64_t t = tb + lane; t < te; t += 32)
+            for (int c = 0; c < NC; ++c) out[tperm[t] + c * nt] = res ? (double)res[t + c * nt] : 0.0;
+        return;
+    }
     float4* st = p2p_smem + warp * (S::kStage * 32 + S::kRaw * 16);
     float* raw = reinterpret_cast<float*>(st + S::kStage * 32);
     constexpr int kMaxT = CORR ? S::kMaxTCorr : S::kMaxT;
@@ -1909,6 +1915,53 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     // work lists (host bookkeeping over the tree's lists)
     std::vector<int> s2u_box, s2u_off{0}, s2u_idx, p2l_box, p2l_off{0}, p2l_idx, tleaf, p2p_off{0}, p2p_idx;
     std::vector<int> tleaf_of(T.nt, 0);
+    // Double layer: a near-field source box whose dipoles all lie along one coordinate
+    // axis and whose points share one coordinate c along it adds exactly zero to a
+    // target leaf whose targets all have that coordinate c too (n.(x - y) = 0 for every
+    // pair, in any precision; the interior of a flat face).  Such boxes are left out of
+    // the near-field lists, detected by exact equality.
+    P.near_zero_pairs = 0;
+    P.near_pairs = 0;
+    std::vector<double> hsx, hsn, htx;
+    std::vector<signed char> plane_k;           // per box: the axis, -1 none, -2 not yet known
+    std::vector<double> plane_c;
+    if (P.kernel == KIFMM_KERNEL_DL && T.ns > 0) {
+        KF_TRY(download(hsx, T.sxyz.p, 3 * (size_t)T.ns, s));
+        KF_TRY(download(hsn, P.snrm.p, 3 * (size_t)T.ns, s));
+        if (!T.same && T.nt > 0) KF_TRY(download(htx, T.txyz.p, 3 * (size_t)T.nt, s));
+        plane_k.assign(T.nbox, -2);
+        plane_c.assign(T.nbox, 0.0);
+    }
+    auto src_plane = [&](int a) -> int {        // the box's plane axis (its coordinate in plane_c)
+        if (plane_k[a] != -2) return plane_k[a];
+        int k = -1;
+        const int64_t j0 = T.h_rng[4 * a], j1 = T.h_rng[4 * a + 1];
+        if (j1 > j0) {
+            for (int d = 0; d < 3; ++d)
+                if (hsn[(size_t)d * T.ns + j0] != 0.0 && hsn[(size_t)((d + 1) % 3) * T.ns + j0] == 0.0 &&
+                    hsn[(size_t)((d + 2) % 3) * T.ns + j0] == 0.0)
+                    k = d;
+            const double c = k >= 0 ? hsx[(size_t)k * T.ns + j0] : 0.0;
+            for (int64_t j = j0; j < j1 && k >= 0; ++j)
+                if (hsn[(size_t)((k + 1) % 3) * T.ns + j] != 0.0 || hsn[(size_t)((k + 2) % 3) * T.ns + j] != 0.0 ||
+                    hsn[(size_t)k * T.ns + j] == 0.0 || hsx[(size_t)k * T.ns + j] != c)
+                    k = -1;
+            plane_c[a] = c;
+        }
+        plane_k[a] = (signed char)k;
+        return k;
+    };
+    auto zero_pair = [&](int b, int a) -> bool {  // source box a adds exactly zero to leaf b
+        if (plane_k.empty()) return false;
+        const int k = src_plane(a);
+        if (k < 0) return false;
+        const std::vector<double>& tx = T.same ? hsx : htx;
+        const int64_t ntp = T.same ? T.ns : T.nt;
+        const double c = plane_c[a];
+        for (int64_t q = T.h_rng[4 * b + 2]; q < T.h_rng[4 * b + 3]; ++q)
+            if (tx[(size_t)k * ntp + q] != c) return false;
+        return true;
+    };
     for (int b = 0; b < T.nbox; ++b) {
         int l = T.h_lvl[b];
         if (T.h_leaf[b] && has_src(T, b) && l >= 2) {
@@ -1931,10 +1984,19 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         }
         if (T.h_leaf[b] && has_trg(T, b)) {
             tleaf.push_back(b);
-            for (int k = T.h_u_off[b]; k < T.h_u_off[b + 1]; ++k) p2p_idx.push_back(T.h_u_idx[k]);
-            for (int k = T.h_w_off[b]; k < T.h_w_off[b + 1]; ++k) p2p_idx.push_back(T.h_w_idx[k]);
+            auto add = [&](int a) {
+                const int64_t pairs = ntb * (T.h_rng[4 * a + 1] - T.h_rng[4 * a]);
+                if (zero_pair(b, a)) {
+                    P.near_zero_pairs += pairs;
+                } else {
+                    p2p_idx.push_back(a);
+                    P.near_pairs += pairs;
+                }
+            };
+            for (int k = T.h_u_off[b]; k < T.h_u_off[b + 1]; ++k) add(T.h_u_idx[k]);
+            for (int k = T.h_w_off[b]; k < T.h_w_off[b + 1]; ++k) add(T.h_w_idx[k]);
             if (x_direct)
-                for (int k = T.h_x_off[b]; k < T.h_x_off[b + 1]; ++k) p2p_idx.push_back(T.h_x_idx[k]);
+                for (int k = T.h_x_off[b]; k < T.h_x_off[b + 1]; ++k) add(T.h_x_idx[k]);
             p2p_off.push_back((int)p2p_idx.size());
             for (int64_t t = T.h_rng[4 * b + 2]; t < T.h_rng[4 * b + 3]; ++t) tleaf_of[t] = b;
             P.max_trg_leaf = std::max<int>(P.max_trg_leaf, (int)(T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2]));
@@ -2026,7 +2088,6 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         const int nr = (int)ranges.size();
         std::vector<int4> hcu;
         std::vector<longlong2> hcr;
-        std::vector<int> hcr_of;                 // the range each corrected entry copies
         if (nr > 0) {
             DBuf<longlong2> dr;
             DBuf<int> drl;
@@ -2051,7 +2112,6 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                     ranges[r].x |= kRangeCorr;
                     hcu.push_back(make_int4(rleaf[r], (int)hcr.size(), (int)hcr.size() + 1, kUnitSplit));
                     hcr.push_back(ranges[r]);
-                    hcr_of.push_back(r);
                 }
             }
         }
@@ -2084,71 +2144,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                     units[i].u.w |= k << 8;
                 }
             }
-            // Coplanar ranges: in an axis unit whose leaf's targets all share one
-            // coordinate c along the dipoles' axis, a range whose sources have that
-            // coordinate too adds exactly zero (n.(x - y) = 0 for every pair, in any
-            // precision): the range is dropped.  (A flat face's interior leaves.)
-            std::vector<char> drop(ranges.size(), 0);
-            bool any_axis = false;
-            for (char a : is_axis) any_axis |= a != 0;
-            if (any_axis) {
-                std::vector<double> hs, ht;
-                KF_TRY(download(hs, T.sxyz.p, 3 * (size_t)T.ns, s));
-                if (!T.same) KF_TRY(download(ht, T.txyz.p, 3 * (size_t)T.nt, s));
-                const std::vector<double>& tc = T.same ? hs : ht;
-                const int64_t ntp = T.same ? T.ns : T.nt;
-                for (size_t i = 0; i < units.size(); ++i) {
-                    if (!is_axis[i]) continue;
-                    const int k = (units[i].u.w >> 8) & 3;
-                    const int b = tleaf[units[i].u.x];
-                    const int64_t t0 = T.h_rng[4 * b + 2], t1 = T.h_rng[4 * b + 3];
-                    if (t1 <= t0) continue;
-                    const double c = tc[(size_t)k * ntp + t0];
-                    bool flat = true;
-                    for (int64_t q = t0; q < t1 && flat; ++q) flat = tc[(size_t)k * ntp + q] == c;
-                    if (!flat) continue;
-                    for (int r = units[i].u.y; r < units[i].u.z; ++r) {
-                        const int64_t j0 = ranges[r].x & kRangeIdx, j1 = ranges[r].y;
-                        bool zero = true;
-                        for (int64_t j = j0; j < j1 && zero; ++j) zero = hs[(size_t)k * T.ns + j] == c;
-                        if (zero) drop[r] = 1;
-                    }
-                }
-            }
-            // compact: units keep their place (an emptied unit still writes its
-            // targets' zero near sums), their work drops with the ranges
-            std::vector<longlong2> kept;
-            kept.reserve(ranges.size());
-            P.near_zero_pairs = 0;
-            for (Unit& u : units) {
-                const int b = tleaf[u.u.x];
-                const int64_t ntg = T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2];
-                const int y = (int)kept.size();
-                for (int r = u.u.y; r < u.u.z; ++r) {
-                    if (drop[r]) {
-                        const int64_t pairs = ntg * (ranges[r].y - (ranges[r].x & kRangeIdx));
-                        u.work -= pairs;
-                        P.near_zero_pairs += pairs;
-                    } else {
-                        kept.push_back(ranges[r]);
-                    }
-                }
-                u.u.y = y;
-                u.u.z = (int)kept.size();
-            }
-            ranges.swap(kept);
-            std::vector<int4> cu;
-            std::vector<longlong2> cr;
-            for (size_t e = 0; e < hcr.size(); ++e) {
-                if (drop[hcr_of[e]]) continue;
-                cu.push_back(make_int4(hcu[e].x, (int)cr.size(), (int)cr.size() + 1, hcu[e].w));
-                cr.push_back(hcr[e]);
-            }
-            hcu.swap(cu);
-            hcr.swap(cr);
         }
-        P.near_pairs = 0;
-        for (const Unit& u : units) P.near_pairs += u.work;
         std::vector<size_t> ord(units.size());
         std::iota(ord.begin(), ord.end(), 0);
         std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {

@@ -143,19 +143,26 @@ def test_near_field_alone_at_single_layer_accuracy():
 
 def test_coplanar_pairs_are_left_out():
     """On a flat face a dipole along the face normal sees the face's own points at
-    n.(x - y) = 0: the plan leaves those source ranges out of the near field (they add
-    exactly zero) and still matches the oracle; a sphere has no such pairs."""
+    n.(x - y) = 0: the plan leaves those source boxes out of the near field (they add
+    exactly zero), in both precisions, and still matches the oracle; a sphere has no
+    such pairs."""
     from paper_1605_01715_gb300 import Plan, Tree
     for geom, expect in (("cube", True), ("sphere", False)):
         m, h, (xyz, w, nrm), sig, refs = case(geom)
-        plan = Plan(Tree(xyz, max_leaf=64), kernel="dl", p=10, precision="mixed", src_nrm=nrm)
-        st = plan.stats()
-        out = plan.matvec(torch.from_numpy(sig).to(DEV) * w).cpu().numpy()
-        err = rel(out, refs["dl"])
-        print("%s: %d near pairs evaluated, %d coplanar pairs left out, rel-L2 %.2e"
-              % (geom, st["near_pairs"], st["near_zero_pairs"], err))
-        assert (st["near_zero_pairs"] > 0) == expect
-        assert err < 1e-6
+        tree = Tree(xyz, max_leaf=64)
+        seen = []
+        for prec in ("mixed", "fp64"):
+            plan = Plan(tree, kernel="dl", p=10, precision=prec, src_nrm=nrm)
+            st = plan.stats()
+            out = plan.matvec(torch.from_numpy(sig).to(DEV) * w).cpu().numpy()
+            err = rel(out, refs["dl"])
+            print("%s %s: %d near pairs evaluated, %d coplanar pairs left out, rel-L2 %.2e"
+                  % (geom, prec, st["near_pairs"], st["near_zero_pairs"], err))
+            assert (st["near_zero_pairs"] > 0) == expect
+            assert err < 1e-6
+            seen.append((st["near_pairs"], st["near_zero_pairs"]))
+        assert seen[0] == seen[1]
+        assert seen[0][0] + seen[0][1] >= tree.stats()["p2p_pairs"]     # U and W lists, plus leaf X
 
 
 def test_benchmark_geometry_meets_1e6():
