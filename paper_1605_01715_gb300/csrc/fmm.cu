@@ -716,8 +716,10 @@ constexpr int kP2PUnitSrc = 2048;
 // layers always take the warp kernel, in passes, for its exact products.
 constexpr int kP2PWarpMaxLeaf = 64;
 // unit flags (int4 .w): bit 0 the leaf's first unit, bit 1 the leaf spans several units;
-// bits 8..9 the dipoles' axis of a KIND 4 unit
-constexpr int kUnitFirst = 1, kUnitSplit = 2;
+// bits 8..9 the dipoles' axis of a KIND 4 unit; bits 16..30 one plus the unit's one pass
+// of 8 kMaxT targets, or 0 for all of the leaf's targets (the passes of a leaf share no
+// targets, so they are dealt to separate warps: each pass walks all of its sources anyway)
+constexpr int kUnitFirst = 1, kUnitSplit = 2, kUnitPassShift = 16;
 
 // targets per lane per pass (plain and corrected-distance launches) and float4 entries
 // staged per source, by kernel: as many targets as keep each kernel within 128
@@ -1146,8 +1148,11 @@ k_p2p_warp(const int* __restrict__ leaves, int nunits, const int4* __restrict__ 
     float4* st = p2p_smem + warp * (S::kStage * 32 + S::kRaw * 16);
     float* raw = reinterpret_cast<float*>(st + S::kStage * 32);
     constexpr int kMaxT = CORR ? S::kMaxTCorr : S::kMaxT;
-    for (int64_t t0 = tb; t0 < te; t0 += 8 * kMaxT) {
-        const int n = (int)(te - t0 < 8 * kMaxT ? te - t0 : 8 * kMaxT);
+    const int pass = u.w >> kUnitPassShift;
+    const int64_t tf = pass ? tb + (int64_t)(pass - 1) * (8 * kMaxT) : tb;
+    const int64_t tl = pass && tf + 8 * kMaxT < te ? tf + 8 * kMaxT : te;
+    for (int64_t t0 = tf; t0 < tl; t0 += 8 * kMaxT) {
+        const int n = (int)(tl - t0 < 8 * kMaxT ? tl - t0 : 8 * kMaxT);
         const int64_t tend = t0 + n;
         switch ((n + 7) >> 3) {
 #define KF_PASS(TT)                                                                                              \
@@ -2031,6 +2036,26 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         std::vector<double> rext;              // per range: largest coordinate offset of its pairs
         auto half = [&](int box) { return std::ldexp(T.root_h, -T.h_lvl[box]); };
         auto exp_of = [](double ext) { return std::max(-100, std::min(100, std::ilogb(ext * (1.0 + 1e-12)) + 1)); };
+        // DL: a source box's dipole axis (0..2; 3 mixed), so that a leaf's units hold boxes
+        // of one axis each and as many as can take the one-term kernel do (a cube's edges)
+        std::vector<signed char> box_ax;
+        if (P.kernel == KIFMM_KERNEL_DL && !hsn.empty()) box_ax.assign(T.nbox, -1);
+        auto axis_class = [&](int a) -> int {
+            if (box_ax.empty()) return 0;
+            if (box_ax[a] >= 0) return box_ax[a];
+            int k = 3;
+            const int64_t j0 = T.h_rng[4 * a], j1 = T.h_rng[4 * a + 1];
+            for (int d = 0; d < 3 && j1 > j0; ++d)
+                if (hsn[(size_t)d * T.ns + j0] != 0.0) k = k == 3 ? d : 4;
+            if (k == 4) k = 3;
+            for (int64_t j = j0; j < j1 && k < 3; ++j)
+                if (hsn[(size_t)k * T.ns + j] == 0.0 || hsn[(size_t)((k + 1) % 3) * T.ns + j] != 0.0 ||
+                    hsn[(size_t)((k + 2) % 3) * T.ns + j] != 0.0)
+                    k = 3;
+            box_ax[a] = (signed char)k;
+            return k;
+        };
+        std::vector<int> lb;
         for (size_t li = 0; li < tleaf.size(); ++li) {
             const int b = tleaf[li];
             const int64_t ntg = T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2];
@@ -2057,8 +2082,14 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                 r0 = (int)ranges.size();
                 cnt = 0;
             };
-            for (int k = p2p_off[li]; k < p2p_off[li + 1]; ++k) {
-                const int a = p2p_idx[k];
+            lb.assign(p2p_idx.begin() + p2p_off[li], p2p_idx.begin() + p2p_off[li + 1]);
+            if (!box_ax.empty())
+                std::stable_sort(lb.begin(), lb.end(), [&](int x, int y) { return axis_class(x) < axis_class(y); });
+            int cls_cur = -1;
+            for (const int a : lb) {
+                const int cls = axis_class(a);
+                if (cnt > 0 && cls != cls_cur) close_unit();
+                cls_cur = cls;
                 const double ha = half(a);
                 double box_ext = hb;
                 for (int d = 0; d < 3; ++d) {
@@ -2144,6 +2175,40 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
                     units[i].u.w |= k << 8;
                 }
             }
+        }
+        // one unit per pass of the leaf's targets (empty units keep the whole leaf)
+        {
+            auto pass_targets = [&](bool axis) {
+                const int k = axis ? 4 : P.kernel == KIFMM_KERNEL_SL ? 0 : P.kernel == KIFMM_KERNEL_DL ? 1
+                                        : P.kernel == KIFMM_KERNEL_ADL ? 2 : 3;
+                const int mt = k == 0 ? NearShape<0>::kMaxT : k == 1 ? NearShape<1>::kMaxT
+                             : k == 2 ? NearShape<2>::kMaxT : k == 3 ? NearShape<3>::kMaxT : NearShape<4>::kMaxT;
+                return (int64_t)8 * mt;
+            };
+            std::vector<Unit> pu;
+            std::vector<char> pa;
+            pu.reserve(units.size());
+            for (size_t i = 0; i < units.size(); ++i) {
+                const int b = tleaf[units[i].u.x];
+                const int64_t ntg = T.h_rng[4 * b + 3] - T.h_rng[4 * b + 2];
+                const int64_t pt = pass_targets(is_axis[i] != 0);
+                const int64_t np = (ntg + pt - 1) / pt;
+                if (units[i].u.y == units[i].u.z || np <= 1) {
+                    pu.push_back(units[i]);
+                    pa.push_back(is_axis[i]);
+                    continue;
+                }
+                const int64_t per = units[i].work / ntg;      // sources of the unit
+                for (int64_t k = 0; k < np; ++k) {
+                    Unit v = units[i];
+                    v.u.w |= (int)(k + 1) << kUnitPassShift;
+                    v.work = std::min(pt, ntg - k * pt) * per;
+                    pu.push_back(v);
+                    pa.push_back(is_axis[i]);
+                }
+            }
+            units.swap(pu);
+            is_axis.swap(pa);
         }
         std::vector<size_t> ord(units.size());
         std::iota(ord.begin(), ord.end(), 0);
