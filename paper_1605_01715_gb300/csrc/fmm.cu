@@ -200,7 +200,9 @@ k_src2surf(const int* __restrict__ boxes, const int* __restrict__ off, const int
 // centre, as q (2 p.y - |p|^2) / (|p - y| |y| (|p - y| + |y|)) -- exact for the variation
 // across the check surface, which is all a gradient kernel's far field keeps (sd holds
 // 1/|y| and |y| per source; pp the |p|^2 of each packed check point pair).
-template <bool NEAR, bool DIPOLE, int NP, bool DIFF = false>
+// AX (dipoles): 0..2 when every source's dipole lies along that axis -- one term of
+// n . (p - y), the same value as the three-term sum, whose other products are exact zeros.
+template <bool NEAR, bool DIPOLE, int NP, bool DIFF = false, int AX = 3>
 __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const float4* __restrict__ sd, int cnt,
                                            const float2* px, const float2* py, const float2* pz, float2* acc,
                                            const float2* pp = nullptr) {
@@ -220,7 +222,7 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
             const float2 dx = __fadd2_rn(px[m], nx), dy = __fadd2_rn(py[m], ny), dz = __fadd2_rn(pz[m], nz);
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             const float2 inv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-            float2 v;
+            float2 f, w;                                                     // the pair's value f w
             if (DIFF) {
                 // |y|^2 - |p - y|^2 = 2 p.y - |p|^2; |p - y| = r2 inv
                 const float2 dot = __ffma2_rn(pz[m], make_float2(y.z, y.z),
@@ -229,20 +231,35 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
                 const float2 a = __fmul2_rn(r2, inv);
                 const float2 sum = __fadd2_rn(a, qc);                        // |p - y| + |y|
                 const float2 rs = make_float2(__fdividef(1.f, sum.x), __fdividef(1.f, sum.y));
-                v = __fmul2_rn(__fmul2_rn(__fmul2_rn(qa, dp), __fmul2_rn(inv, qb)), rs);
+                f = __fmul2_rn(__fmul2_rn(qa, dp), __fmul2_rn(inv, qb));
+                w = rs;
             } else if (DIPOLE) {
-                const float2 num = __ffma2_rn(qc, dz, __ffma2_rn(qb, dy, __fmul2_rn(qa, dx)));
-                v = __fmul2_rn(num, __fmul2_rn(__fmul2_rn(inv, inv), inv));
+                if (AX == 0) f = __fmul2_rn(qa, dx);
+                else if (AX == 1) f = __fmul2_rn(qb, dy);
+                else if (AX == 2) f = __fmul2_rn(qc, dz);
+                else f = __ffma2_rn(qc, dz, __ffma2_rn(qb, dy, __fmul2_rn(qa, dx)));
+                w = __fmul2_rn(__fmul2_rn(inv, inv), inv);
             } else {
-                v = __fmul2_rn(qa, inv);
+                f = qa;
+                w = inv;
             }
             if (NEAR) {
-                v.x = r2.x >= d2 ? v.x : 0.f;
-                v.y = r2.y >= d2 ? v.y : 0.f;
+                w.x = r2.x >= d2 ? w.x : 0.f;
+                w.y = r2.y >= d2 ? w.y : 0.f;
             }
-            acc[m] = __fadd2_rn(acc[m], v);
+            acc[m] = __ffma2_rn(f, w, acc[m]);
         }
     }
+}
+
+template <bool NEAR, bool DIPOLE, int NP, bool DIFF>
+__device__ __forceinline__ void surf_pairs_ax(int ax, const float4* __restrict__ sp, const float4* __restrict__ sd,
+                                              int cnt, const float2* px, const float2* py, const float2* pz,
+                                              float2* acc, const float2* pp) {
+    if (DIPOLE && ax == 0) surf_pairs<NEAR, DIPOLE, NP, DIFF, 0>(sp, sd, cnt, px, py, pz, acc, pp);
+    else if (DIPOLE && ax == 1) surf_pairs<NEAR, DIPOLE, NP, DIFF, 1>(sp, sd, cnt, px, py, pz, acc, pp);
+    else if (DIPOLE && ax == 2) surf_pairs<NEAR, DIPOLE, NP, DIFF, 2>(sp, sd, cnt, px, py, pz, acc, pp);
+    else surf_pairs<NEAR, DIPOLE, NP, DIFF, 3>(sp, sd, cnt, px, py, pz, acc, pp);
 }
 
 //
@@ -258,7 +275,7 @@ __global__ void __launch_bounds__(NT)
 k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* __restrict__ idx, int down,
          const float4* __restrict__ bcf, const int64_t* __restrict__ rng, const float* __restrict__ sxf, int64_t ns,
          const float* __restrict__ qs, const float* __restrict__ surf, int Q, int Qp, __half* __restrict__ vin_h,
-         __half* __restrict__ vin_l, int* __restrict__ bexp) {
+         __half* __restrict__ vin_l, int* __restrict__ bexp, const int* __restrict__ bax) {
     __shared__ float4 sp[NT];
     __shared__ float4 sd[(DIPOLE || DIFF) ? NT : 1];
     const int b = boxes[blockIdx.x];
@@ -290,6 +307,7 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
         const float dm = fmaxf(fabsf((ah.x - bh.x) + (al.x - bl.x)),
                                fmaxf(fabsf((ah.y - bh.y) + (al.y - bl.y)), fabsf((ah.z - bh.z) + (al.z - bl.z))));
         const bool near = fmaxf(dm - ah.w - rf, rf - dm - ah.w) <= margin;
+        const int ax = (DIPOLE && bax) ? bax[a] : 3;      // the source box's dipole axis, or 3
         for (int64_t j0 = sb; j0 < se; j0 += NT) {
             const int64_t j = j0 + threadIdx.x;
             if (j < se) {
@@ -307,9 +325,9 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
             __syncthreads();
             const int cnt = (int)((se - j0) < (int64_t)NT ? (se - j0) : (int64_t)NT);
             if (near)
-                surf_pairs<true, DIPOLE, NP, DIFF>(sp, sd, cnt, px, py, pz, acc, pp);
+                surf_pairs_ax<true, DIPOLE, NP, DIFF>(ax, sp, sd, cnt, px, py, pz, acc, pp);
             else
-                surf_pairs<false, DIPOLE, NP, DIFF>(sp, sd, cnt, px, py, pz, acc, pp);
+                surf_pairs_ax<false, DIPOLE, NP, DIFF>(ax, sp, sd, cnt, px, py, pz, acc, pp);
             __syncthreads();
         }
     }
@@ -404,14 +422,14 @@ int launch_surf(const Plan& P, const Tree& T, bool dl, int nbox, const int* boxe
         if (diff)                                                                                                \
             k_surf_f<false, NP, NT, true><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p,  \
                                                               T.ns, q, sf, npts, stride, P.sin_h.p, P.sin_l.p,   \
-                                                              P.sexp.p);                                         \
+                                                              P.sexp.p, nullptr);                                \
         else                                                                                                     \
             k_surf_f<false, NP, NT><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, q,  \
-                                                        sf, npts, stride, P.sin_h.p, P.sin_l.p, P.sexp.p);       \
+                                                        sf, npts, stride, P.sin_h.p, P.sin_l.p, P.sexp.p, nullptr); \
         break;                                                                                                   \
     case 2 * (2 * NP * NT) + 1:                                                                                  \
         k_surf_f<true, NP, NT><<<nbox, NT, 0, s>>>(boxes, off, idx, down, P.bcf.p, T.rng.p, P.sxf.p, T.ns, q, sf,    \
-                                                   npts, stride, P.sin_h.p, P.sin_l.p, P.sexp.p);                \
+                                                   npts, stride, P.sin_h.p, P.sin_l.p, P.sexp.p, P.bax.p);       \
         break;
             KF_SURF(1, 128) KF_SURF(2, 96) KF_SURF(2, 128) KF_SURF(3, 96) KF_SURF(3, 128) KF_SURF(4, 128)
 #undef KF_SURF
@@ -1956,6 +1974,26 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         plane_k[a] = (signed char)k;
         return k;
     };
+    // DL: a source box's dipole axis (0..2; 3 mixed).  A leaf's near-field units hold boxes
+    // of one axis each, so that as many as can take the one-term kernel do (a cube's
+    // edges), and the surface kernel takes one term for such boxes too.
+    std::vector<signed char> box_ax;
+    if (!plane_k.empty()) box_ax.assign(T.nbox, -1);
+    auto axis_class = [&](int a) -> int {
+        if (box_ax.empty()) return 0;
+        if (box_ax[a] >= 0) return box_ax[a];
+        int k = 3;
+        const int64_t j0 = T.h_rng[4 * a], j1 = T.h_rng[4 * a + 1];
+        for (int d = 0; d < 3 && j1 > j0; ++d)
+            if (hsn[(size_t)d * T.ns + j0] != 0.0) k = k == 3 ? d : 4;
+        if (k == 4) k = 3;
+        for (int64_t j = j0; j < j1 && k < 3; ++j)
+            if (hsn[(size_t)k * T.ns + j] == 0.0 || hsn[(size_t)((k + 1) % 3) * T.ns + j] != 0.0 ||
+                hsn[(size_t)((k + 2) % 3) * T.ns + j] != 0.0)
+                k = 3;
+        box_ax[a] = (signed char)k;
+        return k;
+    };
     auto zero_pair = [&](int b, int a) -> bool {  // source box a adds exactly zero to leaf b
         if (plane_k.empty()) return false;
         const int k = src_plane(a);
@@ -2019,6 +2057,12 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     KF_TRY(P.tleaf.upload(tleaf, s));
     KF_TRY(P.p2p_off.upload(p2p_off, s));
     KF_TRY(P.p2p_idx.upload(p2p_idx, s));
+    if (!P.fp64 && !box_ax.empty()) {
+        std::vector<int> hbax(T.nbox, 3);
+        for (int a : s2u_idx) hbax[a] = axis_class(a);
+        for (int a : p2l_idx) hbax[a] = axis_class(a);
+        KF_TRY(P.bax.upload(hbax, s));
+    }
     // mixed: near-field work units of at most kP2PUnitSrc sources, heaviest first.  Each
     // range carries its offset exponent E (2^E above every coordinate offset of the leaf's
     // targets and the range's sources, from the boxes' extents) and the flags of an FP64
@@ -2036,25 +2080,6 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         std::vector<double> rext;              // per range: largest coordinate offset of its pairs
         auto half = [&](int box) { return std::ldexp(T.root_h, -T.h_lvl[box]); };
         auto exp_of = [](double ext) { return std::max(-100, std::min(100, std::ilogb(ext * (1.0 + 1e-12)) + 1)); };
-        // DL: a source box's dipole axis (0..2; 3 mixed), so that a leaf's units hold boxes
-        // of one axis each and as many as can take the one-term kernel do (a cube's edges)
-        std::vector<signed char> box_ax;
-        if (P.kernel == KIFMM_KERNEL_DL && !hsn.empty()) box_ax.assign(T.nbox, -1);
-        auto axis_class = [&](int a) -> int {
-            if (box_ax.empty()) return 0;
-            if (box_ax[a] >= 0) return box_ax[a];
-            int k = 3;
-            const int64_t j0 = T.h_rng[4 * a], j1 = T.h_rng[4 * a + 1];
-            for (int d = 0; d < 3 && j1 > j0; ++d)
-                if (hsn[(size_t)d * T.ns + j0] != 0.0) k = k == 3 ? d : 4;
-            if (k == 4) k = 3;
-            for (int64_t j = j0; j < j1 && k < 3; ++j)
-                if (hsn[(size_t)k * T.ns + j] == 0.0 || hsn[(size_t)((k + 1) % 3) * T.ns + j] != 0.0 ||
-                    hsn[(size_t)((k + 2) % 3) * T.ns + j] != 0.0)
-                    k = 3;
-            box_ax[a] = (signed char)k;
-            return k;
-        };
         std::vector<int> lb;
         for (size_t li = 0; li < tleaf.size(); ++li) {
             const int b = tleaf[li];
