@@ -2405,6 +2405,11 @@ template <typename Real>
 int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, const Real* ops, const Real* in,
               Real* out, int b0, int b1, cudaStream_t s, int& launches);
 
+// Evaluated near-field pairs per target below which the near field starts after M2L
+// (the 1M cube: 52, every other pair being an exact zero left out; curved surfaces:
+// several hundred).
+constexpr int64_t kLateNearPairs = 100;
+
 // Mixed precision: two-term FP16 on the tensor cores (tcgen05), every translation
 // between projected check potentials (see build_projected): U2U in the up basis (ru of
 // Ku per box), M2L from the up to the down basis, L2L in the down basis (rd of Kd).
@@ -2618,7 +2623,11 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         }
         ++launches;
     }
-    if (near_overlap) KF_TRY(fork_near());
+    // A near field much smaller than the far field (few evaluated pairs per target, as on
+    // flat faces) starts after M2L, beside the coarse L2L levels and D2T, rather than
+    // beside S2U and the upward pass, whose arithmetic it would slow.
+    const bool late_near = near_overlap && P.near_pairs < kLateNearPairs * T.nt;
+    if (near_overlap && !late_near) KF_TRY(fork_near());
     KF_TRY(mark(2));
     // mixed: the leaves' projections; U2U, deepest parents first
     if constexpr (mixed) KF_TRY(project(P, 3, P.proj_up, up, s, launches));
@@ -2639,6 +2648,10 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     // the upward pass split levels 3 and deeper (mixed); level 2 is split here
     KF_TRY(run_pairs<Real>(P, kM2L, P.m2l, 0, P.m2l.ntiles, B.m2l, up, dn, T.level_off[std::min(2, T.nlev)],
                            T.level_off[std::min(3, T.nlev)], s, launches));
+    if (late_near) {
+        KF_CHECK_CUDA(cudaEventRecord(P.ev_fork, s));
+        KF_TRY(fork_near());
+    }
     KF_TRY(mark(5));
     // L2L, coarsest children first (ADL in FP64: each level's potentials shifted to zero
     // mean first; the mixed tables carry that centring)
