@@ -254,12 +254,15 @@ typedef struct {
                                          on the projections onto Pu's range)          */
     int32_t m2l_rows;                 /* its rows: q_points (FP64) or rank_down (mixed:
                                          it yields the projection onto Pd's range)    */
-    int32_t near_units;               /* mixed: near-field work units (pieces of at
-                                         most 2048 sources of one target leaf)        */
+    int32_t near_units;               /* mixed: near-field work units (one pass of a
+                                         target leaf's targets over at most 2048 of
+                                         its sources)                                  */
     int32_t near_split_leaves;        /* mixed: target leaves spread over several
                                          units (their sums meet by FP64 atomics)      */
     int32_t near_overlap;             /* 1: the near field runs on its own (lowest-
-                                         priority) stream beside the far field, so its
+                                         priority) stream beside the far field -- from
+                                         the gather on, or after M2L when it evaluates
+                                         fewer than 100 pairs per target -- so its
                                          profiled phase time spans the overlap         */
     int32_t s2u_points;               /* up-check points S2U evaluates: q_points (FP64)
                                          or the skeleton of kifmm_up_skeleton (mixed)  */
