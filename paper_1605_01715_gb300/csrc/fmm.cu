@@ -2347,6 +2347,7 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
         KF_CHECK_CUDA(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
         KF_CHECK_CUDA(cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming));
         KF_CHECK_CUDA(cudaEventCreateWithFlags(&P.ev_far, cudaEventDisableTiming));
+        KF_CHECK_CUDA(cudaEventCreateWithFlags(&P.ev_zero, cudaEventDisableTiming));
     }
 
     KF_TRY(stamp(2));
@@ -2604,8 +2605,13 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
         up = P.zu.p;
         dn = P.zd.p;
         dw = P.ops->Kd;
-        KF_CHECK_CUDA(cudaMemsetAsync(up, 0, P.zu.bytes(), s));
-        KF_CHECK_CUDA(cudaMemsetAsync(dn, 0, P.zd.bytes(), s));
+        // zeroed on the near field's stream when there is one, beside S2U (which does not
+        // touch them); the far field waits before its first accumulation into them
+        const cudaStream_t zs = near_overlap ? P.near_stream : s;
+        if (near_overlap) KF_CHECK_CUDA(cudaStreamWaitEvent(zs, P.ev_fork, 0));
+        KF_CHECK_CUDA(cudaMemsetAsync(up, 0, P.zu.bytes(), zs));
+        KF_CHECK_CUDA(cudaMemsetAsync(dn, 0, P.zd.bytes(), zs));
+        if (near_overlap) KF_CHECK_CUDA(cudaEventRecord(P.ev_zero, zs));
         launches += 2;
     }
     KF_TRY(mark(1));
@@ -2630,7 +2636,10 @@ int matvec(Plan& P, const Bufs<Real>& B, const double* q, double* out, cudaStrea
     if (near_overlap && !late_near) KF_TRY(fork_near());
     KF_TRY(mark(2));
     // mixed: the leaves' projections; U2U, deepest parents first
-    if constexpr (mixed) KF_TRY(project(P, 3, P.proj_up, up, s, launches));
+    if constexpr (mixed) {
+        if (near_overlap) KF_CHECK_CUDA(cudaStreamWaitEvent(s, P.ev_zero, 0));
+        KF_TRY(project(P, 3, P.proj_up, up, s, launches));
+    }
     for (int l = T.nlev - 1; l >= 2; --l)
         KF_TRY(run_pairs<Real>(P, kU2U, P.u2u, P.u2u.level_tile[l], P.u2u.level_tile[l + 1], B.m2m, up, up,
                                T.level_off[std::min(l + 1, T.nlev)], T.level_off[std::min(l + 2, T.nlev)], s,

@@ -141,7 +141,7 @@ struct Plan {
     // far field's many short launches leave idle; both join the caller's stream before
     // the far-field sum is added
     cudaStream_t near_stream = nullptr, far_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr, ev_zero = nullptr;
     const double* g_q = nullptr;
     double* g_out = nullptr;
 
@@ -169,6 +169,7 @@ struct Plan {
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (ev_far) cudaEventDestroy(ev_far);
+        if (ev_zero) cudaEventDestroy(ev_zero);
         if (near_stream) cudaStreamDestroy(near_stream);
         if (far_stream) cudaStreamDestroy(far_stream);
     }
