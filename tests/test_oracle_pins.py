@@ -194,6 +194,32 @@ def test_scaling_exponents():
         assert np.allclose(f2 * L**power, f1, rtol=1e-12, atol=1e-12 * np.abs(f1).max())
 
 
+def test_flat_plate_double_layer():
+    """A flat plate's double layer, dipoles along its normal: exactly zero at the plate's
+    own points (n.(x - y) = 0 for every pair), and the solid angle of the square on its
+    axis (4 atan(a^2 / (z sqrt(2 a^2 + z^2))) for a square of side 2a at height z),
+    approached as h^2 by the midpoint rule."""
+    a, z = 1.0, 0.3
+    omega = 4.0 * math.atan(a * a / (z * math.sqrt(2 * a * a + z * z)))
+    errs = []
+    for n in (32, 64):
+        h = 2 * a / n
+        c = -a + h * (np.arange(n) + 0.5)
+        gx, gy = np.meshgrid(c, c, indexing="ij")
+        src = np.stack([gx.ravel(), gy.ravel(), np.zeros(n * n)])
+        nrm = np.zeros_like(src)
+        nrm[2] = 1.0
+        w = np.full(n * n, h * h)
+        own = oracle.direct("dl", src, src, w, src_nrm=nrm)
+        assert np.all(own == 0.0)
+        above = oracle.direct("dl", np.array([[0.0], [0.0], [z]]), src, w, src_nrm=nrm)[0]
+        below = oracle.direct("dl", np.array([[0.0], [0.0], [-z]]), src, w, src_nrm=nrm)[0]
+        assert below == pytest.approx(-above, rel=1e-14)
+        errs.append(abs(above - omega) / omega)
+    assert errs[1] < 1e-3
+    assert 0.15 < errs[1] / errs[0] < 0.35
+
+
 def test_tolerance_radius_exclusion():
     """Pairs closer than 1e-5 contribute nothing (Sec. III.A.1); farther pairs do."""
     d = oracle.DELTA
