@@ -252,6 +252,48 @@ __device__ __forceinline__ void surf_pairs(const float4* __restrict__ sp, const 
     }
 }
 
+// Dipoles along axis K whose sources all lie in one plane normal to K (a flat face's
+// leaf): the offset along K, dk = p_K - c, is the same for every source of the box, so
+// the pairs only sum q_K / r^3 (r^2 = the in-plane offsets' squares + dk^2) and the
+// caller multiplies the box's sum by dk once.  Two in-plane offsets instead of three.
+template <bool NEAR, int NP, int K>
+__device__ __forceinline__ void surf_pairs_plane(const float4* __restrict__ sp, const float4* __restrict__ sd,
+                                                 int cnt, const float2* px, const float2* py, const float2* pz,
+                                                 const float2* dk2, float2* acc) {
+    const float d2 = (float)(kDelta * kDelta);
+#pragma unroll 2
+    for (int jj = 0; jj < cnt; ++jj) {
+        const float4 y = sp[jj];
+        const float4 dq = sd[jj];
+        const float qk = K == 0 ? y.w : (K == 1 ? dq.x : dq.y);
+        const float ya = K == 0 ? y.y : y.x, yb = K == 2 ? y.y : y.z;      // the in-plane coordinates
+        const float2 na = make_float2(-ya, -ya), nb = make_float2(-yb, -yb), q2 = make_float2(qk, qk);
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            const float2 da = __fadd2_rn(K == 0 ? py[m] : px[m], na);
+            const float2 db = __fadd2_rn(K == 2 ? py[m] : pz[m], nb);
+            const float2 r2 = __ffma2_rn(da, da, __ffma2_rn(db, db, dk2[m]));
+            const float2 inv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+            float2 w = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+            if (NEAR) {
+                w.x = r2.x >= d2 ? w.x : 0.f;
+                w.y = r2.y >= d2 ? w.y : 0.f;
+            }
+            acc[m] = __ffma2_rn(q2, w, acc[m]);
+        }
+    }
+}
+
+template <bool NEAR, int NP>
+__device__ __forceinline__ void surf_pairs_plane_k(int k, const float4* __restrict__ sp,
+                                                   const float4* __restrict__ sd, int cnt, const float2* px,
+                                                   const float2* py, const float2* pz, const float2* dk2,
+                                                   float2* acc) {
+    if (k == 0) surf_pairs_plane<NEAR, NP, 0>(sp, sd, cnt, px, py, pz, dk2, acc);
+    else if (k == 1) surf_pairs_plane<NEAR, NP, 1>(sp, sd, cnt, px, py, pz, dk2, acc);
+    else surf_pairs_plane<NEAR, NP, 2>(sp, sd, cnt, px, py, pz, dk2, acc);
+}
+
 template <bool NEAR, bool DIPOLE, int NP, bool DIFF>
 __device__ __forceinline__ void surf_pairs_ax(int ax, const float4* __restrict__ sp, const float4* __restrict__ sd,
                                               int cnt, const float2* px, const float2* py, const float2* pz,
@@ -307,7 +349,25 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
         const float dm = fmaxf(fabsf((ah.x - bh.x) + (al.x - bl.x)),
                                fmaxf(fabsf((ah.y - bh.y) + (al.y - bl.y)), fabsf((ah.z - bh.z) + (al.z - bl.z))));
         const bool near = fmaxf(dm - ah.w - rf, rf - dm - ah.w) <= margin;
-        const int ax = (DIPOLE && bax) ? bax[a] : 3;      // the source box's dipole axis, or 3
+        // the source box's dipole axis (0..2), 3, or 4 + the axis of a box in one plane
+        // (the plane form only at 2 NP <= 4 points a thread: above, its extra registers spill)
+        const int ax0 = (DIPOLE && bax && se > sb) ? bax[a] : 3;
+        const bool plane = DIPOLE && NP <= 2 && ax0 >= 4;
+        const int ax = ax0 >= 4 && !plane ? ax0 - 4 : ax0;
+        float2 dk[NP], dk2[NP], accb[NP];
+        if (plane) {
+            // the plane's offset from the box centre, formed as the staged sources' are
+            const int k = ax - 4;
+            const float c = k == 0 ? (sxf[sb] - bh.x) + (sxf[3 * ns + sb] - bl.x)
+                          : k == 1 ? (sxf[ns + sb] - bh.y) + (sxf[4 * ns + sb] - bl.y)
+                                   : (sxf[2 * ns + sb] - bh.z) + (sxf[5 * ns + sb] - bl.z);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) {
+                dk[m] = __fadd2_rn(k == 0 ? px[m] : (k == 1 ? py[m] : pz[m]), make_float2(-c, -c));
+                dk2[m] = __fmul2_rn(dk[m], dk[m]);
+                accb[m] = make_float2(0.f, 0.f);
+            }
+        }
         for (int64_t j0 = sb; j0 < se; j0 += NT) {
             const int64_t j = j0 + threadIdx.x;
             if (j < se) {
@@ -324,11 +384,19 @@ k_surf_f(const int* __restrict__ boxes, const int* __restrict__ off, const int* 
             }
             __syncthreads();
             const int cnt = (int)((se - j0) < (int64_t)NT ? (se - j0) : (int64_t)NT);
-            if (near)
+            if (plane) {
+                if (near) surf_pairs_plane_k<true, NP>(ax - 4, sp, sd, cnt, px, py, pz, dk2, accb);
+                else surf_pairs_plane_k<false, NP>(ax - 4, sp, sd, cnt, px, py, pz, dk2, accb);
+            } else if (near) {
                 surf_pairs_ax<true, DIPOLE, NP, DIFF>(ax, sp, sd, cnt, px, py, pz, acc, pp);
-            else
+            } else {
                 surf_pairs_ax<false, DIPOLE, NP, DIFF>(ax, sp, sd, cnt, px, py, pz, acc, pp);
+            }
             __syncthreads();
+        }
+        if (plane) {
+#pragma unroll
+            for (int m = 0; m < NP; ++m) acc[m] = __ffma2_rn(accb[m], dk[m], acc[m]);
         }
     }
     // the box's largest |potential| (points past Q hold partial sums of a repeated point)
@@ -2059,8 +2127,10 @@ int setup(Plan& P, const double* src_nrm, const double* trg_nrm, cudaStream_t s)
     KF_TRY(P.p2p_idx.upload(p2p_idx, s));
     if (!P.fp64 && !box_ax.empty()) {
         std::vector<int> hbax(T.nbox, 3);
-        for (int a : s2u_idx) hbax[a] = axis_class(a);
-        for (int a : p2l_idx) hbax[a] = axis_class(a);
+        // 4 + k: every source of the box in one plane normal to its dipoles' axis k
+        auto code = [&](int a) { return src_plane(a) >= 0 ? 4 + src_plane(a) : axis_class(a); };
+        for (int a : s2u_idx) hbax[a] = code(a);
+        for (int a : p2l_idx) hbax[a] = code(a);
         KF_TRY(P.bax.upload(hbax, s));
     }
     // mixed: near-field work units of at most kP2PUnitSrc sources, heaviest first.  Each

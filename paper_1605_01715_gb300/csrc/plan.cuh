@@ -87,7 +87,8 @@ struct Plan {
     DBuf<float> sxf;                // mixed: sorted source coordinates as FP32 hi/lo pairs, 6 x ns SoA
     DBuf<float> txf;                // mixed, targets apart from the sources: the same for them
     DBuf<float4> bcf;               // mixed: per box {centre hi, h}, {centre lo, 0}, {r_upcheck, r_dncheck}
-    DBuf<int> bax;                  // mixed DL: per source leaf, the one axis of its dipoles (0..2) or 3
+    DBuf<int> bax;                  // mixed DL: per source leaf, the one axis k of its dipoles (0..2), 3
+                                    // (none), or 4 + k when its points also lie in one plane normal to k
     DBuf<float> tnrm_f;             // mixed ADL: sorted target normals, FP32 hi (3 rows) and lo (3 rows)
 
     // work lists
