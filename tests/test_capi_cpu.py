@@ -134,3 +134,31 @@ def test_up_skeleton_sizes_and_arguments(lib):
     for p, k in ((1, 1), (17, 1), (10, 0), (10, 489)):
         with pytest.raises(KifmmError):
             kifmm_up_skeleton(p, k)
+
+
+def test_stats_structs_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of kifmm_tree_stats and kifmm_plan_stats have the C
+    header's size and field offsets (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    from paper_1605_01715_gb300.capi import PlanStats, TreeStats
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no host C compiler")
+    structs = (("kifmm_tree_stats", TreeStats), ("kifmm_plan_stats", PlanStats))
+    body = ['#include <stdio.h>', '#include <stddef.h>', '#include "kifmm.h"', "int main(void) {"]
+    for cname, cls in structs:
+        body.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            body.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    body += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(body) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.splitlines())
+    for cname, cls in structs:
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(cls, f).offset, (cname, f)
