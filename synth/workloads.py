@@ -8,9 +8,10 @@ Sizes follow the configurations the library is benchmarked and tested on:
 * ``demag_cube_1m``   unit cube, n=296 per face (1,051,392 triangles), double
                       layer with density n.M, M = z-hat, p=10 (p=8 misses 1e-6),
                       both pseudo-inverses truncated at 1e-8 (enough on flat faces),
-                      at most 128 points per leaf.
+                      at most 192 points per leaf (``demag_cube_270k``: n=150, the
+                      same knobs but the truncations, for profiling).
 * ``demag_sphere_1m`` unit geodesic sphere f=229 (1,048,820 triangles), same
-                      (default truncations).
+                      (default truncations), at most 128 points per leaf.
 * ``polar_64``        64 spheres, radii U[0.5,1.5], centres in a 20^3 box with a
                       0.05 surface gap, f=23 (10,580 triangles each, 677,120
                       unknowns), contrast eps_in/eps_out U[2,20], E0 = z-hat; adjoint
@@ -45,12 +46,12 @@ def _sl_sphere_20k():
 
 def _demag_cube_1m():
     m = cube_surface(296)
-    return dict(mesh=m, kernel="dl", p=10, max_leaf=128, magnetization=(0.0, 0.0, 1.0), pinv_cutoff=1e-8)
+    return dict(mesh=m, kernel="dl", p=10, max_leaf=192, magnetization=(0.0, 0.0, 1.0), pinv_cutoff=1e-8)
 
 
 def _demag_cube_270k():
     m = cube_surface(150)
-    return dict(mesh=m, kernel="dl", p=10, max_leaf=128, magnetization=(0.0, 0.0, 1.0))
+    return dict(mesh=m, kernel="dl", p=10, max_leaf=192, magnetization=(0.0, 0.0, 1.0))
 
 
 def _demag_sphere_1m():
