@@ -2477,8 +2477,8 @@ int run_pairs(const Plan& P, int which, const PairTiles& pt, int t0, int t1, con
               Real* out, int b0, int b1, cudaStream_t s, int& launches);
 
 // Evaluated near-field pairs per target below which the near field starts after M2L
-// (the 1M cube: 52, once its exact zeros are left out; curved surfaces: several
-// hundred).
+// (the 1M cube at 128 points per leaf: 52, once its exact zeros are left out; at 192:
+// 298; curved surfaces: several hundred).
 constexpr int64_t kLateNearPairs = 100;
 
 // Mixed precision: two-term FP16 on the tensor cores (tcgen05), every translation
